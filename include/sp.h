@@ -1,0 +1,177 @@
+/*
+ * sp.h -- C ABI of the region-scheduled ("semi-parallel") evolution of a
+ * complex scalar string field on one GB300.
+ *
+ * The method (Blanco-Pillado, Olum, Shlaer, "A new parallel simulation
+ * technique", Sec. 1-4): spacetime is cut by null surfaces into many small
+ * regions that receive data only through initial surfaces and emit it only
+ * through final surfaces, so each region can be evolved on its own as soon as
+ * its predecessors are done, and a manager hands ready regions to workers
+ * (Sec. 4).  Here a region is a pyramid, inverted pyramid or wedge of B^3
+ * lattice cells and B/2 leapfrog steps; the manager is a device work queue
+ * and the workers are the CTAs of one persistent kernel.  The model equation,
+ * in conformal time tau with a = (tau / tau_ref)^nu, is
+ *
+ *   phi'' + 2 (nu / tau) phi' - Lap7 phi + a^2 lambda (|phi|^2 - eta^2) phi = 0,
+ *
+ * advanced by the staggered leapfrog (FP32 with a Kahan-compensated drift).
+ *
+ * Conventions for every entry point:
+ *   - Return value: SP_OK (0) or a negative SP_E* code; sp_strerror() names
+ *     it.  No C++ exception crosses this boundary.
+ *   - Device pointers are plain CUDA device addresses of the current device.
+ *     Host pointers are ordinary (preferably pinned) host memory.
+ *   - Work is enqueued on the stream given at creation.  Asynchronous device
+ *     errors (a bounded wait that gave up, a CUDA fault) are reported by the
+ *     next call that synchronises (sp_evolve without SP_ASYNC,
+ *     sp_read_surface).
+ *   - Fields: complex64 arrays (float2: re, im) of n[0]*n[1]*n[2] sites,
+ *     x fastest: site index x + n[0] * (y + n[1] * z).
+ */
+#ifndef SP_H
+#define SP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define SP_OK 0
+#define SP_EINVAL (-1)          /* bad argument or call order */
+#define SP_ENOMEM (-2)          /* device or host allocation failed */
+#define SP_ECUDA (-3)           /* a CUDA runtime call failed */
+#define SP_EUNSTABLE (-4)       /* leapfrog stability bound violated by the plan */
+#define SP_ETIMEOUT (-5)        /* a bounded device wait gave up */
+#define SP_ENONFINITE (-6)      /* non-finite field detected by a diagnostic */
+#define SP_EFAULT_INJECTED (-7) /* a host-injected region failure was recorded */
+#define SP_ENOTPLANNED (-8)     /* sp_evolve before sp_region_plan */
+
+/* ---- flags of sp_evolve ---- */
+#define SP_ASYNC 1u      /* return without synchronising the stream */
+#define SP_MONOLITHIC 2u /* whole-grid sweep, one launch per step (comparator) */
+#define SP_RESTART 4u    /* treat the current state as level 0 (tau = tau0) */
+#define SP_TRACE 8u      /* record (start, end) globaltimer ns of every region (SP_SURF_TRACE) */
+
+/* ---- what of sp_read_surface / sp_write_surface ---- */
+#define SP_SURF_STATE 0   /* phi, pi, c of one simulation: 3 * sites * 8 bytes */
+#define SP_SURF_DIAG 1    /* one sp_diag */
+#define SP_SURF_TRACE 2   /* per-region (start, end) ns of the last region launch */
+#define SP_SURF_WINDING 3 /* int8 plaquette windings [3][sites] */
+#define SP_SURF_PLAN 4    /* one sp_plan_info */
+
+/* ---- region ordering of sp_region_plan ---- */
+#define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
+#define SP_ORDER_LEARNED 1 /* cost-model priority (results are identical) */
+
+typedef struct sp_grid sp_grid; /* opaque */
+
+/* Physical and numerical parameters of one simulation. */
+typedef struct {
+    int32_t n[3];        /* grid sides (sites); each a multiple of the region base B, n/B >= 2 */
+    double dx;           /* lattice spacing (> 0) */
+    double dt;           /* conformal time step (> 0) */
+    double lambda;       /* quartic coupling (>= 0) */
+    double eta;          /* vacuum expectation value (>= 0) */
+    double nu;           /* expansion exponent: a = (tau / tau_ref)^nu; 0 flat, 1 radiation, 2 matter */
+    double tau0;         /* conformal time at level 0 (> 0) */
+    double tau_ref;      /* time at which a = 1 (> 0); normally tau0 + steps * dt */
+    int32_t damp_steps;  /* initial levels with the velocity discarded each step (tau frozen at tau0) */
+    int32_t reserved;    /* must be 0 */
+} sp_params;
+
+/* Diagnostics of one simulation at its current level. */
+typedef struct {
+    int64_t level;          /* current level n */
+    double tau, a;          /* conformal time and scale factor at that level */
+    double kinetic;         /* sum |pi|^2 (pi at n - 1/2) */
+    double gradient;        /* sum over forward links |phi(x+e) - phi(x)|^2 / dx^2 */
+    double potential;       /* sum a^2 (lambda / 2) (|phi|^2 - eta^2)^2 */
+    double total;           /* kinetic + gradient + potential */
+    int64_t pierced[3];     /* plaquettes with nonzero winding, by normal axis x, y, z */
+    int64_t abs_winding;    /* sum |W| over all plaquettes */
+    int64_t net_winding[3]; /* sum W by normal axis (0 on a periodic grid) */
+    double string_length;   /* (pierced[0] + pierced[1] + pierced[2]) * dx */
+} sp_diag;
+
+/* Plan summary of one simulation (traffic is of this design, per band). */
+typedef struct {
+    int32_t base_B, threads, ctas_per_sm, grid;
+    int64_t regions_per_band;
+    int64_t updates_per_band;
+    int64_t bytes_read_per_band;
+    int64_t bytes_written_per_band;
+    double bytes_per_update;
+    int64_t mailbox_bytes;
+} sp_plan_info;
+
+/*
+ * sp_grid_create -- describe n_sims independent simulations.
+ *   p         : array of n_sims parameter sets (host memory, copied).
+ *   state_dev : NULL, or 3 * n_sims device pointers (phi, pi, c of sim 0, then
+ *               sim 1, ...), each n[0]*n[1]*n[2] float2.  The caller keeps
+ *               ownership and must keep them alive until sp_destroy.  With
+ *               NULL the library allocates zeroed state it frees itself.
+ *               Between calls the state holds (phi_n, pi_{n-1/2}, c_n).
+ *   cuda_stream : cudaStream_t used for all work (NULL = legacy stream).
+ *   out       : receives the handle.
+ * Errors: SP_EINVAL (bad parameters), SP_ENOMEM, SP_ECUDA.
+ */
+int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, void *cuda_stream, sp_grid **out);
+
+/*
+ * sp_region_plan -- build the region tiling, the dependency DAG and the
+ * surface routing tables (paper Sec. 2 geometry and Sec. 3 sizing), and size
+ * the persistent launch.
+ *   base_B     : region base in cells (8 or 16; B/2 steps per band), or 0 to
+ *                pick one per simulation.  Every n[d] must be a multiple of B
+ *                with n[d] / B >= 2.
+ *   block_shape: threads per CTA (128, 256, 512 or 1024), or 0 for the default.
+ *   order      : SP_ORDER_STATIC or SP_ORDER_LEARNED.
+ *   model_path : cost-model weights for SP_ORDER_LEARNED, or NULL.
+ * Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA.
+ */
+int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t order, const char *model_path);
+
+/*
+ * sp_evolve -- advance every simulation by n_steps leapfrog steps.
+ * Whole bands of B/2 steps run as regions in one persistent launch; a
+ * remainder of fewer than B/2 steps runs as whole-grid steps with the same
+ * arithmetic.  SP_MONOLITHIC runs every step as a whole-grid sweep (bit-exact
+ * with the region path).  Unless SP_ASYNC is given the call synchronises the
+ * stream and reports device errors.
+ * Errors: SP_EINVAL, SP_ENOTPLANNED, SP_EUNSTABLE (dt^2 (12/dx^2 + 2 lambda
+ * eta^2 a^2) >= 4 at some level), SP_ETIMEOUT, SP_ECUDA.
+ */
+int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags);
+
+/*
+ * sp_read_surface -- copy out one simulation's state or diagnostics.
+ *   what : SP_SURF_STATE, SP_SURF_DIAG, SP_SURF_TRACE, SP_SURF_WINDING or
+ *          SP_SURF_PLAN; dst_bytes must be at least the size of that item.
+ *   dst_is_device : nonzero if dst is device memory.
+ * Synchronises the stream.  Errors: SP_EINVAL, SP_ETIMEOUT (pending device
+ * error), SP_ECUDA.
+ */
+int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size_t dst_bytes, int32_t dst_is_device);
+
+/*
+ * sp_write_surface -- load one simulation's state (what = SP_SURF_STATE:
+ * phi, pi, c consecutively, 3 * sites * 8 bytes) from host or device memory.
+ * Enqueued on the grid's stream.  Errors: SP_EINVAL, SP_ECUDA.
+ */
+int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device);
+
+/* sp_destroy -- free everything the library allocated (not caller state). */
+int sp_destroy(sp_grid *g);
+
+/* sp_strerror -- static description of an error code. */
+const char *sp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP_H */

@@ -1,0 +1,319 @@
+// planner.cpp -- builds the split-tiling tables (see planner.h).
+//
+// Everything here is derived by enumerating cells: for each region type and
+// level, which cells it computes, which cells it must receive (its initial
+// surfaces), who computes those, and where they go.  The kernel follows the
+// resulting lists; no geometry is hand-coded on the device.
+#include "planner.h"
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <set>
+#include <sstream>
+#include <tuple>
+
+namespace sp {
+
+static int floor_div(int a, int b)
+{
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+bool owner_1d(int r, int L, int B, int *delta)
+{
+    // Inverted piece I_m covers [m B - L, m B + L) and upright U_m covers
+    // [m B + L, m B + B - L) at level L (offsets from c_j).
+    int m = floor_div(r + L, B);
+    int rr = r - m * B;  // in [-L, B - L)
+    *delta = m;
+    return rr < L;
+}
+
+namespace {
+
+inline bool in_active_1d(bool inv, int r, int k, int B)
+{
+    return inv ? (r >= -k && r < k) : (r >= k && r < B - k);
+}
+
+inline bool in_active(int S, const int r[3], int k, int B)
+{
+    if (k <= 0) return false;
+    for (int d = 0; d < 3; ++d)
+        if (!in_active_1d(inverted(S, d), r[d], k, B)) return false;
+    return true;
+}
+
+// 7-point neighbour of A(k) but not in A(k)
+inline bool in_ring(int S, const int r[3], int k, int B)
+{
+    if (in_active(S, r, k, B)) return false;
+    for (int d = 0; d < 3; ++d)
+        for (int s = -1; s <= 1; s += 2) {
+            int q[3] = {r[0], r[1], r[2]};
+            q[d] += s;
+            if (in_active(S, q, k, B)) return true;
+        }
+    return false;
+}
+
+inline int u_of(int S, int d, int r, int H) { return r + (inverted(S, d) ? H + 1 : 1); }
+
+struct Idx {
+    int phi, pc;
+};
+
+inline Idx index_of(int S, const int r[3], int B)
+{
+    int H = B / 2, P = B + 2;
+    int u[3];
+    for (int d = 0; d < 3; ++d) u[d] = u_of(S, d, r[d], H);
+    Idx x;
+    x.phi = (u[2] * P + u[1]) * P + u[0];
+    bool own = true;
+    for (int d = 0; d < 3; ++d) own = own && u[d] >= 1 && u[d] <= B;
+    x.pc = own ? ((u[2] - 1) * B + (u[1] - 1)) * B + (u[0] - 1) : -1;
+    return x;
+}
+
+inline bool in_u_box(int S, const int r[3], int B)
+{
+    int H = B / 2, P = B + 2;
+    for (int d = 0; d < 3; ++d) {
+        int u = u_of(S, d, r[d], H);
+        if (u < 0 || u >= P) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+std::string build_tables(int B, TileTables *tp)
+{
+    TileTables &t = *tp;
+    t = TileTables();
+    if (B % 2 != 0 || B < 4 || B > kMaxB) return "base size B must be even and in [4, 32]";
+    const int H = B / 2, P = B + 2;
+    t.B = B;
+    t.H = H;
+    t.P = P;
+    const int rlo = -H - 2, rhi = B + 2;  // enumeration range of offsets per axis
+
+    for (int S = 0; S < kTypes; ++S) {
+        t.levels[S] = (S == kTypes - 1) ? H : H - 1;
+        for (int k = 0; k <= kMaxH; ++k)
+            for (int d = 0; d < 3; ++d) {
+                int lo, hi;
+                if (k == 0 || k > H) {
+                    lo = hi = 1;
+                } else if (inverted(S, d)) {
+                    lo = H - k + 1;
+                    hi = H + k + 1;
+                } else {
+                    lo = k + 1;
+                    hi = B - k + 1;
+                }
+                t.active[S][k].lo[d] = lo;
+                t.active[S][k].hi[d] = hi;
+            }
+        for (int d = 0; d < 3; ++d) {
+            bool inv = inverted(S, d);
+            // phi: A(1) grown by one cell; pc: A(1)
+            t.base_phi[S].lo[d] = inv ? H - 1 : 1;
+            t.base_phi[S].hi[d] = inv ? H + 3 : B + 1;
+            t.base_pc[S].lo[d] = inv ? H : 2;
+            t.base_pc[S].hi[d] = inv ? H + 2 : B;
+        }
+    }
+
+    // ---- sloped initial surfaces: imports per (consumer type, level) ----
+    struct Exp {
+        int producer, L;
+        ExportEntry e;
+    };
+    std::vector<Exp> exports;
+    std::set<std::tuple<int, int, int, int>> preds[kTypes];       // (S', dx, dy, dz)
+    std::set<std::tuple<int, int, int, int>> succs[kTypes];       // (S, ex, ey, ez)
+    int64_t imp_bytes[kTypes] = {0};
+    for (int S = 0; S < kTypes; ++S) {
+        int32_t off = 0;
+        for (int L = 0; L < kMaxH; ++L) {
+            t.imp_full_off[S][L] = (int32_t)t.imp_full.size();
+            t.imp_phi_off[S][L] = (int32_t)t.imp_phi.size();
+            t.imp_full_n[S][L] = t.imp_phi_n[S][L] = 0;
+            t.mb_level_off[S][L] = off;
+            if (L < 1 || L > H - 1) continue;
+            std::vector<std::array<int, 3>> full, ring;
+            for (int z = rlo; z < rhi; ++z)
+                for (int y = rlo; y < rhi; ++y)
+                    for (int x = rlo; x < rhi; ++x) {
+                        int r[3] = {x, y, z};
+                        if (in_active(S, r, L, B)) continue;
+                        if (in_active(S, r, L + 1, B))
+                            full.push_back({x, y, z});
+                        else if (in_ring(S, r, L + 1, B))
+                            ring.push_back({x, y, z});
+                    }
+            const int nf = (int)full.size(), np = (int)ring.size();
+            t.imp_full_n[S][L] = nf;
+            t.imp_phi_n[S][L] = np;
+            imp_bytes[S] += 24LL * nf + 8LL * np;
+            for (int kind = 0; kind < 2; ++kind) {
+                const auto &cells = kind == 0 ? full : ring;
+                for (int i = 0; i < (int)cells.size(); ++i) {
+                    int r[3] = {cells[i][0], cells[i][1], cells[i][2]};
+                    if (!in_u_box(S, r, B)) return "import cell outside the region's shared-memory box";
+                    Idx ix = index_of(S, r, B);
+                    if (kind == 0) {
+                        if (ix.pc < 0) return "full-state import is not one of the region's own cells";
+                        t.imp_full.push_back(ix.phi | (ix.pc << 16));
+                    } else {
+                        t.imp_phi.push_back(ix.phi);
+                    }
+                    // owner at level L in the same band
+                    int Sp = 0, delta[3], rp[3];
+                    for (int d = 0; d < 3; ++d) {
+                        bool inv = owner_1d(r[d], L, B, &delta[d]);
+                        if (inv) Sp |= 1 << d;
+                        if (delta[d] < -1 || delta[d] > 0) return "import owner is not an adjacent region";
+                        if (!inverted(S, d) && (inv || delta[d] != 0))
+                            return "import along an upright axis comes from another region";
+                        rp[d] = r[d] - delta[d] * B;
+                    }
+                    if ((Sp & ~S) != 0 || Sp == S) return "import owner type is not a proper subset";
+                    if (!in_active(Sp, rp, L, B)) return "import owner does not compute the cell";
+                    Idx px = index_of(Sp, rp, B);
+                    if (px.pc < 0) return "producer cell outside its own box";
+                    int ebits = 0;
+                    for (int d = 0; d < 3; ++d)
+                        if (delta[d] == -1) ebits |= 1 << d;
+                    ExportEntry e;
+                    e.src = px.phi | ((kind == 0 ? px.pc : 0xFFFF) << 16);
+                    e.code = S | (ebits << 3);
+                    e.dst_phi = kind == 0 ? off + 2 * nf + i : off + 3 * nf + i;
+                    e.dst_pc = kind == 0 ? off + 2 * i : -1;
+                    exports.push_back({Sp, L, e});
+                    preds[S].insert({Sp, delta[0], delta[1], delta[2]});
+                    succs[Sp].insert({S, -delta[0], -delta[1], -delta[2]});
+                }
+            }
+            off += 3 * nf + np;
+            off += off & 1;  // keep every chunk 16-byte aligned
+        }
+        t.mb_size[S] = off;
+    }
+
+    // ---- final surfaces: export lists per (producer type, level) ----
+    std::stable_sort(exports.begin(), exports.end(), [](const Exp &a, const Exp &b) {
+        if (a.producer != b.producer) return a.producer < b.producer;
+        if (a.L != b.L) return a.L < b.L;
+        if (a.e.code != b.e.code) return a.e.code < b.e.code;
+        return a.e.dst_phi < b.e.dst_phi;
+    });
+    int64_t exp_bytes[kTypes] = {0};
+    {
+        size_t i = 0;
+        for (int S = 0; S < kTypes; ++S)
+            for (int L = 0; L < kMaxH; ++L) {
+                t.exp_off[S][L] = (int32_t)t.exp.size();
+                while (i < exports.size() && exports[i].producer == S && exports[i].L == L) {
+                    t.exp.push_back(exports[i].e);
+                    exp_bytes[S] += exports[i].e.dst_pc >= 0 ? 24 : 8;
+                    ++i;
+                }
+                t.exp_n[S][L] = (int32_t)t.exp.size() - t.exp_off[S][L];
+            }
+        if (i != exports.size()) return "export bookkeeping mismatch";
+    }
+
+    // ---- band base: previous band's inverted-pyramid tops ----
+    std::set<std::tuple<int, int, int, int>> nsucc[2];
+    for (int S = 0; S < kTypes; ++S) {
+        int64_t base_cells = 0;
+        std::set<std::tuple<int, int, int>> own[2];
+        for (int z = rlo; z < rhi; ++z)
+            for (int y = rlo; y < rhi; ++y)
+                for (int x = rlo; x < rhi; ++x) {
+                    int r[3] = {x, y, z};
+                    if (!in_active(S, r, 1, B) && !in_ring(S, r, 1, B)) continue;
+                    ++base_cells;
+                    for (int d = 0; d < 3; ++d) {
+                        int u = u_of(S, d, r[d], H);
+                        if (u < t.base_phi[S].lo[d] || u >= t.base_phi[S].hi[d]) return "base cell outside base box";
+                    }
+                    for (int q = 0; q < 2; ++q) {
+                        // owner index offset i - j of T(xyz) in band b-1, band b offset parity q
+                        int o[3];
+                        for (int d = 0; d < 3; ++d) o[d] = q + floor_div(r[d], B);
+                        own[q].insert({o[0], o[1], o[2]});
+                        nsucc[q].insert({S, -o[0], -o[1], -o[2]});
+                    }
+                }
+        if (own[0].size() != own[1].size()) return "previous-band predecessor count depends on parity";
+        t.prev_preds[S] = (int32_t)own[0].size();
+        t.same_preds[S] = (int32_t)preds[S].size();
+        int expect_same = 1;
+        for (int d = 0; d < 3; ++d) expect_same *= inverted(S, d) ? 3 : 1;
+        if (t.same_preds[S] > expect_same - 1) return "more same-band predecessors than 3^|S| - 1";
+        if (t.prev_preds[S] != (1 << __builtin_popcount(S))) return "previous-band predecessor count is not 2^|S|";
+        for (auto &s : succs[S]) {
+            Succ x;
+            x.type = (int8_t)std::get<0>(s);
+            x.e[0] = (int8_t)std::get<1>(s);
+            x.e[1] = (int8_t)std::get<2>(s);
+            x.e[2] = (int8_t)std::get<3>(s);
+            t.same_succ[S].push_back(x);
+        }
+        t.updates[S] = 0;
+        for (int k = 1; k <= t.levels[S]; ++k) t.updates[S] += t.active[S][k].volume();
+        t.bytes_read[S] = 8 * base_cells + 16 * t.active[S][1].volume() + imp_bytes[S];
+        t.bytes_written[S] = exp_bytes[S] + (S == kTypes - 1 ? 24LL * B * B * B : 0);
+    }
+    for (int q = 0; q < 2; ++q)
+        for (auto &s : nsucc[q]) {
+            Succ x;
+            x.type = (int8_t)std::get<0>(s);
+            x.e[0] = (int8_t)std::get<1>(s);
+            x.e[1] = (int8_t)std::get<2>(s);
+            x.e[2] = (int8_t)std::get<3>(s);
+            t.next_succ[q].push_back(x);
+        }
+    if (t.same_succ[kTypes - 1].size() != 0) return "inverted pyramid has same-band successors";
+    if ((int)t.next_succ[0].size() != kMaxNextSucc || (int)t.next_succ[1].size() != kMaxNextSucc)
+        return "inverted pyramid does not have 27 next-band successors";
+    for (int S = 0; S < kTypes; ++S)
+        if ((int)t.same_succ[S].size() > kMaxSameSucc) return "too many same-band successors";
+
+    // ---- exact cover of one period cell at every level ----
+    for (int k = 1; k <= H; ++k) {
+        int64_t v = 0;
+        for (int S = 0; S < kTypes; ++S) v += t.active[S][k].volume();
+        if (v != (int64_t)B * B * B) return "regions do not tile the period cell at some level";
+    }
+    return std::string();
+}
+
+PlanStats plan_stats(const TileTables &t, const int n[3])
+{
+    PlanStats s{};
+    int64_t J = 1;
+    for (int d = 0; d < 3; ++d) J *= n[d] / t.B;
+    s.regions_per_band = J * kTypes;
+    int64_t upd = 0, rd = 0, wr = 0;
+    for (int S = 0; S < kTypes; ++S) {
+        upd += t.updates[S];
+        rd += t.bytes_read[S];
+        wr += t.bytes_written[S];
+    }
+    s.updates_per_band = J * upd;
+    s.bytes_read_per_band = J * rd;
+    s.bytes_written_per_band = J * wr;
+    s.bytes_per_update = (double)(rd + wr) / (double)upd;
+    s.bands = 0;
+    return s;
+}
+
+}  // namespace sp

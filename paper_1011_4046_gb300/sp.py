@@ -1,0 +1,269 @@
+"""Python binding of the C ABI in include/sp.h (argument marshalling only).
+
+The functions ``sp_grid_create``, ``sp_region_plan``, ``sp_evolve``,
+``sp_read_surface``, ``sp_write_surface``, ``sp_destroy`` and
+``sp_strerror`` have the names and meaning of the C entry points; every
+site-update they cause runs in the CUDA kernels of ``libsp.so``.  There is no
+Python or CPU compute path: if the library is not built, loading raises.
+
+:class:`Grid` is a convenience wrapper that keeps the handle together with
+the torch tensors (device memory) and stream it was created with.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SP_OK = 0
+SP_EINVAL = -1
+SP_ENOMEM = -2
+SP_ECUDA = -3
+SP_EUNSTABLE = -4
+SP_ETIMEOUT = -5
+SP_ENONFINITE = -6
+SP_EFAULT_INJECTED = -7
+SP_ENOTPLANNED = -8
+
+SP_ASYNC = 1
+SP_MONOLITHIC = 2
+SP_RESTART = 4
+SP_TRACE = 8
+
+SP_SURF_STATE = 0
+SP_SURF_DIAG = 1
+SP_SURF_TRACE = 2
+SP_SURF_WINDING = 3
+SP_SURF_PLAN = 4
+
+SP_ORDER_STATIC = 0
+SP_ORDER_LEARNED = 1
+
+
+class sp_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3),
+        ("dx", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("tau0", ctypes.c_double),
+        ("tau_ref", ctypes.c_double),
+        ("damp_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class sp_diag(ctypes.Structure):
+    _fields_ = [
+        ("level", ctypes.c_int64),
+        ("tau", ctypes.c_double),
+        ("a", ctypes.c_double),
+        ("kinetic", ctypes.c_double),
+        ("gradient", ctypes.c_double),
+        ("potential", ctypes.c_double),
+        ("total", ctypes.c_double),
+        ("pierced", ctypes.c_int64 * 3),
+        ("abs_winding", ctypes.c_int64),
+        ("net_winding", ctypes.c_int64 * 3),
+        ("string_length", ctypes.c_double),
+    ]
+
+
+class sp_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("base_B", ctypes.c_int32),
+        ("threads", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("grid", ctypes.c_int32),
+        ("regions_per_band", ctypes.c_int64),
+        ("updates_per_band", ctypes.c_int64),
+        ("bytes_read_per_band", ctypes.c_int64),
+        ("bytes_written_per_band", ctypes.c_int64),
+        ("bytes_per_update", ctypes.c_double),
+        ("mailbox_bytes", ctypes.c_int64),
+    ]
+
+
+class SpError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {sp_strerror(code)} ({code})" if what else f"{sp_strerror(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+HEADER = os.path.join(_build.ROOT, "include", "sp.h")
+
+
+def declared_entry_points():
+    """Function names declared in include/sp.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(sp_\w+)\s*\(", text, flags=re.M)))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsp.so; raises if it is not built (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() (needs nvcc)")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        lib.sp_grid_create.argtypes = [ctypes.POINTER(sp_params), ctypes.c_int32, ctypes.POINTER(vp), vp,
+                                       ctypes.POINTER(vp)]
+        lib.sp_region_plan.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_char_p]
+        lib.sp_evolve.argtypes = [vp, ctypes.c_int64, ctypes.c_uint32]
+        lib.sp_read_surface.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
+        lib.sp_write_surface.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
+        lib.sp_destroy.argtypes = [vp]
+        lib.sp_strerror.argtypes = [ctypes.c_int]
+        lib.sp_strerror.restype = ctypes.c_char_p
+        for f in ("sp_grid_create", "sp_region_plan", "sp_evolve", "sp_read_surface", "sp_write_surface",
+                  "sp_destroy"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+# ------------------------------------------------------------ C entry points
+def sp_strerror(code: int) -> str:
+    return load().sp_strerror(int(code)).decode()
+
+
+def sp_grid_create(params, state_ptrs=None, stream: int = 0):
+    """params: sequence of sp_params; state_ptrs: None or 3*len(params) device addresses."""
+    n = len(params)
+    arr = (sp_params * n)(*params)
+    ptrs = None
+    if state_ptrs is not None:
+        ptrs = (ctypes.c_void_p * len(state_ptrs))(*[int(p) for p in state_ptrs])
+    h = ctypes.c_void_p()
+    rc = load().sp_grid_create(arr, n, ptrs, ctypes.c_void_p(int(stream)), ctypes.byref(h))
+    return rc, h
+
+
+def sp_region_plan(h, base_B=0, block_shape=0, order=SP_ORDER_STATIC, model_path=None):
+    mp = model_path.encode() if model_path else None
+    return load().sp_region_plan(h, int(base_B), int(block_shape), int(order), mp)
+
+
+def sp_evolve(h, n_steps, flags=0):
+    return load().sp_evolve(h, int(n_steps), int(flags))
+
+
+def sp_read_surface(h, sim, what, dst_ptr, dst_bytes, dst_is_device):
+    return load().sp_read_surface(h, int(sim), int(what), ctypes.c_void_p(int(dst_ptr)), int(dst_bytes),
+                                  int(bool(dst_is_device)))
+
+
+def sp_write_surface(h, sim, what, src_ptr, src_bytes, src_is_device):
+    return load().sp_write_surface(h, int(sim), int(what), ctypes.c_void_p(int(src_ptr)), int(src_bytes),
+                                   int(bool(src_is_device)))
+
+
+def sp_destroy(h):
+    return load().sp_destroy(h)
+
+
+# ------------------------------------------------------------ helpers
+def make_params(n, dx=1.0, dt=0.25, lam=2.0, eta=1.0, nu=0.0, tau0=1.0, tau_ref=1.0, damp_steps=0) -> sp_params:
+    if isinstance(n, int):
+        n = (n, n, n)
+    p = sp_params()
+    p.n[0], p.n[1], p.n[2] = (int(v) for v in n)
+    p.dx, p.dt, p.lam, p.eta, p.nu = float(dx), float(dt), float(lam), float(eta), float(nu)
+    p.tau0, p.tau_ref, p.damp_steps, p.reserved = float(tau0), float(tau_ref), int(damp_steps), 0
+    return p
+
+
+def _check(rc, what):
+    if rc != SP_OK:
+        raise SpError(rc, what)
+
+
+class Grid:
+    """Handle + the torch device tensors (phi, pi, c per simulation) + stream."""
+
+    def __init__(self, params, states=None, stream=None, device="cuda"):
+        import torch
+
+        self.params = list(params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        if states is None:
+            states = []
+            for p in self.params:
+                shape = (p.n[2], p.n[1], p.n[0])
+                states.append(tuple(torch.zeros(shape, dtype=torch.complex64, device=device) for _ in range(3)))
+        self.states = states
+        ptrs = [t.data_ptr() for st in states for t in st]
+        rc, self.h = sp_grid_create(self.params, ptrs, self.stream.cuda_stream)
+        _check(rc, "sp_grid_create")
+
+    def plan(self, base_B=0, threads=0, order=SP_ORDER_STATIC, model_path=None):
+        _check(sp_region_plan(self.h, base_B, threads, order, model_path), "sp_region_plan")
+
+    def evolve(self, n_steps, flags=0):
+        _check(sp_evolve(self.h, n_steps, flags), "sp_evolve")
+
+    def write_state(self, sim, phi, pi, c):
+        buf = np.ascontiguousarray(np.stack([np.asarray(phi), np.asarray(pi), np.asarray(c)]), dtype=np.complex64)
+        _check(sp_write_surface(self.h, sim, SP_SURF_STATE, buf.ctypes.data, buf.nbytes, 0), "sp_write_surface")
+        self.stream.synchronize()
+
+    def read_state(self, sim):
+        p = self.params[sim]
+        out = np.empty((3, p.n[2], p.n[1], p.n[0]), dtype=np.complex64)
+        _check(sp_read_surface(self.h, sim, SP_SURF_STATE, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
+        return out[0], out[1], out[2]
+
+    def diag(self, sim=0) -> dict:
+        d = sp_diag()
+        _check(sp_read_surface(self.h, sim, SP_SURF_DIAG, ctypes.addressof(d), ctypes.sizeof(d), 0),
+               "sp_read_surface")
+        return {f: (list(getattr(d, f)) if f in ("pierced", "net_winding") else getattr(d, f))
+                for f, _ in sp_diag._fields_}
+
+    def winding(self, sim=0):
+        p = self.params[sim]
+        out = np.empty((3, p.n[2], p.n[1], p.n[0]), dtype=np.int8)
+        _check(sp_read_surface(self.h, sim, SP_SURF_WINDING, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
+        return out
+
+    def plan_info(self, sim=0) -> dict:
+        d = sp_plan_info()
+        _check(sp_read_surface(self.h, sim, SP_SURF_PLAN, ctypes.addressof(d), ctypes.sizeof(d), 0),
+               "sp_read_surface")
+        return {f: getattr(d, f) for f, _ in sp_plan_info._fields_}
+
+    def trace(self, sim, n_regions):
+        out = np.empty((n_regions, 2), dtype=np.uint64)
+        _check(sp_read_surface(self.h, sim, SP_SURF_TRACE, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
+        return out
+
+    def close(self):
+        if self.h:
+            sp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,422 @@
+// region_exec.cpp -- TEST-ONLY CPU scaffold for the region planner.
+//
+// Compiled by the tests (never part of libsp.so).  It takes the planner's
+// tables exactly as the GPU kernel does and
+//   * checks on a concrete periodic grid that every (site, level) is computed
+//     by exactly one region, that every read of a region is produced by one
+//     of its predecessors, and that no write can overtake a read it would
+//     clobber (main arrays and the two-slot mailbox ring), by reachability in
+//     the dependency DAG the kernel releases;
+//   * executes the regions one at a time in a seeded random topological
+//     order with the same FP32 site update, so the result can be compared bit
+//     for bit with a whole-grid CPU sweep.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "sp_update.h"
+
+using sp::f2;
+
+namespace {
+
+struct Grid {
+    int n[3], J[3], Jtot, B, H, P, nbands;
+    int64_t sites() const { return (int64_t)n[0] * n[1] * n[2]; }
+    int64_t regions() const { return (int64_t)nbands * 8 * Jtot; }
+    int64_t id(int band, int S, const int j[3]) const
+    {
+        return ((int64_t)band * 8 + S) * Jtot + j[0] + J[0] * (j[1] + J[1] * j[2]);
+    }
+    void decode(int64_t t, int *band, int *S, int j[3]) const
+    {
+        *band = (int)(t / (8 * Jtot));
+        int64_t r = t % (8 * Jtot);
+        *S = (int)(r / Jtot);
+        int jl = (int)(r % Jtot);
+        j[0] = jl % J[0];
+        j[1] = (jl / J[0]) % J[1];
+        j[2] = jl / (J[0] * J[1]);
+    }
+    int64_t site(const int p[3]) const { return p[0] + (int64_t)n[0] * (p[1] + (int64_t)n[1] * p[2]); }
+};
+
+int wrap(int p, int n) { return ((p % n) + n) % n; }
+
+// successors exactly as the kernel releases them
+std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t r)
+{
+    int band, S, j[3];
+    g.decode(r, &band, &S, j);
+    std::vector<int64_t> out;
+    for (const sp::Succ &s : t.same_succ[S]) {
+        int jc[3];
+        for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + s.e[d], g.J[d]);
+        out.push_back(g.id(band, s.type, jc));
+    }
+    if (S == 7 && band + 1 < g.nbands)
+        for (const sp::Succ &s : t.next_succ[(band + 1) & 1]) {
+            int jc[3];
+            for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + s.e[d], g.J[d]);
+            out.push_back(g.id(band + 1, s.type, jc));
+        }
+    return out;
+}
+
+int initial_count(const sp::TileTables &t, int band, int S) { return t.same_preds[S] + (band > 0 ? t.prev_preds[S] : 0); }
+
+// global coordinate of local u along axis d
+int gcoord(const Grid &g, int band, int S, const int j[3], int d, int u)
+{
+    int o = (band & 1) * g.H;
+    return wrap(o + j[d] * g.B + u - (sp::inverted(S, d) ? g.H + 1 : 1), g.n[d]);
+}
+
+bool setup(int B, const int n[3], int nbands, Grid *g, sp::TileTables *t, std::string *err)
+{
+    *err = sp::build_tables(B, t);
+    if (!err->empty()) return false;
+    g->B = B;
+    g->H = B / 2;
+    g->P = B + 2;
+    g->nbands = nbands;
+    g->Jtot = 1;
+    for (int d = 0; d < 3; ++d) {
+        g->n[d] = n[d];
+        if (n[d] % B || n[d] / B < 2) {
+            *err = "grid side not a multiple of B with at least 2 regions";
+            return false;
+        }
+        g->J[d] = n[d] / B;
+        g->Jtot *= g->J[d];
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Structural checks on a concrete grid.  Returns 0 and fills msg on failure.
+int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
+{
+    int n[3] = {nx, ny, nz};
+    Grid g;
+    sp::TileTables t;
+    std::string err;
+    auto fail = [&](const std::string &m) {
+        std::snprintf(msg, msglen, "%s", m.c_str());
+        return 0;
+    };
+    if (!setup(B, n, nbands, &g, &t, &err)) return fail(err);
+    const int64_t R = g.regions(), sites = g.sites();
+
+    // 1) exact cover: every (site, level) computed by exactly one region
+    for (int band = 0; band < nbands; ++band)
+        for (int k = 1; k <= g.H; ++k) {
+            std::vector<int> cover(sites, 0);
+            for (int S = 0; S < 8; ++S)
+                for (int jl = 0; jl < g.Jtot; ++jl) {
+                    int j[3] = {jl % g.J[0], (jl / g.J[0]) % g.J[1], jl / (g.J[0] * g.J[1])};
+                    if (k > t.levels[S]) continue;
+                    const sp::Box3 &A = t.active[S][k];
+                    for (int uz = A.lo[2]; uz < A.hi[2]; ++uz)
+                        for (int uy = A.lo[1]; uy < A.hi[1]; ++uy)
+                            for (int ux = A.lo[0]; ux < A.hi[0]; ++ux) {
+                                int p[3] = {gcoord(g, band, S, j, 0, ux), gcoord(g, band, S, j, 1, uy),
+                                            gcoord(g, band, S, j, 2, uz)};
+                                cover[g.site(p)]++;
+                            }
+                }
+            for (int64_t s = 0; s < sites; ++s)
+                if (cover[s] != 1) return fail("level not covered exactly once");
+        }
+
+    // 2) DAG: counters match the number of releasing predecessors; acyclic
+    std::vector<std::vector<int64_t>> succ(R);
+    std::vector<int> indeg(R, 0);
+    for (int64_t r = 0; r < R; ++r) {
+        succ[r] = successors(t, g, r);
+        for (int64_t s : succ[r]) indeg[s]++;
+    }
+    for (int64_t r = 0; r < R; ++r) {
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        if (indeg[r] != initial_count(t, band, S)) return fail("predecessor count differs from releases");
+    }
+    // reachability (descendants) by DFS from each region
+    std::vector<std::vector<uint8_t>> reach(R, std::vector<uint8_t>(R, 0));
+    for (int64_t r = 0; r < R; ++r) {
+        std::vector<int64_t> stack = succ[r];
+        while (!stack.empty()) {
+            int64_t x = stack.back();
+            stack.pop_back();
+            if (x == r) return fail("cycle in the region DAG");
+            if (reach[r][x]) continue;
+            reach[r][x] = 1;
+            for (int64_t y : succ[x]) stack.push_back(y);
+        }
+    }
+
+    // 3) main-array hazards: the base read at band b must come from the band b-1
+    //    writer (a predecessor) and precede the band-b writer of the same site
+    std::vector<std::vector<int64_t>> top_writer(nbands, std::vector<int64_t>(sites, -1));
+    for (int band = 0; band < nbands; ++band)
+        for (int jl = 0; jl < g.Jtot; ++jl) {
+            int j[3] = {jl % g.J[0], (jl / g.J[0]) % g.J[1], jl / (g.J[0] * g.J[1])};
+            for (int uz = 1; uz <= B; ++uz)
+                for (int uy = 1; uy <= B; ++uy)
+                    for (int ux = 1; ux <= B; ++ux) {
+                        int p[3] = {gcoord(g, band, 7, j, 0, ux), gcoord(g, band, 7, j, 1, uy),
+                                    gcoord(g, band, 7, j, 2, uz)};
+                        if (top_writer[band][g.site(p)] != -1) return fail("two tops write one site");
+                        top_writer[band][g.site(p)] = g.id(band, 7, j);
+                    }
+        }
+    for (int64_t r = 0; r < R; ++r) {
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        const sp::Box3 &bp = t.base_phi[S], &bc = t.base_pc[S];
+        for (int uz = bp.lo[2]; uz < bp.hi[2]; ++uz)
+            for (int uy = bp.lo[1]; uy < bp.hi[1]; ++uy)
+                for (int ux = bp.lo[0]; ux < bp.hi[0]; ++ux) {
+                    int out = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]) +
+                              (uz < bc.lo[2] || uz >= bc.hi[2]);
+                    if (out > 1) continue;
+                    int p[3] = {gcoord(g, band, S, j, 0, ux), gcoord(g, band, S, j, 1, uy),
+                                gcoord(g, band, S, j, 2, uz)};
+                    int64_t s = g.site(p);
+                    if (band > 0) {
+                        int64_t w = top_writer[band - 1][s];
+                        if (w < 0 || !reach[w][r]) return fail("base read not produced by a predecessor");
+                    }
+                    int64_t w2 = top_writer[band][s];
+                    if (w2 < 0) return fail("site without a band top");
+                    if (w2 != r && !reach[r][w2]) return fail("band top may overwrite an unread base");
+                }
+    }
+
+    // 4) mailbox hazards: writer of a mailbox word is a predecessor of its
+    //    reader; writers two bands later (same slot) are its descendants
+    for (int64_t r = 0; r < R; ++r) {
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        for (int L = 1; L < g.H; ++L) {
+            const int *beg = t.exp.empty() ? nullptr : nullptr;
+            (void)beg;
+            for (int i = 0; i < t.exp_n[S][L]; ++i) {
+                const sp::ExportEntry &e = t.exp[t.exp_off[S][L] + i];
+                int jc[3];
+                for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + ((e.code >> (3 + d)) & 1), g.J[d]);
+                const int64_t consumer = g.id(band, e.code & 7, jc);
+                if (!reach[r][consumer]) return fail("mailbox writer is not a predecessor of its reader");
+                if (band >= 2) {
+                    const int64_t old_reader = g.id(band - 2, e.code & 7, jc);
+                    if (!reach[old_reader][r]) return fail("mailbox slot reused before its reader finished");
+                }
+            }
+        }
+    }
+    // 5) every mailbox word that is read has exactly one writer per band
+    for (int Sc = 1; Sc < 8; ++Sc) {
+        std::vector<int> hits(t.mb_size[Sc], 0);
+        for (int Sp = 0; Sp < 8; ++Sp)
+            for (int L = 1; L < g.H; ++L)
+                for (int i = 0; i < t.exp_n[Sp][L]; ++i) {
+                    const sp::ExportEntry &e = t.exp[t.exp_off[Sp][L] + i];
+                    if ((e.code & 7) != Sc) continue;
+                    hits[e.dst_phi]++;
+                    if (e.dst_pc >= 0) {
+                        hits[e.dst_pc]++;
+                        hits[e.dst_pc + 1]++;
+                    }
+                }
+        int64_t used = 0;
+        for (int L = 1; L < g.H; ++L) used += 3LL * t.imp_full_n[Sc][L] + t.imp_phi_n[Sc][L];
+        int64_t written = 0;
+        for (int v : hits) {
+            if (v > 1) return fail("mailbox word written twice");
+            written += v;
+        }
+        if (written != used) return fail("mailbox words read but never written");
+    }
+    return 1;
+}
+
+// Runs nsteps levels (a multiple of H) on FP32 state arrays (float2 as
+// interleaved floats).  mode 0: whole-grid sweep; mode 1: regions in a random
+// topological order drawn from order_seed.  coef holds one LevelCoef per level.
+int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_seed, const float *coef4,
+           float dt, float inv_dx2, float eta2, float *phi, float *pi, float *c, char *msg, int msglen)
+{
+    int n[3] = {nx, ny, nz};
+    Grid g;
+    sp::TileTables t;
+    std::string err;
+    auto fail = [&](const std::string &m) {
+        std::snprintf(msg, msglen, "%s", m.c_str());
+        return 0;
+    };
+    if (nsteps % (B / 2)) return fail("nsteps must be a multiple of B/2");
+    if (!setup(B, n, nsteps / (B / 2), &g, &t, &err)) return fail(err);
+    const sp::LevelCoef *coef = reinterpret_cast<const sp::LevelCoef *>(coef4);
+    sp::PhysConst q{dt, inv_dx2, eta2, 0.0f};
+    f2 *F = reinterpret_cast<f2 *>(phi), *V = reinterpret_cast<f2 *>(pi), *K = reinterpret_cast<f2 *>(c);
+    const int64_t sites = g.sites();
+
+    if (mode == 0) {
+        std::vector<f2> nxt(sites);
+        for (int lvl = 0; lvl < nsteps; ++lvl) {
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        int p[3] = {x, y, z};
+                        auto at = [&](int dx, int dy, int dz) {
+                            int r[3] = {wrap(x + dx, nx), wrap(y + dy, ny), wrap(z + dz, nz)};
+                            return F[g.site(r)];
+                        };
+                        int64_t s = g.site(p);
+                        nxt[s] = sp::site_update(F[s], at(-1, 0, 0), at(1, 0, 0), at(0, -1, 0), at(0, 1, 0),
+                                                 at(0, 0, -1), at(0, 0, 1), V[s], K[s], coef[lvl], q);
+                    }
+            std::memcpy(F, nxt.data(), sites * sizeof(f2));
+        }
+        return 1;
+    }
+
+    // ---- region executor: the kernel's data flow, one region at a time ----
+    const int P = g.P, H = g.H;
+    const int64_t R = g.regions();
+    std::vector<std::vector<f2>> mbox(2);
+    std::vector<int64_t> type_off(8);
+    int64_t slot = 0;
+    for (int S = 0; S < 8; ++S) {
+        type_off[S] = slot;
+        slot += (int64_t)g.Jtot * t.mb_size[S];
+    }
+    for (auto &m : mbox) m.assign(slot, f2{NAN, NAN});
+    std::vector<int> count(R);
+    std::vector<int64_t> ready;
+    for (int64_t r = 0; r < R; ++r) {
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        count[r] = initial_count(t, band, S);
+        if (count[r] == 0) ready.push_back(r);
+    }
+    std::mt19937_64 rng(order_seed);
+    std::vector<f2> buf0(P * P * P), buf1(P * P * P);
+    std::vector<f2> pis(B * B * B), cs(B * B * B);
+    int64_t done = 0;
+    while (!ready.empty()) {
+        size_t pick = (size_t)(rng() % ready.size());
+        int64_t r = ready[pick];
+        ready[pick] = ready.back();
+        ready.pop_back();
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        std::fill(buf0.begin(), buf0.end(), f2{NAN, NAN});
+        std::fill(buf1.begin(), buf1.end(), f2{NAN, NAN});
+        std::fill(pis.begin(), pis.end(), f2{NAN, NAN});
+        std::fill(cs.begin(), cs.end(), f2{NAN, NAN});
+        auto gsite = [&](int ux, int uy, int uz) {
+            int p[3] = {gcoord(g, band, S, j, 0, ux), gcoord(g, band, S, j, 1, uy), gcoord(g, band, S, j, 2, uz)};
+            return g.site(p);
+        };
+        // base
+        const sp::Box3 &bp = t.base_phi[S], &bc = t.base_pc[S];
+        for (int uz = bp.lo[2]; uz < bp.hi[2]; ++uz)
+            for (int uy = bp.lo[1]; uy < bp.hi[1]; ++uy)
+                for (int ux = bp.lo[0]; ux < bp.hi[0]; ++ux) {
+                    int out = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]) +
+                              (uz < bc.lo[2] || uz >= bc.hi[2]);
+                    if (out > 1) continue;
+                    int64_t s = gsite(ux, uy, uz);
+                    buf0[(uz * P + uy) * P + ux] = F[s];
+                    if (out == 0) {
+                        int ci = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+                        pis[ci] = V[s];
+                        cs[ci] = K[s];
+                    }
+                }
+        std::vector<f2> &mb = mbox[band & 1];
+        const int64_t self = type_off[S] + (int64_t)(j[0] + g.J[0] * (j[1] + g.J[1] * j[2])) * t.mb_size[S];
+        for (int k = 1; k <= t.levels[S]; ++k) {
+            std::vector<f2> &prev = (k & 1) ? buf0 : buf1;
+            std::vector<f2> &cur = (k & 1) ? buf1 : buf0;
+            if (k <= H - 1 && S != 0) {
+                const int64_t base = self + t.mb_level_off[S][k];
+                const int nf = t.imp_full_n[S][k], np = t.imp_phi_n[S][k];
+                for (int i = 0; i < nf; ++i) {
+                    int e = t.imp_full[t.imp_full_off[S][k] + i];
+                    pis[e >> 16] = mb[base + 2 * i];
+                    cs[e >> 16] = mb[base + 2 * i + 1];
+                    cur[e & 0xFFFF] = mb[base + 2 * nf + i];
+                }
+                for (int i = 0; i < np; ++i) cur[t.imp_phi[t.imp_phi_off[S][k] + i]] = mb[base + 3 * nf + i];
+            }
+            const sp::Box3 &A = t.active[S][k];
+            const int PP = P * P;
+            for (int uz = A.lo[2]; uz < A.hi[2]; ++uz)
+                for (int uy = A.lo[1]; uy < A.hi[1]; ++uy)
+                    for (int ux = A.lo[0]; ux < A.hi[0]; ++ux) {
+                        int pi_ = (uz * P + uy) * P + ux;
+                        int ci = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+                        cur[pi_] = sp::site_update(prev[pi_], prev[pi_ - 1], prev[pi_ + 1], prev[pi_ - P],
+                                                   prev[pi_ + P], prev[pi_ - PP], prev[pi_ + PP], pis[ci], cs[ci],
+                                                   coef[band * H + k - 1], q);
+                    }
+            if (k <= H - 1)
+                for (int i = 0; i < t.exp_n[S][k]; ++i) {
+                    const sp::ExportEntry &e = t.exp[t.exp_off[S][k] + i];
+                    int jc[3];
+                    for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + ((e.code >> (3 + d)) & 1), g.J[d]);
+                    const int Sc = e.code & 7;
+                    const int64_t dst = type_off[Sc] + (int64_t)(jc[0] + g.J[0] * (jc[1] + g.J[1] * jc[2])) *
+                                                           t.mb_size[Sc];
+                    mb[dst + e.dst_phi] = cur[e.src & 0xFFFF];
+                    if (e.dst_pc >= 0) {
+                        mb[dst + e.dst_pc] = pis[(e.src >> 16) & 0xFFFF];
+                        mb[dst + e.dst_pc + 1] = cs[(e.src >> 16) & 0xFFFF];
+                    }
+                }
+            if (k == H)
+                for (int uz = 1; uz <= B; ++uz)
+                    for (int uy = 1; uy <= B; ++uy)
+                        for (int ux = 1; ux <= B; ++ux) {
+                            int64_t s = gsite(ux, uy, uz);
+                            int ci = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+                            F[s] = cur[(uz * P + uy) * P + ux];
+                            V[s] = pis[ci];
+                            K[s] = cs[ci];
+                        }
+        }
+        for (int64_t s : successors(t, g, r))
+            if (--count[s] == 0) ready.push_back(s);
+        ++done;
+    }
+    if (done != R) return fail("not every region ran");
+    return 1;
+}
+
+// Traffic per update of the design for base B (for the byte-count test).
+double rx_bytes_per_update(int B, int64_t *read_per_band_cell, int64_t *write_per_band_cell, int64_t *upd)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return -1.0;
+    int64_t r = 0, w = 0, u = 0;
+    for (int S = 0; S < 8; ++S) {
+        r += t.bytes_read[S];
+        w += t.bytes_written[S];
+        u += t.updates[S];
+    }
+    *read_per_band_cell = r;
+    *write_per_band_cell = w;
+    *upd = u;
+    return (double)(r + w) / (double)u;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+"""Region planner (host logic, CPU only).
+
+The planner is checked on concrete periodic grids by a test-only C++
+scaffold (tests/cpu_exec/region_exec.cpp) that uses the planner's tables
+exactly as the GPU kernel does:
+
+* exact cover -- every (site, level) is computed by exactly one region;
+* the DAG the kernel releases is acyclic and its counters equal the
+  number of releasing predecessors;
+* hazards -- every base or mailbox read is produced by a predecessor, and
+  nothing overwrites a value (band tops in the main arrays, the two-slot
+  mailbox ring) before every reader of it is done;
+* the regions executed one at a time in random topological orders with the
+  FP32 site update reproduce a whole-grid FP32 sweep bit for bit.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1011_4046_gb300 import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1011_4046_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def rx():
+    out_dir = os.path.join(HERE, "cpu_exec", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "librx.so")
+    srcs = [os.path.join(HERE, "cpu_exec", "region_exec.cpp"), os.path.join(CSRC, "planner.cpp")]
+    if not os.path.exists(lib) or any(os.path.getmtime(s) > os.path.getmtime(lib) for s in
+                                      srcs + [os.path.join(CSRC, "planner.h"), os.path.join(CSRC, "sp_update.h")]):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", f"-I{CSRC}", *srcs,
+                        "-o", tmp], check=True)
+        os.replace(tmp, lib)
+    L = ctypes.CDLL(lib)
+    L.rx_check.argtypes = [ctypes.c_int] * 5 + [ctypes.c_char_p, ctypes.c_int]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.rx_run.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, fp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                              fp, fp, fp, ctypes.c_char_p, ctypes.c_int]
+    L.rx_bytes_per_update.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 3
+    L.rx_bytes_per_update.restype = ctypes.c_double
+    return L
+
+
+@pytest.mark.parametrize("B,n,bands", [(8, (16, 16, 16), 4), (8, (16, 24, 32), 4), (4, (8, 8, 12), 5),
+                                       (6, (12, 18, 12), 4), (16, (32, 32, 32), 3)])
+def test_tiling_dag_and_hazards(rx, B, n, bands):
+    msg = ctypes.create_string_buffer(256)
+    ok = rx.rx_check(B, *n, bands, msg, 256)
+    assert ok == 1, msg.value.decode()
+
+
+def test_traffic_counts_match_the_brute_force_survey_figures(rx):
+    """Read bytes per site-update reproduce the independent brute-force count
+    (25.2 / 13.8 / 7.2 B at B = 8 / 16 / 32).  Writes are higher than a
+    write-once design because a face cell is written into each consumer's
+    mailbox."""
+    got = {}
+    for B in (8, 16, 32):
+        r, w, u = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        total = rx.rx_bytes_per_update(B, ctypes.byref(r), ctypes.byref(w), ctypes.byref(u))
+        assert u.value == (B // 2) * B ** 3  # every cell of one period, every level
+        got[B] = (r.value / u.value, w.value / u.value, total)
+    assert abs(got[8][0] - 25.2) < 0.05 and abs(got[16][0] - 13.8) < 0.05 and abs(got[32][0] - 7.2) < 0.05
+    for B in got:
+        assert abs(got[B][0] + got[B][1] - got[B][2]) < 1e-9
+    assert got[16][2] < got[8][2] and got[32][2] < got[16][2]
+
+
+def _coef_table(levels, nu, dt, lam, tau0, tau_ref):
+    out = np.zeros((levels, 4), dtype=np.float32)
+    for n in range(levels):
+        tau = tau0 + n * dt
+        a = (tau / tau_ref) ** nu
+        d = nu * dt / tau
+        out[n] = ((1 - d) / (1 + d), dt / (1 + d), a * a * lam, 0.0)
+    return out
+
+
+@pytest.mark.parametrize("B,n,steps,seed", [(8, (16, 16, 16), 16, 1), (4, (8, 12, 16), 10, 2),
+                                            (6, (12, 12, 18), 9, 3), (16, (32, 32, 32), 16, 4)])
+def test_region_executor_bit_exact_vs_sweep(rx, B, n, steps, seed):
+    phi0, pi0, c0 = inputs.initial_state(n, seed, "gaussian")
+    pi0 = inputs.gaussian_field(n, seed + 100, sigma=0.2)
+    coef = _coef_table(steps, 2.0, 0.25, 2.0, 10.0, 10.0 + steps * 0.25)
+    fp = ctypes.POINTER(ctypes.c_float)
+
+    def run(mode, order_seed):
+        f, v, c = (np.ascontiguousarray(a, dtype=np.complex64).copy() for a in (phi0, pi0, c0))
+        msg = ctypes.create_string_buffer(256)
+        ok = rx.rx_run(B, *n, steps, mode, order_seed, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
+                       f.view(np.float32).ctypes.data_as(fp), v.view(np.float32).ctypes.data_as(fp),
+                       c.view(np.float32).ctypes.data_as(fp), msg, 256)
+        assert ok == 1, msg.value.decode()
+        return f, v, c
+
+    ref = run(0, 0)
+    assert np.all(np.isfinite(ref[0]))
+    for order_seed in (11, 12, 13):
+        got = run(1, order_seed)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
