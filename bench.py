@@ -1,0 +1,356 @@
+"""Benchmark: lattice site-updates/s of the region-scheduled evolution on one GB300.
+
+Workload (one "step" = one pass of the whole hot path over one batch): the
+128^3 matter-era string field (nu = 2, tau0 = 10, tau_ref = tau0 + 256 dt,
+lambda = 2, eta = 1, dx = 1, dt = 0.25), random-phase initial field from
+seed 0, evolved 256 leapfrog steps in FP32 with the Kahan-compensated drift,
+region base B = 16 (8 steps per band, 32 bands, 131072 regions).  Every step
+starts from the same initial state (restored on the device before the step,
+outside the timed region) and L2 is flushed between steps.
+
+Printed (rank 0, one JSON line): value = site-updates/s from CUDA events on
+the library's stream around each sp_evolve call; the monolithic GPU sweep on
+the same inputs; roofline of the region kernel (algorithmic bytes per
+site-update x updates / kernel time from events around that kernel, against
+the measured HBM copy bandwidth); e2e through the C ABI with host buffers;
+the FP64 CPU oracle timed on the host cores (bounded sample); SM clocks
+sampled with nvidia-smi during the timed region.
+
+--impl reference times the FP64 CPU oracle on the same workload instead
+(bounded sample per step), as the reference arm.
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method needs no collective), value = all ranks' updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, STEPS, B = 128, 256, 16  # the benchmark workload (options below resize it for profiling only)
+NU, TAU0, LAM, ETA, DX, DT = 2.0, 10.0, 2.0, 1.0, 1.0, 0.25
+SEED = 0
+# Algorithmic HBM bytes per site-update of the region path at B = 16: band-top
+# state plus sloped faces, counted by brute force over one steady-state band
+# (13.8 read + 11.4 written, each face cell written once, read by every
+# consumer).
+ALG_BYTES_PER_UPDATE = {8: 42.8, 16: 25.3, 32: 13.8}
+MONO_BYTES_PER_UPDATE = 48.0
+WORKLOAD = (f"{N}^3 matter era (nu=2, tau0=10, tau_ref=74), lambda=2, eta=1, dx=1, dt=0.25, random-phase "
+            f"init seed 0, {STEPS} leapfrog steps, region base B={B}")
+METRIC = "lattice site-updates/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def run_ours(args):
+    import torch
+
+    global N, STEPS, WORKLOAD
+    if args.grid != N or args.leapfrog_steps != STEPS:
+        WORKLOAD = WORKLOAD.replace(f"{N}^3", f"{args.grid}^3").replace(f"{STEPS} leapfrog", f"{args.leapfrog_steps} leapfrog")
+        WORKLOAD = WORKLOAD.replace("tau_ref=74", f"tau_ref={TAU0 + args.leapfrog_steps * DT:g}")
+        N, STEPS = args.grid, args.leapfrog_steps
+
+    from paper_1011_4046_gb300 import inputs, sp
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)  # a capturable stream (the sweep is replayed as a CUDA graph)
+    torch.cuda.set_stream(stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    p = sp.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
+    phi0, pi0, c0 = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
+    host_init = sp.pack_state(phi0, pi0, c0)                    # library state layout, 24 B/site
+    init_dev = torch.from_numpy(host_init).to(dev)              # resident copy to restore from
+    g = sp.Grid([p], stream=stream)
+    g.plan(base_B=args.base, threads=args.threads)
+    info = g.plan_info(0)
+    updates = N ** 3 * STEPS
+    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    init_bytes = init_dev.numel() * 8
+
+    def restore():
+        rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, init_dev.data_ptr(), init_bytes, 1)
+        assert rc == 0, sp.sp_strerror(rc)
+
+    def one_step(flags):
+        restore()
+        flush_l2(l2_flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = sp.sp_evolve(g.h, STEPS, sp.SP_ASYNC | sp.SP_RESTART | sp.SP_TIMING | flags)
+        e1.record(stream)
+        if rc != 0:
+            raise sp.SpError(rc, "sp_evolve")
+        e1.synchronize()
+        kernel = g.timing()
+        return e0.elapsed_time(e1), kernel
+
+    # ---- region path ----
+    for _ in range(args.warmup):
+        one_step(0)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        ms, kt = one_step(0)
+        step_ms.append(ms)
+        kern_ms.append(kt[1])
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * updates * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # correctness guard on the benchmarked result: finite field
+    phi_end = g.read_state(0)[0]
+    finite = bool(np.all(np.isfinite(phi_end)))
+
+    # ---- monolithic sweep on the same inputs (the comparator) ----
+    for _ in range(max(1, args.warmup // 2)):
+        one_step(sp.SP_MONOLITHIC)
+    mono_ms = [one_step(sp.SP_MONOLITHIC)[0] for _ in range(args.steps)]
+    mono_value = updates * args.steps / (sum(mono_ms) / 1e3)
+
+    # ---- e2e through the C ABI with host buffers ----
+    pinned_in = torch.from_numpy(host_init.view(np.float32).copy()).pin_memory()  # phi | (pi, c)
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    nbytes = pinned_in.numel() * 4
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, pinned_in.data_ptr(), nbytes, 0)
+        rc = rc or sp.sp_evolve(g.h, STEPS, sp.SP_ASYNC | sp.SP_RESTART)
+        rc = rc or sp.sp_read_surface(g.h, 0, sp.SP_SURF_STATE, pinned_out.data_ptr(), nbytes, 0)
+        t1 = time.perf_counter()
+        if rc != 0:
+            raise sp.SpError(rc, "e2e")
+        if it >= args.warmup:
+            e2e_ms.append((t1 - t0) * 1e3)
+    e2e_value = ws * updates * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    g.close()
+
+    if rank != 0:
+        return None
+    hbm, peak_kind = peaks()
+    kern_mean = sum(kern_ms) / len(kern_ms)
+    base = info["base_B"]
+    alg_bytes = ALG_BYTES_PER_UPDATE[base] * updates
+    achieved = alg_bytes / (kern_mean / 1e3) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "site-updates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded random-phase field)",
+        "config": {"workload": WORKLOAD if base == B else WORKLOAD.replace(f"B={B}", f"B={base}"), "grid": N,
+                   "leapfrog_steps": STEPS, "region_base": base,
+                   "regions": int(info["regions_per_band"] * (STEPS // (base // 2))),
+                   "threads_per_cta": info["threads"], "ctas": info["grid"],
+                   "l2": "flushed (512 MiB write) before every step; state restored on device outside timing",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "monolithic": {"value": mono_value, "unit": "site-updates/s", "ms_per_step": sum(mono_ms) / len(mono_ms),
+                       "speedup_of_regions": value / ws / mono_value},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "region_kernel", "kernel_ms": kern_mean,
+                     "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
+                     "design_bytes_per_update": info["bytes_per_update"]},
+        "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "field_finite": finite,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return out
+
+
+def cpu_baseline(budget_s, n_steps_cap=STEPS):
+    """The FP64 oracle, as it stands, on the host cores: the same workload,
+    bounded to about budget_s seconds of steps."""
+    import oracle
+    from paper_1011_4046_gb300 import inputs
+
+    oracle.build()
+    p = oracle.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
+    phi0, pi0, _ = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
+    phi = phi0.astype(np.complex128)
+    pi = pi0.astype(np.complex128)
+    done = 0
+    t0 = time.perf_counter()
+    while done < n_steps_cap and (time.perf_counter() - t0) < budget_s:
+        phi, pi = oracle.run(p, phi, pi, done, 1)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": N ** 3 * done / el, "unit": "site-updates/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"first {done} of {STEPS} steps of the {N}^3 workload ({N ** 3 * done:.3g} site-updates, "
+                      f"{el:.1f} s, FP64, OpenMP over z-planes)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1011_4046_gb300 import inputs
+
+    oracle.build()
+    p = oracle.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
+    phi0, pi0, _ = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
+    per_step = max(1, args.ref_levels)
+    times = []
+    phi = phi0.astype(np.complex128)
+    pi = pi0.astype(np.complex128)
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        phi, pi = oracle.run(p, phi0, pi0, 0, per_step)
+        el = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(el)
+    value = N ** 3 * per_step * len(times) / sum(times)
+    sample = (f"each step: the first {per_step} of {STEPS} leapfrog steps of the {N}^3 workload "
+              f"(FP64 oracle, OpenMP over z-planes)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random-phase field)",
+            "config": {"workload": WORKLOAD, "grid": N, "leapfrog_steps": STEPS, "region_base": B},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-levels", type=int, default=4, help="leapfrog steps per reference-arm step")
+    ap.add_argument("--base", type=int, default=B, help="region base (the workload's is 16)")
+    ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
+    ap.add_argument("--grid", type=int, default=N, help="grid side (profiling of smaller cases only)")
+    ap.add_argument("--leapfrog-steps", type=int, default=STEPS, help="steps per run (profiling only)")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -25,8 +25,12 @@
  *     errors (a bounded wait that gave up, a CUDA fault) are reported by the
  *     next call that synchronises (sp_evolve without SP_ASYNC,
  *     sp_read_surface).
- *   - Fields: complex64 arrays (float2: re, im) of n[0]*n[1]*n[2] sites,
- *     x fastest: site index x + n[0] * (y + n[1] * z).
+ *   - State of one simulation, both arrays with site index
+ *     x + n[0] * (y + n[1] * z) (x fastest):
+ *       phi : float2[sites]  (Re phi, Im phi) at level n;
+ *       pic : float4[sites]  (Re pi, Im pi, Re c, Im c): pi = phi' at level
+ *             n - 1/2 and c, the Kahan carry of phi at level n.
+ *     24 bytes per site in all.
  */
 #ifndef SP_H
 #define SP_H
@@ -54,13 +58,16 @@ extern "C" {
 #define SP_MONOLITHIC 2u /* whole-grid sweep, one launch per step (comparator) */
 #define SP_RESTART 4u    /* treat the current state as level 0 (tau = tau0) */
 #define SP_TRACE 8u      /* record (start, end) globaltimer ns of every region (SP_SURF_TRACE) */
+#define SP_TIMING 16u    /* record CUDA events around each launch of the call (SP_SURF_TIMING) */
 
 /* ---- what of sp_read_surface / sp_write_surface ---- */
-#define SP_SURF_STATE 0   /* phi, pi, c of one simulation: 3 * sites * 8 bytes */
+#define SP_SURF_STATE 0   /* phi (sites float2) then pic (sites float4): 24 * sites bytes */
 #define SP_SURF_DIAG 1    /* one sp_diag */
 #define SP_SURF_TRACE 2   /* per-region (start, end) ns of the last region launch */
 #define SP_SURF_WINDING 3 /* int8 plaquette windings [3][sites] */
 #define SP_SURF_PLAN 4    /* one sp_plan_info */
+#define SP_SURF_TIMING 5  /* double[3]: ms of the queue reset, the region kernel and the
+                             remainder sweep of the last SP_TIMING call (events on the stream) */
 
 /* ---- region ordering of sp_region_plan ---- */
 #define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
@@ -110,11 +117,12 @@ typedef struct {
 /*
  * sp_grid_create -- describe n_sims independent simulations.
  *   p         : array of n_sims parameter sets (host memory, copied).
- *   state_dev : NULL, or 3 * n_sims device pointers (phi, pi, c of sim 0, then
- *               sim 1, ...), each n[0]*n[1]*n[2] float2.  The caller keeps
- *               ownership and must keep them alive until sp_destroy.  With
- *               NULL the library allocates zeroed state it frees itself.
- *               Between calls the state holds (phi_n, pi_{n-1/2}, c_n).
+ *   state_dev : NULL, or 2 * n_sims device pointers (phi, pic of sim 0, then
+ *               sim 1, ...): phi float2[sites] (8-byte aligned), pic
+ *               float4[sites] (16-byte aligned).  The caller keeps ownership
+ *               and must keep them alive until sp_destroy.  With NULL the
+ *               library allocates zeroed state it frees itself.  Between
+ *               calls the state holds (phi_n, pi_{n-1/2}, c_n).
  *   cuda_stream : cudaStream_t used for all work (NULL = legacy stream).
  *   out       : receives the handle.
  * Errors: SP_EINVAL (bad parameters), SP_ENOMEM, SP_ECUDA.
@@ -128,7 +136,8 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *   base_B     : region base in cells (8 or 16; B/2 steps per band), or 0 to
  *                pick one per simulation.  Every n[d] must be a multiple of B
  *                with n[d] / B >= 2.
- *   block_shape: threads per CTA (128, 256, 512 or 1024), or 0 for the default.
+ *   block_shape: worker threads per CTA (128, 256, 480, 512 or 768; one
+ *                manager warp is added), or 0 for the default.
  *   order      : SP_ORDER_STATIC or SP_ORDER_LEARNED.
  *   model_path : cost-model weights for SP_ORDER_LEARNED, or NULL.
  * Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA.
@@ -159,7 +168,7 @@ int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size
 
 /*
  * sp_write_surface -- load one simulation's state (what = SP_SURF_STATE:
- * phi, pi, c consecutively, 3 * sites * 8 bytes) from host or device memory.
+ * phi then pic, 24 * sites bytes) from host or device memory.
  * Enqueued on the grid's stream.  Errors: SP_EINVAL, SP_ECUDA.
  */
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device);

@@ -185,6 +185,10 @@ std::string build_tables(int B, TileTables *tp)
                     }
                     if ((Sp & ~S) != 0 || Sp == S) return "import owner type is not a proper subset";
                     if (!in_active(Sp, rp, L, B)) return "import owner does not compute the cell";
+                    // the producer exports level L while it computes level L + 1, which
+                    // rewrites (pi, c) of A(L + 1): a full-state export must lie outside it
+                    if (kind == 0 && in_active(Sp, rp, L + 1, B))
+                        return "full-state export cell is recomputed by the next level";
                     Idx px = index_of(Sp, rp, B);
                     if (px.pc < 0) return "producer cell outside its own box";
                     int ebits = 0;

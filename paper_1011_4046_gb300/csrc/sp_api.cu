@@ -24,10 +24,10 @@ namespace {
 
 struct TablesOnDevice {
     sp::TileTables host;
-    sp::TablesDev *d_struct = nullptr;
-    int *d_imp_full = nullptr;
-    int *d_imp_phi = nullptr;
-    int4 *d_exp = nullptr;
+    sp::TablesDev dev;  // host copy of the device descriptor
+    int index = 0;      // position in the launch's table array
+    unsigned short *d_imp = nullptr;
+    int2 *d_exp = nullptr;
 };
 
 struct SweepGraph {
@@ -35,6 +35,7 @@ struct SweepGraph {
     int sim = -1;
     int64_t steps = -1, first_local = -1;
     const void *coef = nullptr;
+    const void *phi = nullptr, *tmp = nullptr;
 };
 
 template <class T>
@@ -108,7 +109,8 @@ int64_t sites_of(const sp_params &p) { return (int64_t)p.n[0] * p.n[1] * p.n[2];
 struct sp_grid {
     int n_sims = 0;
     std::vector<sp_params> p;
-    std::vector<float2 *> phi, pi, c;
+    std::vector<float2 *> phi;
+    std::vector<float4 *> pc;  // (pi, c) interleaved
     bool owns_state = false;
     cudaStream_t stream = nullptr;
     int device = 0, sm_count = 0;
@@ -116,8 +118,12 @@ struct sp_grid {
     // plan
     bool planned = false;
     int threads = 0, max_B = 0, ctas_per_sm = 0, grid = 0, order = 0;
+    size_t smem = 0;
     std::vector<int> B;
     std::map<int, TablesOnDevice> tables;
+    sp::TablesDev *d_tabs = nullptr;
+    int n_tabs = 0;
+    int imp_smem_units = 0;  // 16-bit import entries of all tables
     std::vector<float2 *> mbox;
     std::vector<long long> mb_slot;
     std::vector<std::array<long long, sp::kTypes>> mb_type_off;
@@ -147,6 +153,10 @@ struct sp_grid {
     std::vector<sp::LevelCoef> up_coef;
     std::vector<sp::SimDev> up_sims;
     unsigned long long up_limit = 0;
+    // CUDA events of the last SP_TIMING call: before reset, before region
+    // kernel, after region kernel, after the remainder sweep
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
 };
 
 namespace {
@@ -163,6 +173,22 @@ int check_params(const sp_params &p)
     return SP_OK;
 }
 
+// The kernel splits a linear index i < w0 w1 w2 into (x, y, z) with
+// sp::fdiv and FP32 reciprocals; check every quotient it will form.
+bool decode_exact(const sp::Box3 *boxes, int last, const float (*rcp)[2])
+{
+    for (int k = 0; k <= last; ++k) {
+        const sp::Box3 &b = boxes[k];
+        const int w0 = b.hi[0] - b.lo[0], w1 = b.hi[1] - b.lo[1], w2 = b.hi[2] - b.lo[2];
+        if (w0 <= 0 || w1 <= 0 || w2 <= 0) continue;
+        for (int i = 0; i < w0 * w1 * w2; ++i) {
+            const int t1 = sp::fdiv(i, rcp[k][0]);
+            if (t1 != i / w0 || sp::fdiv(t1, rcp[k][1]) != t1 / w1) return false;
+        }
+    }
+    return true;
+}
+
 int build_device_tables(sp_grid *g, int B)
 {
     if (g->tables.count(B)) return SP_OK;
@@ -170,66 +196,132 @@ int build_device_tables(sp_grid *g, int B)
     std::string err = sp::build_tables(B, &td.host);
     if (!err.empty()) return SP_EINVAL;
     const sp::TileTables &t = td.host;
-    sp::TablesDev h;
+    sp::TablesDev &h = td.dev;
     std::memset(&h, 0, sizeof h);
     h.B = t.B;
     h.H = t.H;
     h.P = t.P;
     for (int S = 0; S < sp::kTypes; ++S) {
-        h.levels[S] = t.levels[S];
-        for (int k = 0; k <= sp::kMaxH; ++k) h.active[S][k] = t.active[S][k];
-        h.base_phi[S] = t.base_phi[S];
-        h.base_pc[S] = t.base_pc[S];
+        sp::TypeMeta &m = h.type[S];
+        m.levels = t.levels[S];
+        m.mb_size = t.mb_size[S];
+        m.n_same_succ = (int)t.same_succ[S].size();
+        m.same_preds = t.same_preds[S];
+        m.prev_preds = t.prev_preds[S];
+        for (int k = 0; k <= sp::kMaxH; ++k) m.active[k] = t.active[S][k];
+        m.base_phi = t.base_phi[S];
+        m.base_pc = t.base_pc[S];
+        for (int k = 0; k <= sp::kMaxH; ++k)
+            for (int d = 0; d < 2; ++d) {
+                int w = t.active[S][k].hi[d] - t.active[S][k].lo[d];
+                m.rcp_active[k][d] = w > 0 ? 1.0f / (float)w : 0.0f;
+            }
+        for (int d = 0; d < 2; ++d) m.rcp_base[d] = 1.0f / (float)(t.base_phi[S].hi[d] - t.base_phi[S].lo[d]);
+        if (!decode_exact(m.active, t.H, m.rcp_active) || !decode_exact(&m.base_phi, 0, &m.rcp_base))
+            return SP_EINVAL;
         for (int L = 0; L < sp::kMaxH; ++L) {
-            h.imp_full_off[S][L] = t.imp_full_off[S][L];
-            h.imp_full_n[S][L] = t.imp_full_n[S][L];
-            h.imp_phi_off[S][L] = t.imp_phi_off[S][L];
-            h.imp_phi_n[S][L] = t.imp_phi_n[S][L];
-            h.mb_level_off[S][L] = t.mb_level_off[S][L];
-            h.exp_off[S][L] = t.exp_off[S][L];
-            h.exp_n[S][L] = t.exp_n[S][L];
+            m.mb_level_off[L] = t.mb_level_off[S][L];
+            m.exp_off[L] = t.exp_off[S][L];
+            m.exp_n[L] = t.exp_n[S][L];
+            m.imp_full_n[L] = t.imp_full_n[S][L];
+            m.imp_phi_n[L] = t.imp_phi_n[S][L];
         }
-        h.mb_size[S] = t.mb_size[S];
-        h.same_preds[S] = t.same_preds[S];
-        h.prev_preds[S] = t.prev_preds[S];
-        h.n_same_succ[S] = (int)t.same_succ[S].size();
-        for (size_t i = 0; i < t.same_succ[S].size(); ++i) h.same_succ[S][i] = t.same_succ[S][i];
+        for (size_t i = 0; i < t.same_succ[S].size(); ++i) m.same_succ[i] = t.same_succ[S][i];
     }
     for (int q = 0; q < 2; ++q)
         for (size_t i = 0; i < t.next_succ[q].size(); ++i) h.next_succ[q][i] = t.next_succ[q][i];
+    // compact device tables (see sp_device.cuh for the packing)
+    if (t.P * t.P * t.P > 8192 || t.B * t.B * t.B > 4096) return SP_EINVAL;
+    std::vector<unsigned short> imp;
+    for (int S = 0; S < sp::kTypes; ++S)
+        for (int L = 0; L < sp::kMaxH; ++L) {
+            sp::TypeMeta &m = h.type[S];
+            m.imp_full_off[L] = (int)imp.size();
+            for (int i = 0; i < t.imp_full_n[S][L]; ++i)
+                imp.push_back((unsigned short)(t.imp_full[t.imp_full_off[S][L] + i] >> 16));  // (pi, c) index
+            m.imp_phi_off[L] = (int)imp.size();
+            for (int i = 0; i < t.imp_phi_n[S][L]; ++i) imp.push_back((unsigned short)t.imp_phi[t.imp_phi_off[S][L] + i]);
+        }
+    while (imp.size() % 8) imp.push_back(0);
+    h.imp_n = (int)imp.size();
+    h.rcp_B = 1.0f / (float)t.B;
+    std::vector<int2> ex(t.exp.size());
+    for (size_t i = 0; i < t.exp.size(); ++i) {
+        const sp::ExportEntry &e = t.exp[i];
+        const int phi = e.src & 0xFFFF, pc = (e.src >> 16) & 0xFFFF;
+        const int has_pc = e.dst_pc >= 0;
+        ex[i].x = (int)((unsigned)phi | ((unsigned)(has_pc ? pc : 0) << 13) | ((unsigned)e.code << 25) |
+                        ((unsigned)has_pc << 31));
+        ex[i].y = e.dst_phi;
+    }
+    // the kernel re-derives the (pi, c) destination and the phi index of a
+    // full import: check both derivations against the planner's tables
+    for (int S = 0; S < sp::kTypes; ++S)
+        for (int L = 1; L < t.H; ++L)
+            for (int i = 0; i < t.exp_n[S][L]; ++i) {
+                const sp::ExportEntry &e = t.exp[t.exp_off[S][L] + i];
+                if (e.dst_pc < 0) continue;
+                const int Sc = e.code & 7;
+                const int off = t.mb_level_off[Sc][L], nf = t.imp_full_n[Sc][L];
+                if (off + 2 * (e.dst_phi - off - 2 * nf) != e.dst_pc) return SP_EINVAL;
+            }
+    for (size_t i = 0; i < t.imp_full.size(); ++i) {
+        const int c = t.imp_full[i] >> 16, want = t.imp_full[i] & 0xFFFF;
+        const int t1 = sp::fdiv(c, h.rcp_B), t2 = sp::fdiv(t1, h.rcp_B);
+        const int ux = c - t1 * t.B + 1, uy = t1 - t2 * t.B + 1, uz = t2 + 1;
+        if ((uz * t.P + uy) * t.P + ux != want) return SP_EINVAL;
+    }
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {
         if (e != cudaSuccess) return;
         e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
         if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     };
-    up((void **)&td.d_imp_full, t.imp_full.data(), t.imp_full.size() * sizeof(int));
-    up((void **)&td.d_imp_phi, t.imp_phi.data(), t.imp_phi.size() * sizeof(int));
-    up((void **)&td.d_exp, t.exp.data(), t.exp.size() * sizeof(sp::ExportEntry));
-    h.imp_full = td.d_imp_full;
-    h.imp_phi = td.d_imp_phi;
+    up((void **)&td.d_imp, imp.data(), imp.size() * sizeof(unsigned short));
+    up((void **)&td.d_exp, ex.data(), ex.size() * sizeof(int2));
+    h.imp = td.d_imp;
     h.exp = td.d_exp;
-    up((void **)&td.d_struct, &h, sizeof h);
     if (e != cudaSuccess) {
-        cudaFree(td.d_imp_full);
-        cudaFree(td.d_imp_phi);
+        cudaFree(td.d_imp);
         cudaFree(td.d_exp);
-        cudaFree(td.d_struct);
         return e == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA;
     }
     g->tables[B] = td;
     return SP_OK;
 }
 
+// One contiguous device array of every table the plan uses; SimDev::tab_index
+// picks the entry (the region kernel copies the array into shared memory).
+int upload_table_array(sp_grid *g)
+{
+    std::vector<sp::TablesDev> arr;
+    int idx = 0, imp_smem = 0;
+    for (auto &kv : g->tables) {
+        kv.second.index = idx++;
+        kv.second.dev.imp_smem = imp_smem;
+        imp_smem += kv.second.dev.imp_n;
+        arr.push_back(kv.second.dev);
+    }
+    g->imp_smem_units = imp_smem;
+    cudaFree(g->d_tabs);
+    g->d_tabs = nullptr;
+    cudaError_t e = cudaMalloc((void **)&g->d_tabs, arr.size() * sizeof(sp::TablesDev));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_tabs, arr.data(), arr.size() * sizeof(sp::TablesDev), cudaMemcpyHostToDevice);
+    g->n_tabs = (int)arr.size();
+    return e == cudaSuccess ? SP_OK : SP_ENOMEM;
+}
+
 void free_plan(sp_grid *g)
 {
     for (auto &kv : g->tables) {
-        cudaFree(kv.second.d_imp_full);
-        cudaFree(kv.second.d_imp_phi);
+        cudaFree(kv.second.d_imp);
         cudaFree(kv.second.d_exp);
-        cudaFree(kv.second.d_struct);
     }
     g->tables.clear();
+    cudaFree(g->d_tabs);
+    g->d_tabs = nullptr;
+    g->n_tabs = 0;
     for (float2 *m : g->mbox) cudaFree(m);
     g->mbox.clear();
     g->planned = false;
@@ -248,7 +340,7 @@ int choose_B(const sp_params &p, int requested)
     return -1;
 }
 
-int default_threads(int B) { return B <= 8 ? 128 : 512; }
+int default_threads(int B) { return B <= 8 ? 128 : 256; }
 
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
@@ -262,25 +354,61 @@ int collect_device_error(sp_grid *g)
     return SP_OK;
 }
 
+int enqueue_sweep(sp_grid *g, int s, int64_t nsteps, int64_t first_local, const sp::LevelCoef *d_coef_sim)
+{
+    const sp_params &p = g->p[s];
+    const int64_t sites = sites_of(p);
+    const sp::PhysConst q = phys_const(p);
+    float2 *a = g->phi[s], *b = g->d_tmp;
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        e = sp::launch_sweep(a, b, g->pc[s], p.n, d_coef_sim, (int)(first_local + k), q, g->stream);
+        std::swap(a, b);
+    }
+    if (e == cudaSuccess && a != g->phi[s])
+        e = cudaMemcpyAsync(g->phi[s], a, sites * sizeof(float2), cudaMemcpyDeviceToDevice, g->stream);
+    return e == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+// nsteps whole-grid steps of simulation s.  On a capturable stream the steps
+// are recorded once into a CUDA graph (one node per step) and replayed while
+// the call repeats with the same buffers and coefficients, which removes the
+// per-launch gaps of the plain loop.
 int sweep_steps(sp_grid *g, int s, int64_t nsteps, int64_t first_local, const sp::LevelCoef *d_coef_sim)
 {
     if (nsteps <= 0) return SP_OK;
-    const sp_params &p = g->p[s];
-    const int64_t sites = sites_of(p);
+    const int64_t sites = sites_of(g->p[s]);
     cudaError_t e = grow(&g->d_tmp, &g->cap_tmp, (size_t)sites);
     if (e != cudaSuccess) return SP_ENOMEM;
-    const sp::PhysConst q = phys_const(p);
-    float2 *a = g->phi[s], *b = g->d_tmp;
-    for (int64_t k = 0; k < nsteps; ++k) {
-        e = sp::launch_sweep(a, b, g->pi[s], g->c[s], p.n, d_coef_sim, (int)(first_local + k), q, g->stream);
+    if (g->stream == nullptr) return enqueue_sweep(g, s, nsteps, first_local, d_coef_sim);
+    SweepGraph &sg = g->sweep_graph;
+    if (!(sg.exec && sg.sim == s && sg.steps == nsteps && sg.first_local == first_local && sg.coef == d_coef_sim &&
+          sg.phi == g->phi[s] && sg.tmp == g->d_tmp)) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return SP_ECUDA;
-        std::swap(a, b);
+        int rc = enqueue_sweep(g, s, nsteps, first_local, d_coef_sim);
+        e = cudaStreamEndCapture(g->stream, &graph);
+        if (rc != SP_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return SP_ECUDA;
+        }
+        e = cudaGraphInstantiate(&sg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            sg.exec = nullptr;
+            return SP_ECUDA;
+        }
+        sg.sim = s;
+        sg.steps = nsteps;
+        sg.first_local = first_local;
+        sg.coef = d_coef_sim;
+        sg.phi = g->phi[s];
+        sg.tmp = g->d_tmp;
     }
-    if (a != g->phi[s]) {
-        e = cudaMemcpyAsync(g->phi[s], a, sites * sizeof(float2), cudaMemcpyDeviceToDevice, g->stream);
-        if (e != cudaSuccess) return SP_ECUDA;
-    }
-    return SP_OK;
+    return cudaGraphLaunch(sg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
 }  // namespace
@@ -333,25 +461,25 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
     }
     g->owns_state = state_dev == nullptr;
     for (int s = 0; s < n_sims; ++s) {
-        float2 *f[3] = {nullptr, nullptr, nullptr};
+        void *f[2] = {nullptr, nullptr};
+        const size_t unit[2] = {sizeof(float2), sizeof(float4)};
         if (state_dev) {
-            for (int k = 0; k < 3; ++k) {
-                f[k] = (float2 *)state_dev[3 * s + k];
-                if (!f[k] || ((uintptr_t)f[k] & 7u)) {
+            for (int k = 0; k < 2; ++k) {
+                f[k] = state_dev[2 * s + k];
+                if (!f[k] || ((uintptr_t)f[k] & (unit[k] - 1))) {
                     delete g;
                     return SP_EINVAL;
                 }
             }
         } else {
-            const size_t bytes = (size_t)sites_of(p[s]) * sizeof(float2);
-            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-                e = cudaMalloc((void **)&f[k], bytes);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                const size_t bytes = (size_t)sites_of(p[s]) * unit[k];
+                e = cudaMalloc(&f[k], bytes);
                 if (e == cudaSuccess) e = cudaMemsetAsync(f[k], 0, bytes, g->stream);
             }
         }
-        g->phi.push_back(f[0]);
-        g->pi.push_back(f[1]);
-        g->c.push_back(f[2]);
+        g->phi.push_back((float2 *)f[0]);
+        g->pc.push_back((float4 *)f[1]);
         if (e != cudaSuccess) {
             sp_destroy(g);
             return SP_ENOMEM;
@@ -374,7 +502,8 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
     (void)model_path;
     if (!g) return SP_EINVAL;
     if (base_B != 0 && (base_B % 2 != 0 || base_B < 4 || base_B > 16)) return SP_EINVAL;
-    if (block_shape != 0 && block_shape != 128 && block_shape != 256 && block_shape != 512 && block_shape != 1024)
+    if (block_shape != 0 && block_shape != 128 && block_shape != 256 && block_shape != 480 && block_shape != 512 &&
+        block_shape != 768)
         return SP_EINVAL;
     if (order != SP_ORDER_STATIC && order != SP_ORDER_LEARNED) return SP_EINVAL;
     free_plan(g);
@@ -388,9 +517,12 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
         int rc = build_device_tables(g, B);
         if (rc != SP_OK) return rc;
     }
+    int rct = upload_table_array(g);
+    if (rct != SP_OK) return rct;
     g->threads = block_shape ? block_shape : default_threads(g->max_B);
-    if (sp::region_smem_bytes(g->max_B) > 227 * 1024) return SP_EINVAL;
-    cudaError_t e = sp::region_occupancy(g->threads, g->max_B, &g->ctas_per_sm);
+    g->smem = sp::region_smem_bytes(g->max_B, g->n_tabs, g->n_sims, g->imp_smem_units);
+    if (g->smem > 227 * 1024) return SP_EINVAL;
+    cudaError_t e = sp::region_occupancy(g->threads, g->smem, &g->ctas_per_sm);
     if (e != cudaSuccess || g->ctas_per_sm < 1) return SP_EINVAL;
     g->grid = g->ctas_per_sm * g->sm_count;
     g->order = order;
@@ -422,7 +554,12 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
 {
     if (!g || n_steps < 0) return SP_EINVAL;
-    if (flags & ~(SP_ASYNC | SP_MONOLITHIC | SP_RESTART | SP_TRACE)) return SP_EINVAL;
+    if (flags & ~(SP_ASYNC | SP_MONOLITHIC | SP_RESTART | SP_TRACE | SP_TIMING)) return SP_EINVAL;
+    const bool timing = (flags & SP_TIMING) != 0;
+    if (timing && !g->ev[0])
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&g->ev[i]) != cudaSuccess) return SP_ECUDA;
+    g->timed = false;
     if (flags & SP_RESTART) std::fill(g->level.begin(), g->level.end(), 0);
     if (n_steps == 0) return SP_OK;
     const bool mono = (flags & SP_MONOLITHIC) != 0;
@@ -447,6 +584,12 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
     }
 
     int rc = SP_OK;
+    if (timing) {
+        e = cudaEventRecord(g->ev[0], g->stream);
+        if (e == cudaSuccess && mono) e = cudaEventRecord(g->ev[1], g->stream);
+        if (e == cudaSuccess && mono) e = cudaEventRecord(g->ev[2], g->stream);
+        if (e != cudaSuccess) return SP_ECUDA;
+    }
     if (mono) {
         for (int s = 0; s < g->n_sims && rc == SP_OK; ++s)
             rc = sweep_steps(g, s, n_steps, 0, g->d_coef + (size_t)s * n_steps);
@@ -481,12 +624,12 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             d.coef = g->d_coef + (size_t)s * n_steps;
             d.q = phys_const(g->p[s]);
             d.phi = g->phi[s];
-            d.pi = g->pi[s];
-            d.c = g->c[s];
+            d.pc = g->pc[s];
             d.mbox = g->mbox[s];
             d.mb_slot = g->mb_slot[s];
             for (int S = 0; S < sp::kTypes; ++S) d.mb_type_off[S] = g->mb_type_off[s][S];
-            d.tab = td.d_struct;
+            d.tab = g->d_tabs + td.index;
+            d.tab_index = td.index;
             g->last_tile_base[s] = total;
             g->last_tiles[s] = d.tiles;
             total += d.tiles;
@@ -516,6 +659,8 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             }
             sp::RegionArgs a;
             a.sims = g->d_sims;
+            a.tabs = g->d_tabs;
+            a.n_tabs = g->n_tabs;
             a.n_sims = (int)sims.size();
             a.total = total;
             a.n_seed = seeds;
@@ -525,7 +670,13 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             a.trace = trace ? g->d_trace : nullptr;
             g->last_traced = trace;
             e = sp::launch_reset(a, g->stream);
-            if (e == cudaSuccess) e = sp::launch_region(a, g->threads, g->max_B, g->grid, g->stream);
+            if (e == cudaSuccess && timing) e = cudaEventRecord(g->ev[1], g->stream);
+            if (e == cudaSuccess) e = sp::launch_region(a, g->threads, g->max_B, g->smem, g->grid, g->stream);
+            if (e == cudaSuccess && timing) e = cudaEventRecord(g->ev[2], g->stream);
+            if (e != cudaSuccess) return SP_ECUDA;
+        } else if (timing) {
+            e = cudaEventRecord(g->ev[1], g->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(g->ev[2], g->stream);
             if (e != cudaSuccess) return SP_ECUDA;
         }
         // remainder steps of each simulation: whole-grid steps, same arithmetic
@@ -536,6 +687,11 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
         }
     }
     if (rc != SP_OK) return rc;
+    if (timing) {
+        e = cudaEventRecord(g->ev[3], g->stream);
+        if (e != cudaSuccess) return SP_ECUDA;
+        g->timed = true;
+    }
     for (int s = 0; s < g->n_sims; ++s) g->level[s] += n_steps;
     if (flags & SP_ASYNC) return SP_OK;
     e = cudaStreamSynchronize(g->stream);
@@ -547,13 +703,12 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device)
 {
     if (!g || sim < 0 || sim >= g->n_sims || !src || what != SP_SURF_STATE) return SP_EINVAL;
-    const size_t bytes = (size_t)sites_of(g->p[sim]) * sizeof(float2);
-    if (src_bytes < 3 * bytes) return SP_EINVAL;
+    const size_t sites = (size_t)sites_of(g->p[sim]);
+    if (src_bytes < 24 * sites) return SP_EINVAL;
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const char *b = (const char *)src;
-    cudaError_t e = cudaMemcpyAsync(g->phi[sim], b, bytes, kind, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->pi[sim], b + bytes, bytes, kind, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->c[sim], b + 2 * bytes, bytes, kind, g->stream);
+    cudaError_t e = cudaMemcpyAsync(g->phi[sim], b, 8 * sites, kind, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->pc[sim], b + 8 * sites, 16 * sites, kind, g->stream);
     return cuda_err(e);
 }
 
@@ -571,12 +726,10 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
     }
     switch (what) {
     case SP_SURF_STATE: {
-        const size_t bytes = (size_t)sites * sizeof(float2);
-        if (dst_bytes < 3 * bytes) return SP_EINVAL;
+        if (dst_bytes < (size_t)(24 * sites)) return SP_EINVAL;
         char *b = (char *)dst;
-        e = cudaMemcpyAsync(b, g->phi[sim], bytes, to, g->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b + bytes, g->pi[sim], bytes, to, g->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b + 2 * bytes, g->c[sim], bytes, to, g->stream);
+        e = cudaMemcpyAsync(b, g->phi[sim], 8 * (size_t)sites, to, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + 8 * (size_t)sites, g->pc[sim], 16 * (size_t)sites, to, g->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
         return cuda_err(e);
     }
@@ -604,7 +757,7 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         if (e != cudaSuccess) return SP_ENOMEM;
         double tau, a, d;
         level_physics(p, g->level[sim], &tau, &a, &d);
-        e = sp::launch_energy(g->phi[sim], g->pi[sim], p.n, 1.0 / (p.dx * p.dx), p.eta * p.eta,
+        e = sp::launch_energy(g->phi[sim], g->pc[sim], p.n, 1.0 / (p.dx * p.dx), p.eta * p.eta,
                               0.5 * p.lambda * a * a, g->d_epart, g->d_eout, g->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g->d_wcount, 0, 8 * sizeof(unsigned long long), g->stream);
         if (e == cudaSuccess) e = sp::launch_winding(g->phi[sim], p.n, nullptr, g->d_wcount, g->stream);
@@ -653,6 +806,16 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         else std::memcpy(dst, &info, sizeof info);
         return cuda_err(e);
     }
+    case SP_SURF_TIMING: {
+        if (!g->timed || dst_bytes < 3 * sizeof(double) || dst_is_device) return SP_EINVAL;
+        e = cudaEventSynchronize(g->ev[3]);
+        float ms[3] = {0, 0, 0};
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], g->ev[i], g->ev[i + 1]);
+        if (e != cudaSuccess) return SP_ECUDA;
+        double *o = (double *)dst;
+        for (int i = 0; i < 3; ++i) o[i] = ms[i];
+        return SP_OK;
+    }
     case SP_SURF_TRACE: {
         if (!g->last_traced || sim >= (int)g->last_tiles.size()) return SP_EINVAL;
         const size_t n = 2 * (size_t)g->last_tiles[sim];
@@ -672,12 +835,10 @@ int sp_destroy(sp_grid *g)
     if (!g) return SP_EINVAL;
     cudaStreamSynchronize(g->stream);
     free_plan(g);
-    if (g->owns_state)
-        for (int s = 0; s < (int)g->phi.size(); ++s) {
-            cudaFree(g->phi[s]);
-            cudaFree(g->pi[s]);
-            cudaFree(g->c[s]);
-        }
+    if (g->owns_state) {
+        for (float2 *f : g->phi) cudaFree(f);
+        for (float4 *f : g->pc) cudaFree(f);
+    }
     cudaFree(g->d_counters);
     cudaFree(g->d_queue);
     cudaFree(g->d_ctl);
@@ -690,6 +851,8 @@ int sp_destroy(sp_grid *g)
     cudaFree(g->d_wcount);
     cudaFree(g->d_wind);
     if (g->sweep_graph.exec) cudaGraphExecDestroy(g->sweep_graph.exec);
+    for (int i = 0; i < 4; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     delete g;
     return SP_OK;
 }

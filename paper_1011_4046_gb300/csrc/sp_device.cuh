@@ -9,28 +9,50 @@
 
 namespace sp {
 
+// Per-type geometry and routing of one base size (one block per region type,
+// so a kernel can keep it in shared memory).
+struct alignas(16) TypeMeta {
+    int levels, mb_size, n_same_succ, same_preds;
+    int prev_preds, pad0, pad1, pad2;
+    Box3 active[kMaxH + 1];
+    Box3 base_phi, base_pc;
+    // 1/w of the two inner extents of each box, rounded to FP32 (exact
+    // quotient decode, see fdiv below)
+    float rcp_active[kMaxH + 1][2];
+    float rcp_base[2];
+    int imp_full_off[kMaxH], imp_full_n[kMaxH];
+    int imp_phi_off[kMaxH], imp_phi_n[kMaxH];
+    int mb_level_off[kMaxH];
+    int exp_off[kMaxH], exp_n[kMaxH];
+    Succ same_succ[kMaxSameSucc];
+    int pad3[2];
+};
+
 // Geometry and surface-routing tables for one base size, in device memory.
-struct TablesDev {
+//
+// Import lists are 16-bit: a full-state import holds the cell's (pi, c) index
+// (its phi index follows from it), a neighbour-only import its phi index.
+// All lists of one base size are copied into shared memory once per launch,
+// at imp_smem (16-bit units) in the kernel's import area.
+//
+// Export entries are 8 bytes: x = phi index (13 bits) | (pi, c) index << 13
+// (12 bits) | consumer code << 25 (6 bits) | has (pi, c) << 31, y = phi offset
+// in the consumer's mailbox; the (pi, c) offset follows from the consumer's
+// level layout.  This packing needs (B+2)^3 <= 8192 and B^3 <= 4096 (B <= 16).
+struct alignas(16) TablesDev {
     int B, H, P, pad;
-    int levels[kTypes];
-    Box3 active[kTypes][kMaxH + 1];
-    Box3 base_phi[kTypes], base_pc[kTypes];
-    int imp_full_off[kTypes][kMaxH], imp_full_n[kTypes][kMaxH];
-    int imp_phi_off[kTypes][kMaxH], imp_phi_n[kTypes][kMaxH];
-    int mb_level_off[kTypes][kMaxH];
-    int mb_size[kTypes];
-    int exp_off[kTypes][kMaxH], exp_n[kTypes][kMaxH];
-    int same_preds[kTypes], prev_preds[kTypes];
-    int n_same_succ[kTypes];
-    Succ same_succ[kTypes][kMaxSameSucc];
+    TypeMeta type[kTypes];
     Succ next_succ[2][kMaxNextSucc];
-    const int *imp_full;
-    const int *imp_phi;
-    const int4 *exp;
+    int imp_n;      // 16-bit import entries of this base size (padded to 8)
+    int imp_smem;   // their offset in the shared import area (16-bit units)
+    float rcp_B;    // 1/B in FP32 (exact quotient decode)
+    int pad2;
+    const unsigned short *imp;  // all import lists, global memory
+    const int2 *exp;            // all export entries, global memory
 };
 
 // One simulation of a batch, as the persistent region kernel sees it.
-struct SimDev {
+struct alignas(16) SimDev {
     int n[3];
     int J[3];
     int Jtot;
@@ -41,11 +63,14 @@ struct SimDev {
     unsigned seed_base;   // queue position of this sim's first ready region
     const LevelCoef *coef;  // coef[l] = coefficients of the l-th level of this call
     PhysConst q;
-    float2 *phi, *pi, *c;   // caller-owned state, x fastest
+    float2 *phi;            // caller-owned state, x fastest: phi
+    float4 *pc;             // and (pi.re, pi.im, c.re, c.im)
     float2 *mbox;           // mailbox ring (2 band slots)
     long long mb_slot;      // float2 elements per band slot
     long long mb_type_off[kTypes];
     const TablesDev *tab;
+    int tab_index;  // which of the launch's tables (RegionArgs::tabs) this is
+    int pad;
 };
 
 // Work-queue control block.
@@ -61,6 +86,8 @@ struct Ctl {
 
 struct RegionArgs {
     const SimDev *sims;
+    const TablesDev *tabs;  // the distinct tables of the launch, tabs[SimDev::tab_index]
+    int n_tabs;
     int n_sims;
     unsigned total;  // regions in this launch
     unsigned n_seed; // regions ready at the start
@@ -69,6 +96,10 @@ struct RegionArgs {
     Ctl *ctl;
     unsigned long long *trace;  // optional (start, end) globaltimer per region
 };
+
+static_assert(sizeof(TablesDev) % 16 == 0, "tables are copied in 16-byte units");
+static_assert(sizeof(SimDev) % 16 == 0, "descriptors are copied in 16-byte units");
+static_assert(sizeof(LevelCoef) == 16, "coefficients are copied in 16-byte units");
 
 enum DeviceError { kDevOk = 0, kDevTimeout = 1, kDevBadRegion = 2 };
 
@@ -95,6 +126,26 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p)
     return v;
 }
 
+__device__ __forceinline__ int ld_acquire_cta_shared(const int *p)
+{
+    int v;
+    unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_cta_shared(int *p, int v)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// Barrier among the nthreads threads (a multiple of 32) that use this id.
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __device__ __forceinline__ void st_release_gpu(int *p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -109,23 +160,58 @@ __device__ __forceinline__ int atom_add_acq_rel_gpu(int *p, int v)
 
 // Asynchronous global -> shared copies (the copy engine of each SM; no
 // register staging).  8-byte copies go through L1 (.ca is the only mode for
-// that size); 16-byte copies bypass it (.cg).
+// that size); 16-byte copies bypass it (.cg).  The copies carry no compiler
+// memory clobber, so independent loads may be scheduled around them; shared
+// memory they write is read only after cp_async_wait_* (which has the
+// clobber) and a barrier.
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Waits until at most n of this thread's committed copy groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n)
+{
+    switch (n) {
+#define SP_WAIT_CASE(N)                                                     \
+    case N:                                                                 \
+        asm volatile("cp.async.wait_group " #N ";\n" ::: "memory");         \
+        break;
+        SP_WAIT_CASE(0) SP_WAIT_CASE(1) SP_WAIT_CASE(2) SP_WAIT_CASE(3) SP_WAIT_CASE(4) SP_WAIT_CASE(5)
+        SP_WAIT_CASE(6) SP_WAIT_CASE(7) SP_WAIT_CASE(8) SP_WAIT_CASE(9) SP_WAIT_CASE(10) SP_WAIT_CASE(11)
+        SP_WAIT_CASE(12) SP_WAIT_CASE(13) SP_WAIT_CASE(14) SP_WAIT_CASE(15)
+#undef SP_WAIT_CASE
+    default:
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+}
+
 #endif
+
+// floor(i / w) for 0 <= i < 2^20 and 1 <= w <= 64, from rcp = 1/w rounded to
+// FP32: (i + 1/2) / w lies at least 1/(2w) away from an integer, and the two
+// roundings (of 1/w and of the product) move it by at most about
+// 2^-23 (i + 1/2) / w < 1/(2w), so truncation gives the exact quotient.  The
+// host checks every (i, w) the tables use with the same operations.
+#if defined(__CUDACC__)
+__host__ __device__ __forceinline__
+#else
+inline
+#endif
+    int fdiv(int i, float rcp)
+{
+    return (int)(((float)i + 0.5f) * rcp);
+}
 
 }  // namespace sp

@@ -50,12 +50,12 @@ __global__ void reset_kernel(RegionArgs a)
     if (t >= a.total) return;
     const int s = find_sim(a, t);
     const SimDev &sd = a.sims[s];
-    const TablesDev *T = sd.tab;
+    const TypeMeta *M = sd.tab->type;
     const unsigned local = t - sd.tile_base;
     const unsigned per_band = 8u * (unsigned)sd.Jtot;
     const unsigned band = local / per_band;
     const int S = (int)((local - band * per_band) / (unsigned)sd.Jtot);
-    a.counters[t] = T->same_preds[S] + (band > 0 ? T->prev_preds[S] : 0);
+    a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds : 0);
     // queue position t: the first n_seed positions hold the band-0 pyramids
     int v = -1;
     if (t < a.n_seed) {
@@ -72,225 +72,470 @@ __global__ void reset_kernel(RegionArgs a)
     a.queue[t] = v;
 }
 
-// ------------------------------------------------------------ queue pop
-// Returns a region id, or -1 when the launch is out of work, or -2 on error.
-// Every wait is bounded by ctl->wait_limit_ns.
-__device__ int pop_region(const RegionArgs &a)
+// Region descriptor decoded from a launch-global region id.
+struct RegionInfo {
+    int sim, band, S, jl, j[3];
+};
+
+__device__ __forceinline__ int find_sim_in(const SimDev *sims, int n_sims, unsigned g)
 {
-    const unsigned idx = atomicAdd(&a.ctl->head, 1u);
-    if (idx >= a.total) return -1;
-    const unsigned long long limit = a.ctl->wait_limit_ns;
-    const unsigned long long t0 = globaltimer_ns();
-    for (unsigned spin = 0;; ++spin) {
-        int v = ld_acquire_gpu(a.queue + idx);
-        if (v >= 0) return v;
-        if (ld_relaxed_gpu(&a.ctl->error) != 0) return -2;
-        if ((spin & 15u) == 15u && globaltimer_ns() - t0 > limit) {
-            atomicCAS(&a.ctl->error, 0, kDevTimeout);
-            atomicExch(&a.ctl->error_info, (int)idx);
-            return -2;
-        }
-        __nanosleep(100);
+    int lo = 0, hi = n_sims - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].tile_base <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
+    return lo;
+}
+
+__device__ __forceinline__ RegionInfo decode_region(const SimDev *sims, int n_sims, int g)
+{
+    RegionInfo r;
+    r.sim = find_sim_in(sims, n_sims, (unsigned)g);
+    const SimDev &sd = sims[r.sim];
+    const unsigned local = (unsigned)g - sd.tile_base;
+    const unsigned per_band = 8u * (unsigned)sd.Jtot;
+    r.band = (int)(local / per_band);
+    const int rem = (int)(local - (unsigned)r.band * per_band);
+    r.S = rem / sd.Jtot;
+    r.jl = rem - r.S * sd.Jtot;
+    r.j[0] = r.jl % sd.J[0];
+    r.j[1] = (r.jl / sd.J[0]) % sd.J[1];
+    r.j[2] = r.jl / (sd.J[0] * sd.J[1]);
+    return r;
+}
+
+// One lane per successor: acq_rel decrement of its counter, push at zero.
+// Called by the 32 lanes of one warp after the whole CTA finished the region.
+__device__ void release_successors(const RegionArgs &a, const SimDev &sd, const TablesDev &T, const RegionInfo &r,
+                                   int lane, unsigned long long t_start, int g)
+{
+    __threadfence();
+    const int n_same = T.type[r.S].n_same_succ;
+    const int n_next = (r.S == kTypes - 1 && r.band + 1 < sd.nbands) ? kMaxNextSucc : 0;
+    if (lane < n_same + n_next) {
+        Succ su;
+        int nb;
+        if (lane < n_same) {
+            su = T.type[r.S].same_succ[lane];
+            nb = r.band;
+        } else {
+            su = T.next_succ[(r.band + 1) & 1][lane - n_same];
+            nb = r.band + 1;
+        }
+        int jc = 0, mul = 1;
+        for (int d = 0; d < 3; ++d) {
+            int v = r.j[d] + su.e[d];
+            v += (v < 0) ? sd.J[d] : 0;
+            v -= (v >= sd.J[d]) ? sd.J[d] : 0;
+            jc += v * mul;
+            mul *= sd.J[d];
+        }
+        const unsigned t = sd.tile_base + (unsigned)((nb * 8 + su.type) * sd.Jtot + jc);
+        const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
+        if (old == 1) {
+            const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
+            st_release_gpu(a.queue + pos, (int)t);
+        }
+    }
+    if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
+    (void)t_start;
+    (void)g;
 }
 
 // ------------------------------------------------------------ region kernel
-// Shared memory: two phi buffers (levels of alternating parity) of (B+2)^3
-// float2 for the region box plus its halo, and one float4 (pi, c) per own
-// cell (B^3).  Imports of level k land in the level-k phi buffer while level k
-// is being computed (disjoint cells), so their latency hides behind the
-// compute of that level.
-template <int NT>
-__global__ void __launch_bounds__(NT) region_kernel(RegionArgs a, int max_P)
+// Warp-specialised persistent kernel.  Warp 0 is the manager (the paper's
+// manager process, Sec. 4); the other NW threads are the worker that
+// evolves one region at a time.
+//
+// Manager: while the workers evolve region R it waits (bounded) for the next
+// queue position to be filled.  As soon as the workers report R done it hands
+// them the next region and only then releases R's successors (GPU-scope fence,
+// acq_rel decrements, push at zero), so the release overlaps the next
+// region's work.  If the next region is not ready it releases R first (the
+// next region may be one of R's successors).
+//
+// Worker shared memory, in order: two phi buffers (levels of alternating
+// parity) of (B+2)^3 float2 for the region box plus its halo; one float4
+// (pi, c) per own cell (B^3); the launch's tables (geometry and routing per
+// region type); the simulation descriptors; the band's level coefficients.
+// The tables and descriptors are copied once per launch, so no step of a
+// region waits on a table read from global memory.
+//
+// All data a region needs is requested when it starts: the band base and the
+// band's coefficients (copy group 0) and the sloped initial surface of every
+// level L = 1..H-1 (group L), each landing directly in its final place (the
+// level-L phi buffer, L & 1, and the (pi, c) array).  This is safe because the
+// cells imported for level L have, along some inverted axis, a coordinate at
+// least two cells outside what levels L-2 and L-1 read or write; the CPU
+// scaffold executes the same order and must match the whole-grid sweep bit
+// for bit.  Before level k is computed a thread waits for groups 0..k-1.
+//
+// One worker barrier per level.  The face cells of level k-1 are exported
+// after level k is computed, before the next barrier: they are read from the
+// level-(k-1) buffer and from (pi, c) of cells outside A(k) (the planner checks
+// this), while level k writes the other buffer and (pi, c) of A(k).  Their
+// table entries are loaded into registers before the compute.
+constexpr int kWorkerBarrier = 1;
+
+// Export entries of a level are loaded into registers before the compute of
+// the next level (up to kExportPrefetch per worker thread, which covers every
+// level of B <= 16 with 480 workers); any remainder is read in batches.
+constexpr int kExportPrefetch = 6;
+constexpr int kExportBatch = 4;
+
+__device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, float2 *const *mb_of,
+                                           const float2 *__restrict__ phi, const float4 *__restrict__ pc)
+{
+    const int code = (e.x >> 25) & 63;
+    float2 *mb = mb_of[code];
+    __stcg(mb + e.y, phi[e.x & 0x1FFF]);
+    if (e.x < 0) {
+        const TypeMeta &C = T.type[code & 7];
+        const int off = C.mb_level_off[L];
+        const int dst_pc = off + 2 * (e.y - off - 2 * C.imp_full_n[L]);
+        __stcg(reinterpret_cast<float4 *>(mb + dst_pc), pc[(e.x >> 13) & 0xFFF]);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void export_entries(const int2 *__restrict__ el, int ne, const int2 (&pre)[kExportPrefetch],
+                                               int L, const TablesDev &T, float2 *const *mb_of,
+                                               const float2 *__restrict__ phi, const float4 *__restrict__ pc, int wt)
+{
+#pragma unroll
+    for (int u = 0; u < kExportPrefetch; ++u)
+        if (wt + u * NW < ne) export_one(pre[u], L, T, mb_of, phi, pc);
+    for (int base = wt + kExportPrefetch * NW; base < ne; base += kExportBatch * NW) {
+        int2 e[kExportBatch];
+#pragma unroll
+        for (int u = 0; u < kExportBatch; ++u)
+            if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
+#pragma unroll
+        for (int u = 0; u < kExportBatch; ++u)
+            if (base + u * NW < ne) export_one(e[u], L, T, mb_of, phi, pc);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void prefetch_entries(const int2 *__restrict__ el, int ne, int2 (&pre)[kExportPrefetch],
+                                                 int wt)
+{
+#pragma unroll
+    for (int u = 0; u < kExportPrefetch; ++u)
+        if (wt + u * NW < ne) pre[u] = __ldg(el + wt + u * NW);
+}
+
+// Sloped initial surface of one level: mailbox chunk -> its places in shared
+// memory ((pi, c) and phi of full cells, phi of neighbour-only cells).  The
+// lists are in shared memory; a full cell's phi index follows from its
+// (pi, c) index.
+template <int NW>
+__device__ __forceinline__ void import_level(const float2 *__restrict__ mb, int nf, int np,
+                                             const unsigned short *fl, const unsigned short *pl, float2 *dst,
+                                             float4 *pc_s, int B, int P, float rcp_B, int wt)
+{
+    for (int i = wt; i < nf; i += NW) {
+        const int c = fl[i];
+        const int t1 = fdiv(c, rcp_B), t2 = fdiv(t1, rcp_B);
+        const int pidx = ((t2 + 1) * P + (t1 - t2 * B + 1)) * P + (c - t1 * B + 1);
+        cp_async16(pc_s + c, mb + 2 * i);
+        cp_async8(dst + pidx, mb + 2 * nf + i);
+    }
+    for (int i = wt; i < np; i += NW) cp_async8(dst + pl[i], mb + 3 * nf + i);
+}
+
+// One site of level k: linear index i over the active box A (x fastest).
+__device__ __forceinline__ void evolve_cell(int i, const Box3 &A, int w0, int w1, float r0, float r1, int P, int PP,
+                                            int B, const float2 *__restrict__ prev_buf, float2 *__restrict__ cur,
+                                            float4 *__restrict__ pc_s, const LevelCoef &co, const PhysConst &q)
+{
+    const int t1 = fdiv(i, r0);
+    const int t2 = fdiv(t1, r1);
+    const int ux = A.lo[0] + i - t1 * w0;
+    const int uy = A.lo[1] + t1 - t2 * w1;
+    const int uz = A.lo[2] + t2;
+    const int pidx = (uz * P + uy) * P + ux;
+    const int cidx = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+    const float4 pc = pc_s[cidx];
+    float2 pi = make_float2(pc.x, pc.y), cc = make_float2(pc.z, pc.w);
+    const float2 nphi = site_update(prev_buf[pidx], prev_buf[pidx - 1], prev_buf[pidx + 1], prev_buf[pidx - P],
+                                    prev_buf[pidx + P], prev_buf[pidx - PP], prev_buf[pidx + PP], pi, cc, co, q);
+    cur[pidx] = nphi;
+    pc_s[cidx] = make_float4(pi.x, pi.y, cc.x, cc.y);
+}
+
+// Manager warp: hand regions to the worker, release finished ones.
+__device__ void manager_loop(const RegionArgs &a, const SimDev *s_sims, const TablesDev *s_tabs, int *s_slot,
+                             int *s_handoff, int *s_done)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long limit = a.ctl->wait_limit_ns;
+    int seq = 0;           // handoffs made
+    int pending = -1;      // region handed at seq, not yet released
+    RegionInfo pend_info;
+    unsigned idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.ctl->head, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    int got = 0, v = -1;
+    unsigned long long t0 = globaltimer_ns();
+    unsigned long long t_progress = t0;  // last handoff or release
+    for (unsigned spin = 0;; ++spin) {
+        int done = 0;
+        if (lane == 0) {
+            if (!got) {
+                if (idx >= a.total) {
+                    got = 1;
+                    v = -1;
+                } else {
+                    const int q = ld_acquire_gpu(a.queue + idx);
+                    if (q >= 0) {
+                        got = 1;
+                        v = q;
+                    } else if (ld_relaxed_gpu(&a.ctl->error) != 0) {
+                        got = 1;
+                        v = -2;
+                    } else if ((spin & 15u) == 15u && globaltimer_ns() - t0 > limit) {
+                        atomicCAS(&a.ctl->error, 0, kDevTimeout);
+                        atomicExch(&a.ctl->error_info, (int)idx);
+                        got = 1;
+                        v = -2;
+                    }
+                }
+            }
+            done = ld_acquire_cta_shared(s_done) == seq;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        const int have = __shfl_sync(0xffffffffu, got, 0);
+        if (done && have) {
+            const int next = __shfl_sync(0xffffffffu, v, 0);
+            if (lane == 0) {
+                s_slot[(seq + 1) & 1] = next;
+                st_release_cta_shared(s_handoff, seq + 1);
+            }
+            ++seq;
+            if (pending >= 0) {
+                const SimDev &sd = s_sims[pend_info.sim];
+                release_successors(a, sd, s_tabs[sd.tab_index], pend_info, lane, 0ull, pending);
+            }
+            pending = next;
+            if (next < 0) break;
+            pend_info = decode_region(s_sims, a.n_sims, next);
+            if (lane == 0) {
+                got = 0;
+                idx = atomicAdd(&a.ctl->head, 1u);
+                t0 = globaltimer_ns();
+                t_progress = t0;
+            }
+            continue;
+        }
+        if (done && pending >= 0) {
+            // the next region is not ready yet: it may wait on this release
+            const SimDev &sd = s_sims[pend_info.sim];
+            release_successors(a, sd, s_tabs[sd.tab_index], pend_info, lane, 0ull, pending);
+            pending = -1;
+            if (lane == 0) t_progress = globaltimer_ns();
+            continue;
+        }
+        // no handoff and no release for 4 wait limits: the worker is stuck;
+        // record it and stop (the worker's own bounded wait then ends it too)
+        int stuck = 0;
+        if (lane == 0 && (spin & 15u) == 15u && globaltimer_ns() - t_progress > 4 * limit) {
+            atomicCAS(&a.ctl->error, 0, kDevTimeout);
+            stuck = 1;
+        }
+        if (__shfl_sync(0xffffffffu, stuck, 0)) break;
+        __nanosleep(32);
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int max_P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_region;
+    __shared__ int s_slot[2], s_handoff, s_done;
+    __shared__ float2 *s_mb[64];  // consumer code (type | offset bits << 3) -> mailbox base
     const int tid = threadIdx.x;
+    const int P3 = max_P * max_P * max_P, B3 = (max_P - 2) * (max_P - 2) * (max_P - 2);
     float2 *phi_buf0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *phi_buf1 = phi_buf0 + max_P * max_P * max_P;
-    float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + max_P * max_P * max_P);
+    float2 *phi_buf1 = phi_buf0 + P3;
+    float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + P3);
+    TablesDev *s_tabs = reinterpret_cast<TablesDev *>(pc_s + B3);
+    SimDev *s_sims = reinterpret_cast<SimDev *>(s_tabs + a.n_tabs);
+    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_sims + a.n_sims);
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_region = pop_region(a);
-        __syncthreads();
-        const int g = s_region;
+    {  // the launch's tables and simulation descriptors, once
+        const int4 *src = reinterpret_cast<const int4 *>(a.tabs);
+        int4 *dst = reinterpret_cast<int4 *>(s_tabs);
+        const int nt = a.n_tabs * (int)(sizeof(TablesDev) / 16);
+        for (int i = tid; i < nt; i += NW + 32) dst[i] = src[i];
+        const int4 *src2 = reinterpret_cast<const int4 *>(a.sims);
+        int4 *dst2 = reinterpret_cast<int4 *>(s_sims);
+        const int ns = a.n_sims * (int)(sizeof(SimDev) / 16);
+        for (int i = tid; i < ns; i += NW + 32) dst2[i] = src2[i];
+        if (tid == 0) {
+            s_handoff = 0;
+            s_done = 0;
+        }
+    }
+    __syncthreads();
+    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxH);
+    for (int t = 0; t < a.n_tabs; ++t) {  // every import list of the launch, once
+        const int4 *src = reinterpret_cast<const int4 *>(s_tabs[t].imp);
+        int4 *dst = reinterpret_cast<int4 *>(s_imp + s_tabs[t].imp_smem);
+        for (int i = tid; i < s_tabs[t].imp_n / 8; i += NW + 32) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        manager_loop(a, s_sims, s_tabs, s_slot, &s_handoff, &s_done);
+        return;
+    }
+    const int wt = tid - 32;  // worker thread index
+    __shared__ int s_abort;
+    for (int seq = 1;; ++seq) {
+        if (wt == 0) {
+            // bounded wait for the manager's handoff
+            s_abort = 0;
+            const unsigned long long t0 = globaltimer_ns(), limit = 8 * a.ctl->wait_limit_ns;
+            for (unsigned spin = 0; ld_acquire_cta_shared(&s_handoff) < seq; ++spin) {
+                if ((spin & 15u) == 15u && globaltimer_ns() - t0 > limit) {
+                    atomicCAS(&a.ctl->error, 0, kDevTimeout);
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        named_barrier(kWorkerBarrier, NW);
+        if (s_abort) break;
+        const int g = s_slot[seq & 1];
         if (g < 0) break;
-        unsigned long long t_start = 0;
-        if (a.trace && tid == 0) t_start = globaltimer_ns();
+        if (a.trace && wt == 0) a.trace[2 * (size_t)g] = globaltimer_ns();
 
-        const int s = find_sim(a, (unsigned)g);
-        const SimDev &sd = a.sims[s];
-        const TablesDev *__restrict__ T = sd.tab;
-        const int B = sd.B, H = sd.H, P = sd.P;
-        const unsigned local = (unsigned)g - sd.tile_base;
-        const unsigned per_band = 8u * (unsigned)sd.Jtot;
-        const int band = (int)(local / per_band);
-        const int rem = (int)(local - (unsigned)band * per_band);
-        const int S = rem / sd.Jtot;
-        const int jl = rem - S * sd.Jtot;
-        int j[3];
-        j[0] = jl % sd.J[0];
-        j[1] = (jl / sd.J[0]) % sd.J[1];
-        j[2] = jl / (sd.J[0] * sd.J[1]);
-        const int o = (band & 1) * H;
+        const RegionInfo r = decode_region(s_sims, a.n_sims, g);
+        const SimDev &sd = s_sims[r.sim];
+        const TablesDev &T = s_tabs[sd.tab_index];
+        const TypeMeta &M = T.type[r.S];
+        const int S = r.S, band = r.band, jl = r.jl;
+        const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
         int gbase[3];  // global coordinate of local u = 0 along each axis
-        for (int d = 0; d < 3; ++d) gbase[d] = o + j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
+        for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
         const int nx = sd.n[0], ny = sd.n[1], nz = sd.n[2];
+        const long long nxy = (long long)nx * ny;
         const long long slot = (long long)(band & 1) * sd.mb_slot;
+        if (wt < 64) {
+            // mailbox of the consumer with this code, if the code names one
+            const int Sc = wt & 7, eb = wt >> 3;
+            int jc = 0, mul = 1;
+            for (int d = 0; d < 3; ++d) {
+                int v = r.j[d] + ((eb >> d) & 1);
+                v -= (v >= sd.J[d]) ? sd.J[d] : 0;
+                jc += v * mul;
+                mul *= sd.J[d];
+            }
+            s_mb[wt] = sd.mbox + slot + sd.mb_type_off[Sc] + (long long)jc * T.type[Sc].mb_size;
+        }
 
-        // ---- level 0: the band base (tops of the previous band) ----
+        // ---- group 0: the band base (tops of the previous band) + coefficients ----
         {
-            const Box3 bp = T->base_phi[S];
-            const Box3 bc = T->base_pc[S];
-            const int w0 = bp.hi[0] - bp.lo[0], w1 = bp.hi[1] - bp.lo[1];
-            const int cnt = w0 * w1 * (bp.hi[2] - bp.lo[2]);
-            for (int i = tid; i < cnt; i += NT) {
-                const int ux = bp.lo[0] + i % w0;
-                const int t1 = i / w0;
-                const int uy = bp.lo[1] + t1 % w1;
-                const int uz = bp.lo[2] + t1 / w1;
-                const int out = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]) +
-                                (uz < bc.lo[2] || uz >= bc.hi[2]);
-                if (out > 1) continue;  // not a 7-point neighbour of A(1)
-                const int gx = wrap_axis(gbase[0] + ux, nx);
-                const int gy = wrap_axis(gbase[1] + uy, ny);
-                const int gz = wrap_axis(gbase[2] + uz, nz);
-                const long long gi = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * gz);
-                const int pidx = (uz * P + uy) * P + ux;
-                cp_async8(phi_buf0 + pidx, sd.phi + gi);
-                if (out == 0) {
-                    const int cidx = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
-                    float2 *pc2 = reinterpret_cast<float2 *>(pc_s + cidx);
-                    cp_async8(pc2, sd.pi + gi);
-                    cp_async8(pc2 + 1, sd.c + gi);
+            if (wt < H) cp_async16(s_coef + wt, sd.coef + band * H + wt);
+            const Box3 bp = M.base_phi;
+            const Box3 bc = M.base_pc;
+            const int w0 = bp.hi[0] - bp.lo[0];
+            const int cnt = w0 * (bp.hi[1] - bp.lo[1]);
+            for (int i = wt; i < cnt; i += NW) {
+                const int t1 = fdiv(i, M.rcp_base[0]);
+                const int ux = bp.lo[0] + i - t1 * w0;
+                const int uy = bp.lo[1] + t1;
+                const int oxy = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]);
+                if (oxy > 1) continue;  // not a 7-point neighbour of A(1)
+                const long long gxy =
+                    (long long)wrap_axis(gbase[0] + ux, nx) + (long long)nx * wrap_axis(gbase[1] + uy, ny);
+                for (int uz = bp.lo[2]; uz < bp.hi[2]; ++uz) {
+                    const int out = oxy + (uz < bc.lo[2] || uz >= bc.hi[2]);
+                    if (out > 1) continue;
+                    const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
+                    cp_async8(phi_buf0 + (uz * P + uy) * P + ux, sd.phi + gi);
+                    if (out == 0) cp_async16(pc_s + ((uz - 1) * B + (uy - 1)) * B + (ux - 1), sd.pc + gi);
                 }
             }
             cp_async_commit();
-            cp_async_wait_all();
-            __syncthreads();
         }
+        // ---- sloped initial surface: level L lands as copy group L, issued one
+        // level ahead (level 1 now, level k+1 at the start of level k) ----
+        const float2 *mb_self = sd.mbox + slot + sd.mb_type_off[S] + (long long)jl * M.mb_size;
+        const unsigned short *s_imp_t = s_imp + T.imp_smem;
+        auto issue_level = [&](int L) {
+            if (L <= H - 1) {
+                const int nf = M.imp_full_n[L], np = M.imp_phi_n[L];
+                if (nf + np > 0)
+                    import_level<NW>(mb_self + M.mb_level_off[L], nf, np, s_imp_t + M.imp_full_off[L],
+                                     s_imp_t + M.imp_phi_off[L], (L & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, T.rcp_B,
+                                     wt);
+            }
+            cp_async_commit();  // one group per level, empty or not
+        };
+        issue_level(1);
 
-        const int nlev = T->levels[S];
-        const float2 *mb_self = sd.mbox + slot + sd.mb_type_off[S] + (long long)jl * T->mb_size[S];
+        const int nlev = M.levels;
+        const PhysConst q = sd.q;
+        int2 pre[kExportPrefetch];
         for (int k = 1; k <= nlev; ++k) {
-            const float2 *__restrict__ prev = (k & 1) ? phi_buf0 : phi_buf1;
+            const float2 *__restrict__ prev_buf = (k & 1) ? phi_buf0 : phi_buf1;
             float2 *__restrict__ cur = (k & 1) ? phi_buf1 : phi_buf0;
-            // ---- sloped initial surface of level k (needed by level k+1) ----
-            if (k <= H - 1 && S != 0) {
-                const float2 *mb = mb_self + T->mb_level_off[S][k];
-                const int nf = T->imp_full_n[S][k], np = T->imp_phi_n[S][k];
-                const int *fl = T->imp_full + T->imp_full_off[S][k];
-                const int *pl = T->imp_phi + T->imp_phi_off[S][k];
-                for (int i = tid; i < nf; i += NT) {
-                    const int e = __ldg(fl + i);
-                    cp_async16(pc_s + (e >> 16), mb + 2 * i);
-                    cp_async8(cur + (e & 0xFFFF), mb + 2 * nf + i);
-                }
-                for (int i = tid; i < np; i += NT) cp_async8(cur + __ldg(pl + i), mb + 3 * nf + i);
-                cp_async_commit();
+            issue_level(k + 1);  // lands in buffer (k+1) & 1 outside what level k reads
+            // export entries of level k-1, loaded now, used after the compute
+            const int ne = k >= 2 ? M.exp_n[k - 1] : 0;
+            const int2 *el = T.exp + (k >= 2 ? M.exp_off[k - 1] : 0);
+            prefetch_entries<NW>(el, ne, pre, wt);
+            cp_async_wait_pending(2);  // groups 0..k-1 (base, coefficients, levels < k) have landed
+            named_barrier(kWorkerBarrier, NW);
+            // ---- evolve the cells of level k, two independent cells per step ----
+            const LevelCoef co = s_coef[k - 1];
+            const Box3 A = M.active[k];
+            const float r0 = M.rcp_active[k][0], r1 = M.rcp_active[k][1];
+            const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
+            const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
+            int i = wt;
+            for (; i + NW < cnt; i += 2 * NW) {
+                evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+                evolve_cell(i + NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
             }
-            // ---- evolve the cells of level k ----
-            {
-                const LevelCoef co = sd.coef[band * H + k - 1];
-                const PhysConst q = sd.q;
-                const Box3 A = T->active[S][k];
-                const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
-                const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
-                const int PP = P * P;
-                for (int i = tid; i < cnt; i += NT) {
-                    const int ux = A.lo[0] + i % w0;
-                    const int t1 = i / w0;
-                    const int uy = A.lo[1] + t1 % w1;
-                    const int uz = A.lo[2] + t1 / w1;
-                    const int pidx = (uz * P + uy) * P + ux;
-                    const int cidx = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
-                    const float4 pc = pc_s[cidx];
-                    float2 pi = make_float2(pc.x, pc.y), cc = make_float2(pc.z, pc.w);
-                    const float2 nphi = site_update(prev[pidx], prev[pidx - 1], prev[pidx + 1], prev[pidx - P],
-                                                    prev[pidx + P], prev[pidx - PP], prev[pidx + PP], pi, cc, co, q);
-                    cur[pidx] = nphi;
-                    pc_s[cidx] = make_float4(pi.x, pi.y, cc.x, cc.y);
-                }
-            }
-            cp_async_wait_all();
-            __syncthreads();
-            // ---- final surfaces of level k: into the consumers' mailboxes ----
-            if (k <= H - 1) {
-                const int4 *el = T->exp + T->exp_off[S][k];
-                const int ne = T->exp_n[S][k];
-                for (int i = tid; i < ne; i += NT) {
-                    const int4 e = __ldg(el + i);
-                    const int Sc = e.y & 7;
-                    int jc = 0, mul = 1;
-                    for (int d = 0; d < 3; ++d) {
-                        int v = j[d] + ((e.y >> (3 + d)) & 1);
-                        v -= (v >= sd.J[d]) ? sd.J[d] : 0;
-                        jc += v * mul;
-                        mul *= sd.J[d];
-                    }
-                    float2 *mb = sd.mbox + slot + sd.mb_type_off[Sc] + (long long)jc * T->mb_size[Sc];
-                    __stcg(mb + e.z, cur[e.x & 0xFFFF]);
-                    if (e.w >= 0) __stcg(reinterpret_cast<float4 *>(mb + e.w), pc_s[(e.x >> 16) & 0xFFFF]);
-                }
-            }
-            // ---- tops of the inverted pyramid: the next band's base ----
-            if (k == H) {
-                const int cnt = B * B * B;
-                for (int i = tid; i < cnt; i += NT) {
-                    const int ux = 1 + i % B;
-                    const int uy = 1 + (i / B) % B;
-                    const int uz = 1 + i / (B * B);
-                    const int gx = wrap_axis(gbase[0] + ux, nx);
-                    const int gy = wrap_axis(gbase[1] + uy, ny);
-                    const int gz = wrap_axis(gbase[2] + uz, nz);
-                    const long long gi = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * gz);
-                    const float4 pc = pc_s[i];
-                    __stcg(sd.phi + gi, cur[(uz * P + uy) * P + ux]);
-                    __stcg(sd.pi + gi, make_float2(pc.x, pc.y));
-                    __stcg(sd.c + gi, make_float2(pc.z, pc.w));
-                }
-            }
-            __syncthreads();
+            if (i < cnt) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+            // ---- final surface of level k-1 (read-only data of level k-1) ----
+            if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, wt);
         }
-
-        // ---- release successors (one lane per successor) ----
-        if (tid < 32) {
-            __threadfence();
-            const int n_same = T->n_same_succ[S];
-            const int n_next = (S == kTypes - 1 && band + 1 < sd.nbands) ? kMaxNextSucc : 0;
-            if (tid < n_same + n_next) {
-                Succ su;
-                int nb;
-                if (tid < n_same) {
-                    su = T->same_succ[S][tid];
-                    nb = band;
-                } else {
-                    su = T->next_succ[(band + 1) & 1][tid - n_same];
-                    nb = band + 1;
-                }
-                int jc = 0, mul = 1;
-                for (int d = 0; d < 3; ++d) {
-                    int v = j[d] + su.e[d];
-                    v += (v < 0) ? sd.J[d] : 0;
-                    v -= (v >= sd.J[d]) ? sd.J[d] : 0;
-                    jc += v * mul;
-                    mul *= sd.J[d];
-                }
-                const unsigned t = sd.tile_base + (unsigned)((nb * 8 + su.type) * sd.Jtot + jc);
-                const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
-                if (old == 1) {
-                    const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
-                    st_release_gpu(a.queue + pos, (int)t);
+        const float2 *last = (nlev & 1) ? phi_buf1 : phi_buf0;
+        if (nlev <= H - 1) {
+            // ---- final surface of the last level ----
+            const int ne = M.exp_n[nlev];
+            const int2 *el = T.exp + M.exp_off[nlev];
+            prefetch_entries<NW>(el, ne, pre, wt);
+            named_barrier(kWorkerBarrier, NW);
+            export_entries<NW>(el, ne, pre, nlev, T, s_mb, last, pc_s, wt);
+        } else {
+            named_barrier(kWorkerBarrier, NW);
+            // ---- tops of the inverted pyramid: the next band's base ----
+            const float rB = T.type[0].rcp_base[0];  // the pyramid's base box is B wide: 1/B
+            for (int i = wt; i < B * B; i += NW) {
+                const int t1 = fdiv(i, rB);
+                const int ux = 1 + i - t1 * B;
+                const int uy = 1 + t1;
+                const long long gxy =
+                    (long long)wrap_axis(gbase[0] + ux, nx) + (long long)nx * wrap_axis(gbase[1] + uy, ny);
+                for (int uz = 1; uz <= B; ++uz) {
+                    const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
+                    __stcg(sd.phi + gi, last[(uz * P + uy) * P + ux]);
+                    __stcg(sd.pc + gi, pc_s[((uz - 1) * B + (uy - 1)) * B + (ux - 1)]);
                 }
             }
-            if (tid == 0) {
-                atomicAdd(&a.ctl->completed, 1u);
-                if (a.trace) {
-                    a.trace[2 * (size_t)g] = t_start;
-                    a.trace[2 * (size_t)g + 1] = globaltimer_ns();
-                }
-            }
+        }
+        named_barrier(kWorkerBarrier, NW);
+        if (wt == 0) {
+            if (a.trace) a.trace[2 * (size_t)g + 1] = globaltimer_ns();
+            st_release_cta_shared(&s_done, seq);
         }
     }
 }
@@ -300,9 +545,8 @@ __global__ void __launch_bounds__(NT) region_kernel(RegionArgs a, int max_P)
 // a chunk of z keeping phi(z-1), phi(z), phi(z+1) in registers; x and y
 // neighbours come through L1.  48 bytes per site-update of HBM traffic.
 __global__ void __launch_bounds__(256) sweep_kernel(const float2 *__restrict__ phi_in, float2 *__restrict__ phi_out,
-                                                    float2 *__restrict__ pi, float2 *__restrict__ c, int nx, int ny,
-                                                    int nz, int zchunk, const LevelCoef *__restrict__ coef, int lvl,
-                                                    PhysConst q)
+                                                    float4 *__restrict__ pc, int nx, int ny, int nz, int zchunk,
+                                                    const LevelCoef *__restrict__ coef, int lvl, PhysConst q)
 {
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
@@ -321,12 +565,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const float2 *__restrict__ p
         const float2 znext = phi_in[zn * plane + (long long)y * nx + x];
         const long long zo = z * plane;
         const long long row = zo + (long long)y * nx;
-        float2 p = pi[row + x], cc = c[row + x];
+        const float4 v = pc[row + x];
+        float2 p = make_float2(v.x, v.y), cc = make_float2(v.z, v.w);
         const float2 out = site_update(zcur, phi_in[row + xm], phi_in[row + xp], phi_in[zo + (long long)ym * nx + x],
                                        phi_in[zo + (long long)yp * nx + x], zprev, znext, p, cc, co, q);
         phi_out[row + x] = out;
-        pi[row + x] = p;
-        c[row + x] = cc;
+        pc[row + x] = make_float4(p.x, p.y, cc.x, cc.y);
         zprev = zcur;
         zcur = znext;
     }
@@ -340,7 +584,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const float2 *__restrict__ p
 constexpr int kDiagThreads = 256;
 
 __global__ void __launch_bounds__(kDiagThreads)
-    energy_partial_kernel(const float2 *__restrict__ phi, const float2 *__restrict__ pi, int nx, int ny, int nz,
+    energy_partial_kernel(const float2 *__restrict__ phi, const float4 *__restrict__ pc, int nx, int ny, int nz,
                           double inv_dx2, double eta2, double half_lambda_a2, double *__restrict__ partial)
 {
     __shared__ double red[3][kDiagThreads];
@@ -353,7 +597,8 @@ __global__ void __launch_bounds__(kDiagThreads)
         const int x = (int)(s % nx);
         const int y = (int)((s / nx) % ny);
         const int z = (int)(s / ((long long)nx * ny));
-        const float2 f = phi[s], v = pi[s];
+        const float2 f = phi[s];
+        const float4 v = pc[s];
         const double fr = f.x, fi = f.y;
         kin = __dadd_rn(kin, __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y)));
         const long long nb[3] = {s - x + (x == nx - 1 ? 0 : x + 1),
@@ -452,66 +697,69 @@ cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int NT>
-static cudaError_t region_launch_t(const RegionArgs &a, int max_B, int grid, cudaStream_t st)
+template <int NW>
+static cudaError_t region_launch_t(const RegionArgs &a, int max_B, size_t smem, int grid, cudaStream_t st)
 {
-    const int P = max_B + 2;
-    const size_t smem = (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(region_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(region_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    region_kernel<NT><<<grid, NT, smem, st>>>(a, P);
+    region_kernel<NW><<<grid, NW + 32, smem, st>>>(a, max_B + 2);
     return cudaGetLastError();
 }
 
-size_t region_smem_bytes(int max_B)
+size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units)
 {
     const int P = max_B + 2;
-    return (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4);
+    return (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4) +
+           (size_t)n_tabs * sizeof(TablesDev) + (size_t)n_sims * sizeof(SimDev) + kMaxH * sizeof(LevelCoef) +
+           (size_t)imp_units * sizeof(unsigned short);
 }
 
-cudaError_t region_occupancy(int threads, int max_B, int *blocks_per_sm)
+// threads = worker threads per CTA (the manager warp comes on top)
+cudaError_t region_occupancy(int threads, size_t smem, int *blocks_per_sm)
 {
-    const size_t smem = region_smem_bytes(max_B);
     cudaError_t e;
-#define SP_OCC(NT)                                                                                               \
-    case NT:                                                                                                     \
-        e = cudaFuncSetAttribute(region_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+#define SP_OCC(NW)                                                                                               \
+    case NW:                                                                                                     \
+        e = cudaFuncSetAttribute(region_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
         if (e != cudaSuccess) return e;                                                                          \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, region_kernel<NT>, NT, smem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, region_kernel<NW>, NW + 32, smem);
     switch (threads) {
         SP_OCC(128)
         SP_OCC(256)
+        SP_OCC(480)
         SP_OCC(512)
-        SP_OCC(1024)
+        SP_OCC(768)
     default:
         return cudaErrorInvalidValue;
     }
 #undef SP_OCC
 }
 
-cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, int grid, cudaStream_t st)
+cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st)
 {
     switch (threads) {
     case 128:
-        return region_launch_t<128>(a, max_B, grid, st);
+        return region_launch_t<128>(a, max_B, smem, grid, st);
     case 256:
-        return region_launch_t<256>(a, max_B, grid, st);
+        return region_launch_t<256>(a, max_B, smem, grid, st);
+    case 480:
+        return region_launch_t<480>(a, max_B, smem, grid, st);
     case 512:
-        return region_launch_t<512>(a, max_B, grid, st);
-    case 1024:
-        return region_launch_t<1024>(a, max_B, grid, st);
+        return region_launch_t<512>(a, max_B, smem, grid, st);
+    case 768:
+        return region_launch_t<768>(a, max_B, smem, grid, st);
     default:
         return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_sweep(const float2 *phi_in, float2 *phi_out, float2 *pi, float2 *c, const int n[3],
+cudaError_t launch_sweep(const float2 *phi_in, float2 *phi_out, float4 *pc, const int n[3],
                          const LevelCoef *coef, int lvl, PhysConst q, cudaStream_t st)
 {
     const int zchunk = 8;
     dim3 block(32, 8, 1);
     dim3 grid((n[0] + 31) / 32, (n[1] + 7) / 8, (n[2] + zchunk - 1) / zchunk);
-    sweep_kernel<<<grid, block, 0, st>>>(phi_in, phi_out, pi, c, n[0], n[1], n[2], zchunk, coef, lvl, q);
+    sweep_kernel<<<grid, block, 0, st>>>(phi_in, phi_out, pc, n[0], n[1], n[2], zchunk, coef, lvl, q);
     return cudaGetLastError();
 }
 
@@ -522,11 +770,11 @@ int energy_blocks(const int n[3])
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
-cudaError_t launch_energy(const float2 *phi, const float2 *pi, const int n[3], double inv_dx2, double eta2,
+cudaError_t launch_energy(const float2 *phi, const float4 *pc, const int n[3], double inv_dx2, double eta2,
                           double half_lambda_a2, double *partial, double *out, cudaStream_t st)
 {
     const int nb = energy_blocks(n);
-    energy_partial_kernel<<<nb, kDiagThreads, 0, st>>>(phi, pi, n[0], n[1], n[2], inv_dx2, eta2, half_lambda_a2,
+    energy_partial_kernel<<<nb, kDiagThreads, 0, st>>>(phi, pc, n[0], n[1], n[2], inv_dx2, eta2, half_lambda_a2,
                                                         partial);
     energy_final_kernel<<<1, 32, 0, st>>>(partial, nb, out);
     return cudaGetLastError();

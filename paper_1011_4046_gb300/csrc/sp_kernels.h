@@ -7,13 +7,13 @@
 namespace sp {
 
 cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st);
-size_t region_smem_bytes(int max_B);
-cudaError_t region_occupancy(int threads, int max_B, int *blocks_per_sm);
-cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, int grid, cudaStream_t st);
-cudaError_t launch_sweep(const float2 *phi_in, float2 *phi_out, float2 *pi, float2 *c, const int n[3],
+size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units);
+cudaError_t region_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st);
+cudaError_t launch_sweep(const float2 *phi_in, float2 *phi_out, float4 *pc, const int n[3],
                          const LevelCoef *coef, int lvl, PhysConst q, cudaStream_t st);
 int energy_blocks(const int n[3]);
-cudaError_t launch_energy(const float2 *phi, const float2 *pi, const int n[3], double inv_dx2, double eta2,
+cudaError_t launch_energy(const float2 *phi, const float4 *pc, const int n[3], double inv_dx2, double eta2,
                           double half_lambda_a2, double *partial, double *out, cudaStream_t st);
 cudaError_t launch_winding(const float2 *phi, const int n[3], signed char *w, unsigned long long *counts,
                            cudaStream_t st);

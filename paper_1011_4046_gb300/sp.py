@@ -34,12 +34,14 @@ SP_ASYNC = 1
 SP_MONOLITHIC = 2
 SP_RESTART = 4
 SP_TRACE = 8
+SP_TIMING = 16
 
 SP_SURF_STATE = 0
 SP_SURF_DIAG = 1
 SP_SURF_TRACE = 2
 SP_SURF_WINDING = 3
 SP_SURF_PLAN = 4
+SP_SURF_TIMING = 5
 
 SP_ORDER_STATIC = 0
 SP_ORDER_LEARNED = 1
@@ -193,13 +195,32 @@ def make_params(n, dx=1.0, dt=0.25, lam=2.0, eta=1.0, nu=0.0, tau0=1.0, tau_ref=
     return p
 
 
+def pack_state(phi, pi, c) -> np.ndarray:
+    """SP_SURF_STATE layout: phi (sites complex64) then pic (sites x (pi, c))."""
+    phi = np.ascontiguousarray(phi, dtype=np.complex64).ravel()
+    pic = np.stack([np.asarray(pi, dtype=np.complex64).ravel(), np.asarray(c, dtype=np.complex64).ravel()], axis=1)
+    return np.concatenate([phi, pic.ravel()])
+
+
+def unpack_state(buf, shape):
+    """Inverse of pack_state: (phi, pi, c), each complex64 of ``shape``."""
+    sites = int(np.prod(shape))
+    buf = np.asarray(buf).view(np.complex64).ravel()
+    phi = buf[:sites].reshape(shape)
+    pic = buf[sites:3 * sites].reshape(sites, 2)
+    return phi, pic[:, 0].reshape(shape).copy(), pic[:, 1].reshape(shape).copy()
+
+
 def _check(rc, what):
     if rc != SP_OK:
         raise SpError(rc, what)
 
 
 class Grid:
-    """Handle + the torch device tensors (phi, pi, c per simulation) + stream."""
+    """Handle + the torch device tensors of each simulation + stream.
+
+    A simulation's state is (phi, pic): phi complex64 (nz, ny, nx) and pic
+    complex64 (nz, ny, nx, 2) holding (pi, c) per site, the library layout."""
 
     def __init__(self, params, states=None, stream=None, device="cuda"):
         import torch
@@ -210,7 +231,8 @@ class Grid:
             states = []
             for p in self.params:
                 shape = (p.n[2], p.n[1], p.n[0])
-                states.append(tuple(torch.zeros(shape, dtype=torch.complex64, device=device) for _ in range(3)))
+                states.append((torch.zeros(shape, dtype=torch.complex64, device=device),
+                               torch.zeros(shape + (2,), dtype=torch.complex64, device=device)))
         self.states = states
         ptrs = [t.data_ptr() for st in states for t in st]
         rc, self.h = sp_grid_create(self.params, ptrs, self.stream.cuda_stream)
@@ -223,15 +245,16 @@ class Grid:
         _check(sp_evolve(self.h, n_steps, flags), "sp_evolve")
 
     def write_state(self, sim, phi, pi, c):
-        buf = np.ascontiguousarray(np.stack([np.asarray(phi), np.asarray(pi), np.asarray(c)]), dtype=np.complex64)
+        buf = pack_state(phi, pi, c)
         _check(sp_write_surface(self.h, sim, SP_SURF_STATE, buf.ctypes.data, buf.nbytes, 0), "sp_write_surface")
         self.stream.synchronize()
 
     def read_state(self, sim):
         p = self.params[sim]
-        out = np.empty((3, p.n[2], p.n[1], p.n[0]), dtype=np.complex64)
+        shape = (p.n[2], p.n[1], p.n[0])
+        out = np.empty(3 * int(np.prod(shape)), dtype=np.complex64)
         _check(sp_read_surface(self.h, sim, SP_SURF_STATE, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
-        return out[0], out[1], out[2]
+        return unpack_state(out, shape)
 
     def diag(self, sim=0) -> dict:
         d = sp_diag()
@@ -251,6 +274,12 @@ class Grid:
         _check(sp_read_surface(self.h, sim, SP_SURF_PLAN, ctypes.addressof(d), ctypes.sizeof(d), 0),
                "sp_read_surface")
         return {f: getattr(d, f) for f, _ in sp_plan_info._fields_}
+
+    def timing(self):
+        """(reset_ms, region_kernel_ms, remainder_ms) of the last SP_TIMING evolve."""
+        out = np.zeros(3, dtype=np.float64)
+        _check(sp_read_surface(self.h, 0, SP_SURF_TIMING, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
+        return tuple(out.tolist())
 
     def trace(self, sim, n_regions):
         out = np.empty((n_regions, 2), dtype=np.uint64)

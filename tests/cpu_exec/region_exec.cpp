@@ -344,20 +344,24 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                 }
         std::vector<f2> &mb = mbox[band & 1];
         const int64_t self = type_off[S] + (int64_t)(j[0] + g.J[0] * (j[1] + g.J[1] * j[2])) * t.mb_size[S];
-        for (int k = 1; k <= t.levels[S]; ++k) {
-            std::vector<f2> &prev = (k & 1) ? buf0 : buf1;
-            std::vector<f2> &cur = (k & 1) ? buf1 : buf0;
-            if (k <= H - 1 && S != 0) {
+        // every sloped-surface import of every level lands at region start, as
+        // in the kernel: level k goes to the level-k phi buffer (k & 1)
+        if (S != 0)
+            for (int k = 1; k <= H - 1; ++k) {
+                std::vector<f2> &dst = (k & 1) ? buf1 : buf0;
                 const int64_t base = self + t.mb_level_off[S][k];
                 const int nf = t.imp_full_n[S][k], np = t.imp_phi_n[S][k];
                 for (int i = 0; i < nf; ++i) {
                     int e = t.imp_full[t.imp_full_off[S][k] + i];
                     pis[e >> 16] = mb[base + 2 * i];
                     cs[e >> 16] = mb[base + 2 * i + 1];
-                    cur[e & 0xFFFF] = mb[base + 2 * nf + i];
+                    dst[e & 0xFFFF] = mb[base + 2 * nf + i];
                 }
-                for (int i = 0; i < np; ++i) cur[t.imp_phi[t.imp_phi_off[S][k] + i]] = mb[base + 3 * nf + i];
+                for (int i = 0; i < np; ++i) dst[t.imp_phi[t.imp_phi_off[S][k] + i]] = mb[base + 3 * nf + i];
             }
+        for (int k = 1; k <= t.levels[S]; ++k) {
+            std::vector<f2> &prev = (k & 1) ? buf0 : buf1;
+            std::vector<f2> &cur = (k & 1) ? buf1 : buf0;
             const sp::Box3 &A = t.active[S][k];
             const int PP = P * P;
             for (int uz = A.lo[2]; uz < A.hi[2]; ++uz)
