@@ -61,6 +61,30 @@ def peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
+                  "paper_1011_4046_gb300/csrc/sp_update.h"]
+
+
+def ncu_traffic(workload_is_default):
+    """DRAM bytes per region-kernel launch from the committed ncu record, or
+    None when the kernel sources changed since it was taken (or the workload
+    differs from the one it was taken on)."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "region_kernel_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for s in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, s), "rb") as f:
+                h.update(f.read())
+        if not workload_is_default or h.hexdigest()[:16] != rec["kernel_sources_sha256_16"]:
+            return None
+        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+    except Exception:
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -85,7 +109,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -261,7 +285,8 @@ def run_ours(args):
         "monolithic": {"value": mono_value, "unit": "site-updates/s", "ms_per_step": sum(mono_ms) / len(mono_ms),
                        "speedup_of_regions": value / ws / mono_value},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(N == 128 and STEPS == 256 and base == B and args.threads == 0),
                      "kernel": "region_kernel", "kernel_ms": kern_mean,
                      "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
                      "design_bytes_per_update": info["bytes_per_update"]},
