@@ -52,6 +52,7 @@ extern "C" {
 #define SP_ENONFINITE (-6)      /* non-finite field detected by a diagnostic */
 #define SP_EFAULT_INJECTED (-7) /* a host-injected region failure was recorded */
 #define SP_ENOTPLANNED (-8)     /* sp_evolve before sp_region_plan */
+#define SP_ESCRATCH (-9)        /* sp_sweep_noalloc: grid or step count beyond its fixed scratch */
 
 /* ---- flags of sp_evolve ---- */
 #define SP_ASYNC 1u      /* return without synchronising the stream */
@@ -172,6 +173,34 @@ int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size
  * Enqueued on the grid's stream.  Errors: SP_EINVAL, SP_ECUDA.
  */
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device);
+
+/*
+ * sp_sweep_noalloc -- advance one simulation by n_steps whole-grid leapfrog
+ * steps without allocating any memory.  (The paper has no counterpart: this
+ * entry point serves callers that may not allocate device memory -- programs
+ * that own all device memory through their own fixed pools, plug-ins that
+ * must not grow the process's footprint, latency-critical paths.)
+ *   p         : parameters of the simulation (host memory).
+ *   phi_dev, pic_dev : its state in the layout above, updated in place.
+ *   level0    : level of the state on entry (selects tau, a and friction).
+ *   n_steps   : steps to take; the work is enqueued on cuda_stream and the
+ *               call returns without synchronising.
+ * Results are bit-identical to sp_evolve(..., SP_MONOLITHIC) from the same
+ * state and level.  Scratch: a phi ping-pong buffer of at most
+ * SP_NOALLOC_MAX_SITES sites (2 MiB) and SP_NOALLOC_MAX_STEPS per-level
+ * coefficients (128 KiB), in fixed device arrays that every GPU loading the
+ * library holds until exit.  The first call on a device looks up those
+ * arrays' device addresses (once per device); make it before any stream
+ * capture.  All calls share the arrays: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: SP_EINVAL, SP_ESCRATCH (more than SP_NOALLOC_MAX_SITES sites or
+ * SP_NOALLOC_MAX_STEPS steps), SP_EUNSTABLE, SP_ECUDA.
+ */
+#define SP_NOALLOC_MAX_SITES 262144
+#define SP_NOALLOC_MAX_STEPS 8192
+int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev, int64_t level0, int64_t n_steps,
+                     void *cuda_stream);
 
 /* sp_destroy -- free everything the library allocated (not caller state). */
 int sp_destroy(sp_grid *g);

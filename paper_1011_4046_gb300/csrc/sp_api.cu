@@ -436,6 +436,9 @@ const char *sp_strerror(int code)
         return "host-injected region failure";
     case SP_ENOTPLANNED:
         return "sp_evolve called before sp_region_plan";
+    case SP_ESCRATCH:
+        return "sp_sweep_noalloc: more than SP_NOALLOC_MAX_SITES (262144) sites or SP_NOALLOC_MAX_STEPS (8192) "
+               "steps, the size of its fixed scratch";
     default:
         return "unknown error";
     }

@@ -29,6 +29,9 @@ SP_ETIMEOUT = -5
 SP_ENONFINITE = -6
 SP_EFAULT_INJECTED = -7
 SP_ENOTPLANNED = -8
+SP_ESCRATCH = -9
+SP_NOALLOC_MAX_SITES = 262144
+SP_NOALLOC_MAX_STEPS = 8192
 
 SP_ASYNC = 1
 SP_MONOLITHIC = 2
@@ -135,10 +138,11 @@ def load(build_if_missing: bool = False):
         lib.sp_read_surface.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
         lib.sp_write_surface.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
         lib.sp_destroy.argtypes = [vp]
+        lib.sp_sweep_noalloc.argtypes = [ctypes.POINTER(sp_params), vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
         lib.sp_strerror.argtypes = [ctypes.c_int]
         lib.sp_strerror.restype = ctypes.c_char_p
         for f in ("sp_grid_create", "sp_region_plan", "sp_evolve", "sp_read_surface", "sp_write_surface",
-                  "sp_destroy"):
+                  "sp_destroy", "sp_sweep_noalloc"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -182,6 +186,12 @@ def sp_write_surface(h, sim, what, src_ptr, src_bytes, src_is_device):
 
 def sp_destroy(h):
     return load().sp_destroy(h)
+
+
+def sp_sweep_noalloc(params, phi_ptr, pic_ptr, level0, n_steps, stream=0):
+    """Whole-grid steps with no memory allocation (see include/sp.h)."""
+    return load().sp_sweep_noalloc(ctypes.byref(params), ctypes.c_void_p(int(phi_ptr)), ctypes.c_void_p(int(pic_ptr)),
+                                   int(level0), int(n_steps), ctypes.c_void_p(int(stream)))
 
 
 # ------------------------------------------------------------ helpers
