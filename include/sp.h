@@ -70,6 +70,9 @@ extern "C" {
 #define SP_SURF_TIMING 5  /* double[3]: ms of the queue reset, the region kernel and the
                              remainder sweep of the last SP_TIMING call (events on the stream) */
 
+/* ---- sp_region_plan: base_B / block_shape chosen by measurement ---- */
+#define SP_AUTOTUNE (-1)
+
 /* ---- region ordering of sp_region_plan ---- */
 #define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
 #define SP_ORDER_LEARNED 1 /* cost-model priority (results are identical) */
@@ -113,6 +116,10 @@ typedef struct {
     int64_t bytes_written_per_band;
     double bytes_per_update;
     int64_t mailbox_bytes;
+    int32_t autotuned;       /* 1 if base_B or block_shape was SP_AUTOTUNE */
+    int32_t tune_candidates; /* candidates the autotuner timed */
+    double tune_best_ms;     /* its trial time of the chosen candidate (16 steps) */
+    double tune_default_ms;  /* its trial time of the default choice, 0 if not timed */
 } sp_plan_info;
 
 /*
@@ -134,11 +141,18 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  * sp_region_plan -- build the region tiling, the dependency DAG and the
  * surface routing tables (paper Sec. 2 geometry and Sec. 3 sizing), and size
  * the persistent launch.
- *   base_B     : region base in cells (8 or 16; B/2 steps per band), or 0 to
- *                pick one per simulation.  Every n[d] must be a multiple of B
- *                with n[d] / B >= 2.
+ *   base_B     : region base in cells (8 or 16; B/2 steps per band); 0 to
+ *                take 16 where it divides every side of a simulation, else 8;
+ *                SP_AUTOTUNE to time both policies (all 8, 16 where
+ *                possible) and keep the faster.  Every n[d] must be a
+ *                multiple of B with n[d] / B >= 2.
  *   block_shape: worker threads per CTA (128, 256, 480, 512 or 768; one
- *                manager warp is added), or 0 for the default.
+ *                manager warp is added); 0 for the default (128 when every
+ *                base is 8, else 256); SP_AUTOTUNE to time the candidates
+ *                (128, 256 for base 8; 256, 480, 512 for base 16).
+ *                The autotuner runs 16-step calls on scratch copies of the
+ *                current state (sides above 128 cells are cut to 128 or 120),
+ *                on the grid's stream; the state itself is not modified.
  *   order      : SP_ORDER_STATIC or SP_ORDER_LEARNED.
  *   model_path : cost-model weights for SP_ORDER_LEARNED, or NULL.
  * Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA.

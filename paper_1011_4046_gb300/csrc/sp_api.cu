@@ -38,6 +38,27 @@ struct SweepGraph {
     const void *phi = nullptr, *tmp = nullptr;
 };
 
+// What the autotuner of the last sp_region_plan measured.
+struct TuneReport {
+    int autotuned = 0, candidates = 0, trial_steps = 0;
+    double best_ms = 0.0, default_ms = 0.0;
+};
+
+// The region path of one sp_evolve call, captured once and replayed while the
+// launch parameters stay the same (the key is every byte that the captured
+// launches take by value).
+struct RegionGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+};
+
+template <class T>
+void append_key(std::vector<unsigned char> *key, const T &v)
+{
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+    key->insert(key->end(), b, b + sizeof(T));
+}
+
 template <class T>
 cudaError_t grow(T **p, size_t *cap, size_t need)
 {
@@ -148,6 +169,9 @@ struct sp_grid {
     std::vector<unsigned> last_tile_base, last_tiles;
     bool last_traced = false;
     SweepGraph sweep_graph;
+    RegionGraph region_graph;
+    TuneReport tune;
+    int use_graphs = 1;  // capture launch sequences on non-legacy streams
     unsigned long long wait_limit_ns = 2000000000ull;
     // what is already on the device (uploads are skipped when unchanged)
     std::vector<sp::LevelCoef> up_coef;
@@ -324,6 +348,9 @@ void free_plan(sp_grid *g)
     g->n_tabs = 0;
     for (float2 *m : g->mbox) cudaFree(m);
     g->mbox.clear();
+    if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);
+    g->region_graph.exec = nullptr;
+    g->region_graph.key.clear();
     g->planned = false;
 }
 
@@ -409,6 +436,233 @@ int sweep_steps(sp_grid *g, int s, int64_t nsteps, int64_t first_local, const sp
         sg.tmp = g->d_tmp;
     }
     return cudaGraphLaunch(sg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+// The launches of one region-path call: reset + persistent region kernel over
+// all simulations' whole bands, then each simulation's remainder steps as
+// whole-grid steps.  Timing events 1 and 2 bracket the region kernel.
+int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool capturing)
+{
+    cudaError_t e = cudaSuccess;
+    auto mark = [&](cudaEvent_t ev) {
+        if (e == cudaSuccess)
+            e = capturing ? cudaEventRecordWithFlags(ev, g->stream, cudaEventRecordExternal)
+                          : cudaEventRecord(ev, g->stream);
+    };
+    if (a) {
+        e = sp::launch_reset(*a, g->stream);
+        if (timing) mark(g->ev[1]);
+        if (e == cudaSuccess) e = sp::launch_region(*a, g->threads, g->max_B, g->smem, g->grid, g->stream);
+        if (timing) mark(g->ev[2]);
+    } else if (timing) {
+        mark(g->ev[1]);
+        mark(g->ev[2]);
+    }
+    if (e != cudaSuccess) return SP_ECUDA;
+    for (int s = 0; s < g->n_sims; ++s) {
+        const int H = g->B[s] / 2;
+        const int64_t done = (n_steps / H) * H;
+        if (n_steps - done <= 0) continue;
+        const int rc = enqueue_sweep(g, s, n_steps - done, done, g->d_coef + (size_t)s * n_steps);
+        if (rc != SP_OK) return rc;
+    }
+    return SP_OK;
+}
+
+// Runs the region-path call.  On a capturable stream the launch sequence is
+// recorded once into a CUDA graph and replayed while every by-value launch
+// parameter is unchanged, so a repeated call costs one graph launch.
+int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing)
+{
+    if (g->stream == nullptr || !g->use_graphs) return enqueue_region_call(g, a, n_steps, timing, false);
+    std::vector<unsigned char> key;
+    append_key(&key, n_steps);
+    append_key(&key, timing);
+    append_key(&key, a != nullptr);
+    if (a) append_key(&key, *a);
+    append_key(&key, g->threads);
+    append_key(&key, g->max_B);
+    append_key(&key, g->smem);
+    append_key(&key, g->grid);
+    append_key(&key, g->d_tmp);
+    append_key(&key, g->d_coef);
+    for (int s = 0; s < g->n_sims; ++s) {
+        append_key(&key, g->phi[s]);
+        append_key(&key, g->pc[s]);
+        append_key(&key, g->B[s]);
+    }
+    RegionGraph &rg = g->region_graph;
+    if (!rg.exec || rg.key != key) {
+        if (rg.exec) cudaGraphExecDestroy(rg.exec);
+        rg.exec = nullptr;
+        rg.key.clear();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return SP_ECUDA;
+        const int rc = enqueue_region_call(g, a, n_steps, timing, true);
+        e = cudaStreamEndCapture(g->stream, &graph);
+        if (rc != SP_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != SP_OK ? rc : SP_ECUDA;
+        }
+        e = cudaGraphInstantiate(&rg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            rg.exec = nullptr;
+            return SP_ECUDA;
+        }
+        rg.key = key;
+    }
+    return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+bool valid_threads(int t) { return t == 128 || t == 256 || t == 480 || t == 512 || t == 768; }
+
+// Builds the plan for fixed region bases (one per simulation) and worker
+// count (0 = default for the largest base).
+int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, const char *model_path)
+{
+    (void)model_path;
+    free_plan(g);
+    g->B = Bs;
+    g->max_B = 0;
+    for (int s = 0; s < g->n_sims; ++s) {
+        g->max_B = std::max(g->max_B, Bs[s]);
+        int rc = build_device_tables(g, Bs[s]);
+        if (rc != SP_OK) return rc;
+    }
+    int rct = upload_table_array(g);
+    if (rct != SP_OK) return rct;
+    g->threads = threads ? threads : default_threads(g->max_B);
+    g->smem = sp::region_smem_bytes(g->max_B, g->n_tabs, g->n_sims, g->imp_smem_units);
+    if (g->smem > 227 * 1024) return SP_EINVAL;
+    cudaError_t e = sp::region_occupancy(g->threads, g->smem, &g->ctas_per_sm);
+    if (e != cudaSuccess || g->ctas_per_sm < 1) return SP_EINVAL;
+    g->grid = g->ctas_per_sm * g->sm_count;
+    g->order = order;
+    // mailbox ring: two band slots per simulation
+    g->mb_slot.assign(g->n_sims, 0);
+    g->mb_type_off.assign(g->n_sims, {});
+    for (int s = 0; s < g->n_sims; ++s) {
+        const sp::TileTables &t = g->tables[g->B[s]].host;
+        long long J = 1;
+        for (int d = 0; d < 3; ++d) J *= g->p[s].n[d] / g->B[s];
+        long long off = 0;
+        for (int S = 0; S < sp::kTypes; ++S) {
+            g->mb_type_off[s][S] = off;
+            off += J * t.mb_size[S];
+        }
+        g->mb_slot[s] = off;
+        float2 *m = nullptr;
+        e = cudaMalloc((void **)&m, std::max<size_t>(2 * off * sizeof(float2), 16));
+        if (e != cudaSuccess) {
+            free_plan(g);
+            return SP_ENOMEM;
+        }
+        g->mbox.push_back(m);
+    }
+    g->planned = true;
+    return SP_OK;
+}
+
+// Side of a trial grid along one axis: the simulation's own side up to 128
+// cells, else 128 (a multiple of 16 when the side is) or 120.
+int trial_side(int n) { return n <= 128 ? n : (n % 16 == 0 ? 128 : 120); }
+
+// Autotuner: times every candidate (region-base policy x worker count) on
+// scratch copies of the simulations -- the state itself is not touched --
+// and returns the fastest.  A candidate is timed by CUDA events around a
+// 16-step region-path call (two bands at B = 16, four at B = 8), best of
+// two after one warm-up call.  Simulations larger than 128 cells along an
+// axis are timed on a 128^3-class trial grid holding the first sites of
+// their state.
+int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, int *best_threads)
+{
+    std::vector<std::vector<int>> policies;
+    if (base_B == SP_AUTOTUNE) {
+        for (int pref : {8, 16}) {
+            std::vector<int> Bs(g->n_sims);
+            bool ok = true;
+            for (int s = 0; s < g->n_sims && ok; ++s) {
+                Bs[s] = choose_B(g->p[s], pref);
+                if (Bs[s] < 0) Bs[s] = choose_B(g->p[s], 8);
+                ok = Bs[s] > 0;
+            }
+            if (ok && std::find(policies.begin(), policies.end(), Bs) == policies.end()) policies.push_back(Bs);
+        }
+    } else {
+        std::vector<int> Bs(g->n_sims);
+        for (int s = 0; s < g->n_sims; ++s) {
+            Bs[s] = choose_B(g->p[s], base_B);
+            if (Bs[s] < 0) return SP_EINVAL;
+        }
+        policies.push_back(Bs);
+    }
+    if (policies.empty()) return SP_EINVAL;
+
+    // trial grids: copies (or leading parts) of each simulation's state
+    std::vector<sp_params> tp = g->p;
+    for (auto &p : tp) {
+        for (int d = 0; d < 3; ++d) p.n[d] = trial_side(p.n[d]);
+        p.damp_steps = 0;
+    }
+    sp_grid *t = nullptr;
+    int rc = sp_grid_create(tp.data(), g->n_sims, nullptr, g->stream, &t);
+    if (rc != SP_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < g->n_sims && e == cudaSuccess; ++s) {
+        const size_t sites = (size_t)sites_of(tp[s]);
+        e = cudaMemcpyAsync(t->phi[s], g->phi[s], sites * sizeof(float2), cudaMemcpyDeviceToDevice, g->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(t->pc[s], g->pc[s], sites * sizeof(float4), cudaMemcpyDeviceToDevice, g->stream);
+    }
+    if (e != cudaSuccess) {
+        sp_destroy(t);
+        return SP_ECUDA;
+    }
+    constexpr int kTrialSteps = 16;
+    float best = 0.0f;
+    bool have = false;
+    for (const auto &Bs : policies) {
+        const int maxB = *std::max_element(Bs.begin(), Bs.end());
+        std::vector<int> shapes;
+        if (block_shape != SP_AUTOTUNE)
+            shapes.push_back(block_shape ? block_shape : default_threads(maxB));
+        else if (maxB <= 8)
+            shapes = {128, 256};
+        else
+            shapes = {256, 480, 512};
+        for (int nt : shapes) {
+            rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr);
+            if (rc == SP_EINVAL) continue;  // does not fit this device
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && rc == SP_OK; ++rep) {
+                rc = sp_evolve(t, kTrialSteps, SP_RESTART | SP_TIMING);
+                float m = 0.0f;
+                if (rc == SP_OK && cudaEventElapsedTime(&m, t->ev[0], t->ev[3]) != cudaSuccess) rc = SP_ECUDA;
+                if (rep == 1 || (rep == 2 && m < ms)) ms = m;
+            }
+            if (rc != SP_OK) {
+                sp_destroy(t);
+                return rc;
+            }
+            ++g->tune.candidates;
+            const bool is_default = Bs == policies.back() && nt == default_threads(maxB);
+            if (is_default) g->tune.default_ms = ms;
+            if (!have || ms < best) {
+                best = ms;
+                have = true;
+                *best_B = Bs;
+                *best_threads = nt;
+            }
+        }
+    }
+    sp_destroy(t);
+    if (!have) return SP_EINVAL;
+    g->tune.autotuned = 1;
+    g->tune.best_ms = best;
+    g->tune.trial_steps = kTrialSteps;
+    return SP_OK;
 }
 
 }  // namespace
@@ -502,56 +756,23 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
 
 int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t order, const char *model_path)
 {
-    (void)model_path;
     if (!g) return SP_EINVAL;
-    if (base_B != 0 && (base_B % 2 != 0 || base_B < 4 || base_B > 16)) return SP_EINVAL;
-    if (block_shape != 0 && block_shape != 128 && block_shape != 256 && block_shape != 480 && block_shape != 512 &&
-        block_shape != 768)
-        return SP_EINVAL;
+    if (base_B != 0 && base_B != SP_AUTOTUNE && (base_B % 2 != 0 || base_B < 4 || base_B > 16)) return SP_EINVAL;
+    if (block_shape != 0 && block_shape != SP_AUTOTUNE && !valid_threads(block_shape)) return SP_EINVAL;
     if (order != SP_ORDER_STATIC && order != SP_ORDER_LEARNED) return SP_EINVAL;
-    free_plan(g);
-    g->B.assign(g->n_sims, 0);
-    g->max_B = 0;
-    for (int s = 0; s < g->n_sims; ++s) {
-        int B = choose_B(g->p[s], base_B);
-        if (B < 0) return SP_EINVAL;
-        g->B[s] = B;
-        g->max_B = std::max(g->max_B, B);
-        int rc = build_device_tables(g, B);
+    g->tune = TuneReport();
+    std::vector<int> Bs(g->n_sims);
+    int threads = block_shape;
+    if (base_B == SP_AUTOTUNE || block_shape == SP_AUTOTUNE) {
+        const int rc = autotune(g, base_B, block_shape, &Bs, &threads);
         if (rc != SP_OK) return rc;
-    }
-    int rct = upload_table_array(g);
-    if (rct != SP_OK) return rct;
-    g->threads = block_shape ? block_shape : default_threads(g->max_B);
-    g->smem = sp::region_smem_bytes(g->max_B, g->n_tabs, g->n_sims, g->imp_smem_units);
-    if (g->smem > 227 * 1024) return SP_EINVAL;
-    cudaError_t e = sp::region_occupancy(g->threads, g->smem, &g->ctas_per_sm);
-    if (e != cudaSuccess || g->ctas_per_sm < 1) return SP_EINVAL;
-    g->grid = g->ctas_per_sm * g->sm_count;
-    g->order = order;
-    // mailbox ring: two band slots per simulation
-    g->mb_slot.assign(g->n_sims, 0);
-    g->mb_type_off.assign(g->n_sims, {});
-    for (int s = 0; s < g->n_sims; ++s) {
-        const sp::TileTables &t = g->tables[g->B[s]].host;
-        long long J = 1;
-        for (int d = 0; d < 3; ++d) J *= g->p[s].n[d] / g->B[s];
-        long long off = 0;
-        for (int S = 0; S < sp::kTypes; ++S) {
-            g->mb_type_off[s][S] = off;
-            off += J * t.mb_size[S];
+    } else {
+        for (int s = 0; s < g->n_sims; ++s) {
+            Bs[s] = choose_B(g->p[s], base_B);
+            if (Bs[s] < 0) return SP_EINVAL;
         }
-        g->mb_slot[s] = off;
-        float2 *m = nullptr;
-        e = cudaMalloc((void **)&m, std::max<size_t>(2 * off * sizeof(float2), 16));
-        if (e != cudaSuccess) {
-            free_plan(g);
-            return SP_ENOMEM;
-        }
-        g->mbox.push_back(m);
     }
-    g->planned = true;
-    return SP_OK;
+    return plan_fixed(g, Bs, threads, order, model_path);
 }
 
 int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
@@ -598,6 +819,8 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             rc = sweep_steps(g, s, n_steps, 0, g->d_coef + (size_t)s * n_steps);
     } else {
         // whole bands as regions, in one persistent launch over all simulations
+        sp::RegionArgs launch;
+        bool have_region = false;
         std::vector<sp::SimDev> sims;
         std::vector<int> sim_of;
         unsigned total = 0, seeds = 0;
@@ -661,6 +884,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
                 g->up_limit = lim;
             }
             sp::RegionArgs a;
+            std::memset(&a, 0, sizeof a);  // padding too: the bytes are a graph key
             a.sims = g->d_sims;
             a.tabs = g->d_tabs;
             a.n_tabs = g->n_tabs;
@@ -672,22 +896,19 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             a.ctl = g->d_ctl;
             a.trace = trace ? g->d_trace : nullptr;
             g->last_traced = trace;
-            e = sp::launch_reset(a, g->stream);
-            if (e == cudaSuccess && timing) e = cudaEventRecord(g->ev[1], g->stream);
-            if (e == cudaSuccess) e = sp::launch_region(a, g->threads, g->max_B, g->smem, g->grid, g->stream);
-            if (e == cudaSuccess && timing) e = cudaEventRecord(g->ev[2], g->stream);
-            if (e != cudaSuccess) return SP_ECUDA;
-        } else if (timing) {
-            e = cudaEventRecord(g->ev[1], g->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(g->ev[2], g->stream);
-            if (e != cudaSuccess) return SP_ECUDA;
+            launch = a;
         }
+        have_region = !sims.empty();
         // remainder steps of each simulation: whole-grid steps, same arithmetic
-        for (int s = 0; s < g->n_sims && rc == SP_OK; ++s) {
+        for (int s = 0; s < g->n_sims; ++s) {
             const int H = g->B[s] / 2;
             const int64_t done = (n_steps / H) * H;
-            rc = sweep_steps(g, s, n_steps - done, done, g->d_coef + (size_t)s * n_steps);
+            if (n_steps - done > 0) {
+                e = grow(&g->d_tmp, &g->cap_tmp, (size_t)sites_of(g->p[s]));
+                if (e != cudaSuccess) return SP_ENOMEM;
+            }
         }
+        rc = run_region_call(g, have_region ? &launch : nullptr, n_steps, timing);
     }
     if (rc != SP_OK) return rc;
     if (timing) {
@@ -805,6 +1026,10 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         info.bytes_written_per_band = ps.bytes_written_per_band;
         info.bytes_per_update = ps.bytes_per_update;
         info.mailbox_bytes = 2 * g->mb_slot[sim] * (int64_t)sizeof(float2);
+        info.autotuned = g->tune.autotuned;
+        info.tune_candidates = g->tune.candidates;
+        info.tune_best_ms = g->tune.best_ms;
+        info.tune_default_ms = g->tune.default_ms;
         if (dst_is_device) e = cudaMemcpy(dst, &info, sizeof info, cudaMemcpyHostToDevice);
         else std::memcpy(dst, &info, sizeof info);
         return cuda_err(e);
@@ -854,6 +1079,7 @@ int sp_destroy(sp_grid *g)
     cudaFree(g->d_wcount);
     cudaFree(g->d_wind);
     if (g->sweep_graph.exec) cudaGraphExecDestroy(g->sweep_graph.exec);
+    if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);
     for (int i = 0; i < 4; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     delete g;

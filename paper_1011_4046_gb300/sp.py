@@ -46,6 +46,7 @@ SP_SURF_WINDING = 3
 SP_SURF_PLAN = 4
 SP_SURF_TIMING = 5
 
+SP_AUTOTUNE = -1
 SP_ORDER_STATIC = 0
 SP_ORDER_LEARNED = 1
 
@@ -93,6 +94,10 @@ class sp_plan_info(ctypes.Structure):
         ("bytes_written_per_band", ctypes.c_int64),
         ("bytes_per_update", ctypes.c_double),
         ("mailbox_bytes", ctypes.c_int64),
+        ("autotuned", ctypes.c_int32),
+        ("tune_candidates", ctypes.c_int32),
+        ("tune_best_ms", ctypes.c_double),
+        ("tune_default_ms", ctypes.c_double),
     ]
 
 
