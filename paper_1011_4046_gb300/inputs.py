@@ -120,3 +120,35 @@ def batched_workload(n_sims: int = 64, lo: int = 48, hi: int = 160, step: int = 
         nu = int(min(int(u[1] * 3), 2))
         out.append((i, n, nu))
     return out
+
+
+# ---------------------------------------------------------------- cost model
+MLP_LAYERS = ((64, 16), (64, 64), (1, 64))  # (fan_out, fan_in) of W1, W2, W3
+MLP_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """He-uniform initial parameters of the 16-64-64-1 cost network, float32.
+
+    Flat layout W1 [64][16], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1];
+    parameter k draws uniform number k of the stream ``seed``: a weight of a
+    layer with fan-in f is (2u - 1) * sqrt(6 / f), computed in FP64 and
+    rounded to FP32 once; biases are 0."""
+    u = uniform01(seed, np.arange(MLP_PARAMS, dtype=np.uint64))
+    out = np.zeros(MLP_PARAMS, dtype=np.float64)
+    o = 0
+    for fan_out, fan_in in MLP_LAYERS:
+        n = fan_out * fan_in
+        out[o:o + n] = (2.0 * u[o:o + n] - 1.0) * np.sqrt(6.0 / fan_in)
+        o += n + fan_out  # the biases stay 0
+    return out.astype(np.float32)
+
+
+def epoch_orders(seed: int, n: int, epochs: int) -> list:
+    """Sample order of each training epoch: the stable argsort of n uniforms,
+    epoch e using counters 2**42 + e * 2**32 + i of the stream ``seed``."""
+    out = []
+    for e in range(epochs):
+        c = np.uint64(2 ** 42 + e * 2 ** 32) + np.arange(n, dtype=np.uint64)
+        out.append(np.argsort(uniform01(seed, c), kind="stable").astype(np.int32))
+    return out
