@@ -60,6 +60,7 @@ extern "C" {
 #define SP_RESTART 4u    /* treat the current state as level 0 (tau = tau0) */
 #define SP_TRACE 8u      /* record (start, end) globaltimer ns of every region (SP_SURF_TRACE) */
 #define SP_TIMING 16u    /* record CUDA events around each launch of the call (SP_SURF_TIMING) */
+#define SP_FEATURES 32u  /* compute the cost-model features of every region of the call (SP_SURF_FEATURES) */
 
 /* ---- what of sp_read_surface / sp_write_surface ---- */
 #define SP_SURF_STATE 0   /* phi (sites float2) then pic (sites float4): 24 * sites bytes */
@@ -69,6 +70,9 @@ extern "C" {
 #define SP_SURF_PLAN 4    /* one sp_plan_info */
 #define SP_SURF_TIMING 5  /* double[3]: ms of the queue reset, the region kernel and the
                              remainder sweep of the last SP_TIMING call (events on the stream) */
+#define SP_SURF_FEATURES 6 /* float[regions][SP_MODEL_FEATURES]: cost-model inputs of the sim's regions
+                              in the last SP_FEATURES (or learned-order) call, in region-id order
+                              (the order of SP_SURF_TRACE) */
 
 /* ---- sp_region_plan: base_B / block_shape chosen by measurement ---- */
 #define SP_AUTOTUNE (-1)
@@ -76,6 +80,11 @@ extern "C" {
 /* ---- region ordering of sp_region_plan ---- */
 #define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
 #define SP_ORDER_LEARNED 1 /* cost-model priority (results are identical) */
+
+/* ---- region cost model ---- */
+#define SP_MODEL_FEATURES 16
+#define SP_MODEL_PARAMS 5313 /* W1[64][16] b1[64] W2[64][64] b2[64] W3[64] b3[1], FP32 */
+typedef struct sp_model sp_model; /* opaque */
 
 typedef struct sp_grid sp_grid; /* opaque */
 
@@ -153,8 +162,12 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *                The autotuner runs 16-step calls on scratch copies of the
  *                current state (sides above 128 cells are cut to 128 or 120),
  *                on the grid's stream; the state itself is not modified.
- *   order      : SP_ORDER_STATIC or SP_ORDER_LEARNED.
- *   model_path : cost-model weights for SP_ORDER_LEARNED, or NULL.
+ *   order      : SP_ORDER_STATIC (ready regions are popped in the order they
+ *                became ready) or SP_ORDER_LEARNED (each call predicts every
+ *                region's cost from its features with the model at
+ *                model_path and pops the predicted-expensive quarter first,
+ *                then the next quarter, ...).  The order never changes results.
+ *   model_path : file written by sp_model_save; required for SP_ORDER_LEARNED.
  * Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA.
  */
 int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t order, const char *model_path);
@@ -187,6 +200,46 @@ int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size
  * Enqueued on the grid's stream.  Errors: SP_EINVAL, SP_ECUDA.
  */
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device);
+
+/*
+ * Region cost model (paper Sec. 4: the manager issues regions so that the
+ * expensive ones do not finish last).  A 16-64-64-1 ReLU network in FP32
+ * predicting log(region time in microseconds) from the 16 features that
+ * SP_FEATURES records (SP_SURF_FEATURES); trained on the GPU by minibatch
+ * Adam (beta 0.9 / 0.999, eps 1e-8) on the mean squared error.
+ *
+ * sp_model_create  -- He-uniform weights from seed (weight k: SplitMix64
+ *                     output k of the stream at seed, (2u-1) sqrt(6/fan_in)),
+ *                     zero biases; work goes to cuda_stream.
+ * sp_model_get_params / sp_model_set_params -- SP_MODEL_PARAMS floats (host),
+ *                     and optionally the 3 bucket thresholds (non-increasing).
+ *                     Setting parameters resets the Adam state.
+ * sp_model_predict -- y_dev[i] = network(x_dev[16 i .. 16 i + 15]) (device).
+ * sp_model_grad    -- gradient (host, SP_MODEL_PARAMS floats) and loss of the
+ *                     mean squared error over n samples (device x, y).
+ * sp_model_adam_step -- one Adam step with the given gradient (host).
+ * sp_model_train   -- epochs x ceil(n / batch) Adam steps on minibatches in
+ *                     the order order_host (epochs * n sample indices), or,
+ *                     when it is NULL, per epoch e the stable argsort of
+ *                     uniforms 2^42 + e 2^32 + i of the stream order_seed.
+ *                     losses_host (optional) receives each minibatch's loss
+ *                     before its step.  Afterwards the bucket thresholds are
+ *                     set to the 75th, 50th and 25th percentiles of the
+ *                     network's predictions on the training set.
+ * sp_model_save / sp_model_load -- parameters and thresholds in a file.
+ * All synchronise the model's stream.  Errors: SP_EINVAL, SP_ENOMEM, SP_ECUDA.
+ */
+int sp_model_create(uint64_t seed, void *cuda_stream, sp_model **out);
+int sp_model_destroy(sp_model *m);
+int sp_model_get_params(sp_model *m, float *params_host, float *thresholds_host);
+int sp_model_set_params(sp_model *m, const float *params_host, const float *thresholds_host);
+int sp_model_predict(sp_model *m, const float *x_dev, int64_t n, float *y_dev);
+int sp_model_grad(sp_model *m, const float *x_dev, const float *y_dev, int64_t n, float *grad_host, double *loss);
+int sp_model_adam_step(sp_model *m, const float *grad_host, float lr, float beta1, float beta2, float eps);
+int sp_model_train(sp_model *m, const float *x_dev, const float *y_dev, int64_t n, int32_t epochs, int32_t batch,
+                   float lr, uint64_t order_seed, const int32_t *order_host, float *losses_host);
+int sp_model_save(sp_model *m, const char *path);
+int sp_model_load(const char *path, void *cuda_stream, sp_model **out);
 
 /*
  * sp_sweep_noalloc -- advance one simulation by n_steps whole-grid leapfrog

@@ -20,6 +20,10 @@
 #include "sp_device.cuh"
 #include "sp_kernels.h"
 
+namespace sp {
+cudaError_t model_buckets(const sp_model *m, const float *X, long long n, unsigned char *prio, cudaStream_t st);
+}
+
 namespace {
 
 struct TablesOnDevice {
@@ -171,6 +175,18 @@ struct sp_grid {
     SweepGraph sweep_graph;
     RegionGraph region_graph;
     TuneReport tune;
+    // learned ordering and cost-model features
+    sp_model *model = nullptr;
+    float *d_feat = nullptr;
+    size_t cap_feat = 0;
+    float4 *d_simf = nullptr;
+    size_t cap_simf = 0;
+    unsigned char *d_prio = nullptr;
+    size_t cap_prio = 0;
+    bool last_features = false;
+    unsigned last_total = 0;
+    unsigned trace_total = 0;    // regions of the last traced call (its trace is still in d_trace)
+    bool prev_trace_ok = false;  // this call's features may read d_trace
     int use_graphs = 1;  // capture launch sequences on non-legacy streams
     unsigned long long wait_limit_ns = 2000000000ull;
     // what is already on the device (uploads are skipped when unchanged)
@@ -441,7 +457,7 @@ int sweep_steps(sp_grid *g, int s, int64_t nsteps, int64_t first_local, const sp
 // The launches of one region-path call: reset + persistent region kernel over
 // all simulations' whole bands, then each simulation's remainder steps as
 // whole-grid steps.  Timing events 1 and 2 bracket the region kernel.
-int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool capturing)
+int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool feats, bool capturing)
 {
     cudaError_t e = cudaSuccess;
     auto mark = [&](cudaEvent_t ev) {
@@ -450,7 +466,13 @@ int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bo
                           : cudaEventRecord(ev, g->stream);
     };
     if (a) {
-        e = sp::launch_reset(*a, g->stream);
+        if (feats) {
+            // the previous call's trace feeds feature 15 when it covered the same regions
+            const unsigned long long *prev = g->prev_trace_ok ? g->d_trace : nullptr;
+            e = sp::launch_features(*a, g->d_simf, prev, g->d_feat, g->stream);
+            if (e == cudaSuccess && a->prio) e = sp::model_buckets(g->model, g->d_feat, a->total, g->d_prio, g->stream);
+        }
+        if (e == cudaSuccess) e = sp::launch_reset(*a, g->stream);
         if (timing) mark(g->ev[1]);
         if (e == cudaSuccess) e = sp::launch_region(*a, g->threads, g->max_B, g->smem, g->grid, g->stream);
         if (timing) mark(g->ev[2]);
@@ -472,12 +494,17 @@ int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bo
 // Runs the region-path call.  On a capturable stream the launch sequence is
 // recorded once into a CUDA graph and replayed while every by-value launch
 // parameter is unchanged, so a repeated call costs one graph launch.
-int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing)
+int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool feats)
 {
-    if (g->stream == nullptr || !g->use_graphs) return enqueue_region_call(g, a, n_steps, timing, false);
+    if (g->stream == nullptr || !g->use_graphs) return enqueue_region_call(g, a, n_steps, timing, feats, false);
     std::vector<unsigned char> key;
     append_key(&key, n_steps);
     append_key(&key, timing);
+    append_key(&key, feats);
+    append_key(&key, g->d_feat);
+    append_key(&key, g->d_simf);
+    append_key(&key, g->d_prio);
+    append_key(&key, g->prev_trace_ok);
     append_key(&key, a != nullptr);
     if (a) append_key(&key, *a);
     append_key(&key, g->threads);
@@ -499,7 +526,7 @@ int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool t
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return SP_ECUDA;
-        const int rc = enqueue_region_call(g, a, n_steps, timing, true);
+        const int rc = enqueue_region_call(g, a, n_steps, timing, feats, true);
         e = cudaStreamEndCapture(g->stream, &graph);
         if (rc != SP_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -522,8 +549,14 @@ bool valid_threads(int t) { return t == 128 || t == 256 || t == 480 || t == 512 
 // count (0 = default for the largest base).
 int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, const char *model_path)
 {
-    (void)model_path;
     free_plan(g);
+    if (g->model) sp_model_destroy(g->model);
+    g->model = nullptr;
+    if (order == SP_ORDER_LEARNED) {
+        if (!model_path) return SP_EINVAL;
+        const int rc = sp_model_load(model_path, g->stream, &g->model);
+        if (rc != SP_OK) return rc;
+    }
     g->B = Bs;
     g->max_B = 0;
     for (int s = 0; s < g->n_sims; ++s) {
@@ -778,7 +811,7 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
 {
     if (!g || n_steps < 0) return SP_EINVAL;
-    if (flags & ~(SP_ASYNC | SP_MONOLITHIC | SP_RESTART | SP_TRACE | SP_TIMING)) return SP_EINVAL;
+    if (flags & ~(SP_ASYNC | SP_MONOLITHIC | SP_RESTART | SP_TRACE | SP_TIMING | SP_FEATURES)) return SP_EINVAL;
     const bool timing = (flags & SP_TIMING) != 0;
     if (timing && !g->ev[0])
         for (int i = 0; i < 4; ++i)
@@ -820,7 +853,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
     } else {
         // whole bands as regions, in one persistent launch over all simulations
         sp::RegionArgs launch;
-        bool have_region = false;
+        bool have_region = false, feats = false, prev_trace_ok = false;
         std::vector<sp::SimDev> sims;
         std::vector<int> sim_of;
         unsigned total = 0, seeds = 0;
@@ -866,10 +899,26 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
         if (!sims.empty()) {
             e = grow(&g->d_sims, &g->cap_sims, sims.size());
             if (e == cudaSuccess) e = grow(&g->d_counters, &g->cap_counters, total);
+            const bool learned = g->order == SP_ORDER_LEARNED && g->model;
+            feats = learned || (flags & SP_FEATURES) != 0;
             if (e == cudaSuccess) e = grow(&g->d_queue, &g->cap_queue, total);
             const bool trace = (flags & SP_TRACE) != 0;
             if (e == cudaSuccess && trace) e = grow(&g->d_trace, &g->cap_trace, 2 * (size_t)total);
+            if (e == cudaSuccess && feats) e = grow(&g->d_feat, &g->cap_feat, (size_t)SP_MODEL_FEATURES * total);
+            if (e == cudaSuccess && feats) e = grow(&g->d_simf, &g->cap_simf, sims.size());
+            if (e == cudaSuccess && learned) e = grow(&g->d_prio, &g->cap_prio, (size_t)total);
             if (e != cudaSuccess) return SP_ENOMEM;
+            if (feats) {
+                std::vector<float4> simf(sims.size());
+                for (size_t i = 0; i < sims.size(); ++i) {
+                    const sp_params &pp = g->p[sim_of[i]];
+                    simf[i] = make_float4((float)g->B[sim_of[i]] / 16.0f, (float)(std::log2((double)sites_of(pp)) / 24.0),
+                                          (float)(pp.nu / 2.0), 0.0f);
+                }
+                e = cudaMemcpyAsync(g->d_simf, simf.data(), simf.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                                    g->stream);
+                if (e != cudaSuccess) return SP_ECUDA;
+            }
             if (sims.size() != g->up_sims.size() ||
                 std::memcmp(sims.data(), g->up_sims.data(), sims.size() * sizeof(sp::SimDev)) != 0) {
                 e = cudaMemcpyAsync(g->d_sims, sims.data(), sims.size() * sizeof(sp::SimDev),
@@ -895,7 +944,12 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             a.queue = g->d_queue;
             a.ctl = g->d_ctl;
             a.trace = trace ? g->d_trace : nullptr;
+            a.prio = learned ? g->d_prio : nullptr;
+            prev_trace_ok = g->trace_total == total;  // the trace buffer still holds a call of this layout
+            if (trace) g->trace_total = total;
             g->last_traced = trace;
+            g->last_features = feats;
+            g->last_total = total;
             launch = a;
         }
         have_region = !sims.empty();
@@ -908,7 +962,8 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
                 if (e != cudaSuccess) return SP_ENOMEM;
             }
         }
-        rc = run_region_call(g, have_region ? &launch : nullptr, n_steps, timing);
+        g->prev_trace_ok = prev_trace_ok;
+        rc = run_region_call(g, have_region ? &launch : nullptr, n_steps, timing, feats);
     }
     if (rc != SP_OK) return rc;
     if (timing) {
@@ -1034,6 +1089,15 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         else std::memcpy(dst, &info, sizeof info);
         return cuda_err(e);
     }
+    case SP_SURF_FEATURES: {
+        if (!g->last_features || sim >= (int)g->last_tiles.size()) return SP_EINVAL;
+        const size_t bytes = (size_t)g->last_tiles[sim] * SP_MODEL_FEATURES * sizeof(float);
+        if (dst_bytes < bytes) return SP_EINVAL;
+        e = cudaMemcpyAsync(dst, g->d_feat + (size_t)g->last_tile_base[sim] * SP_MODEL_FEATURES, bytes,
+                            dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        return cuda_err(e);
+    }
     case SP_SURF_TIMING: {
         if (!g->timed || dst_bytes < 3 * sizeof(double) || dst_is_device) return SP_EINVAL;
         e = cudaEventSynchronize(g->ev[3]);
@@ -1078,6 +1142,10 @@ int sp_destroy(sp_grid *g)
     cudaFree(g->d_eout);
     cudaFree(g->d_wcount);
     cudaFree(g->d_wind);
+    cudaFree(g->d_feat);
+    cudaFree(g->d_simf);
+    cudaFree(g->d_prio);
+    if (g->model) sp_model_destroy(g->model);
     if (g->sweep_graph.exec) cudaGraphExecDestroy(g->sweep_graph.exec);
     if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);
     for (int i = 0; i < 4; ++i)

@@ -73,6 +73,9 @@ struct alignas(16) SimDev {
     int pad;
 };
 
+// Priority buckets of the learned ordering (bucket 0 is queued first).
+constexpr int kBuckets = 4;
+
 // Work-queue control block.
 struct Ctl {
     unsigned int head;   // next queue position to pop
@@ -82,6 +85,8 @@ struct Ctl {
     unsigned long long wait_limit_ns;  // per-wait bound for every spin
     unsigned int completed;            // regions finished
     unsigned int pad;
+    unsigned int bcount[kBuckets];     // learned ordering: band-0 seeds per bucket,
+    unsigned int bcursor[kBuckets];    // and the next free position of each bucket's run
 };
 
 struct RegionArgs {
@@ -95,6 +100,10 @@ struct RegionArgs {
     int *queue;      // ready regions in release order (-1 = not yet pushed)
     Ctl *ctl;
     unsigned long long *trace;  // optional (start, end) globaltimer per region
+    // Learned ordering: priority bucket of every region (0 first), or nullptr.
+    // With it the seeds are queued bucket by bucket and the successors that
+    // one finished region makes ready are pushed bucket by bucket.
+    const unsigned char *prio;
 };
 
 static_assert(sizeof(TablesDev) % 16 == 0, "tables are copied in 16-byte units");
@@ -116,6 +125,20 @@ __device__ __forceinline__ int ld_acquire_gpu(const int *p)
 {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu_u(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_gpu_u(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 

@@ -37,6 +37,20 @@ __device__ __forceinline__ int wrap_axis(int p, int n)
 }
 
 // ------------------------------------------------------------ queue reset
+// Region id of the t-th band-0 pyramid of the launch (t < n_seed).
+__device__ __forceinline__ int seed_region(const RegionArgs &a, unsigned t)
+{
+    int lo = 0, hi = a.n_sims - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.sims[mid].seed_base <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return (int)(a.sims[lo].tile_base + (t - a.sims[lo].seed_base));
+}
+
 __global__ void reset_kernel(RegionArgs a)
 {
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,6 +60,10 @@ __global__ void reset_kernel(RegionArgs a)
         a.ctl->error = 0;
         a.ctl->error_info = 0;
         a.ctl->completed = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+            a.ctl->bcount[b] = 0;
+            a.ctl->bcursor[b] = 0;
+        }
     }
     if (t >= a.total) return;
     const int s = find_sim(a, t);
@@ -57,19 +75,28 @@ __global__ void reset_kernel(RegionArgs a)
     const int S = (int)((local - band * per_band) / (unsigned)sd.Jtot);
     a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds : 0);
     // queue position t: the first n_seed positions hold the band-0 pyramids
-    int v = -1;
-    if (t < a.n_seed) {
-        int lo = 0, hi = a.n_sims - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (a.sims[mid].seed_base <= t)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        v = (int)(a.sims[lo].tile_base + (t - a.sims[lo].seed_base));
-    }
-    a.queue[t] = v;
+    // (with the learned ordering seed_kernel writes them, bucket by bucket)
+    a.queue[t] = (t < a.n_seed && !a.prio) ? seed_region(a, t) : -1;
+}
+
+// Learned ordering: band-0 pyramids per bucket (after reset_kernel zeroed the counts).
+__global__ void seed_count_kernel(RegionArgs a)
+{
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.n_seed) atomicAdd(&a.ctl->bcount[a.prio[seed_region(a, t)]], 1u);
+}
+
+// Learned ordering: the band-0 pyramids in queue positions [0, n_seed),
+// bucket 0 first (order within a bucket is immaterial).
+__global__ void seed_kernel(RegionArgs a)
+{
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_seed) return;
+    const int v = seed_region(a, t);
+    const int b = a.prio[v];
+    unsigned base = 0;
+    for (int q = 0; q < b; ++q) base += a.ctl->bcount[q];
+    a.queue[base + atomicAdd(&a.ctl->bcursor[b], 1u)] = v;
 }
 
 // Region descriptor decoded from a launch-global region id.
@@ -115,6 +142,8 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
     __threadfence();
     const int n_same = T.type[r.S].n_same_succ;
     const int n_next = (r.S == kTypes - 1 && r.band + 1 < sd.nbands) ? kMaxNextSucc : 0;
+    bool ready = false;
+    int region = -1;
     if (lane < n_same + n_next) {
         Succ su;
         int nb;
@@ -135,9 +164,22 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
         }
         const unsigned t = sd.tile_base + (unsigned)((nb * 8 + su.type) * sd.Jtot + jc);
         const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
-        if (old == 1) {
+        ready = old == 1;
+        region = (int)t;
+        if (a.prio == nullptr && ready) {
             const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
             st_release_gpu(a.queue + pos, (int)t);
+        }
+    }
+    if (a.prio) {
+        // learned ordering: the successors made ready here are queued bucket by bucket
+        const int b = ready ? a.prio[region] : kBuckets;
+        for (int q = 0; q < kBuckets; ++q) {
+            if (b == q) {
+                const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
+                st_release_gpu(a.queue + pos, region);
+            }
+            __syncwarp();
         }
     }
     if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
@@ -690,10 +732,92 @@ __global__ void __launch_bounds__(kDiagThreads)
 }
 
 // ------------------------------------------------------------ launchers
+// ------------------------------------------------------------ region features
+// The 16 inputs of the region cost model, per region of a launch, from its
+// descriptor and from the state at the start of the call (the footprint of
+// the region's own cells, sampled on a 2 x 2 x 2 lattice):
+//   0-2  inverted axes of the region type (x, y, z);  3  |S| / 3 (phase);
+//   4    B / 16;  5  log2(sites) / 24;  6  nu / 2;  7  a^2 lambda at the band's
+//   first level;  8  band / bands;  9  (4 band + |S|) / (4 bands);
+//   10, 11  mean and max |phi|^2;  12  mean |pi|^2;  13  fraction of sampled
+//   xy plaquettes with nonzero winding;  14  mean |phi(x+1) - phi(x)|^2 / dx^2;
+//   15  the region's measured time in the previous traced call (us / 20), or 0.
+// simf[s] = (B / 16, log2(sites) / 24, nu / 2, 0) of simulation s.
+__global__ void __launch_bounds__(128) feature_kernel(RegionArgs a, const float4 *__restrict__ simf,
+                                                      const unsigned long long *__restrict__ prev_trace,
+                                                      float *__restrict__ X)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (int)a.total) return;
+    const RegionInfo r = decode_region(a.sims, a.n_sims, g);
+    const SimDev &sd = a.sims[r.sim];
+    const float4 sf = simf[r.sim];
+    const int S = r.S, B = sd.B, H = sd.H, nb = sd.nbands;
+    const int ns = (S & 1) + ((S >> 1) & 1) + ((S >> 2) & 1);
+    float f[16];
+    f[0] = (float)(S & 1);
+    f[1] = (float)((S >> 1) & 1);
+    f[2] = (float)((S >> 2) & 1);
+    f[3] = ns / 3.0f;
+    f[4] = sf.x;
+    f[5] = sf.y;
+    f[6] = sf.z;
+    f[7] = sd.coef[r.band * H].m;
+    f[8] = (float)r.band / (float)nb;
+    f[9] = (float)(4 * r.band + ns) / (float)(4 * nb);
+    int gb[3];
+    for (int d = 0; d < 3; ++d) gb[d] = (r.band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
+    const int nx = sd.n[0], ny = sd.n[1], nz = sd.n[2];
+    const int stride = B / 2;
+    double sphi = 0.0, spi = 0.0, sgrad = 0.0;
+    float mphi = 0.0f;
+    int pierced = 0;
+    for (int m = 0; m < 8; ++m) {
+        const int x = wrap_axis(gb[0] + 1 + stride * (m & 1), nx);
+        const int y = wrap_axis(gb[1] + 1 + stride * ((m >> 1) & 1), ny);
+        const int z = wrap_axis(gb[2] + 1 + stride * (m >> 2), nz);
+        const int x1 = x + 1 == nx ? 0 : x + 1, y1 = y + 1 == ny ? 0 : y + 1;
+        const long long row = (long long)nx * (y + (long long)ny * z), row1 = (long long)nx * (y1 + (long long)ny * z);
+        const float2 p0 = sd.phi[row + x], p1 = sd.phi[row + x1], p2 = sd.phi[row1 + x1], p3 = sd.phi[row1 + x];
+        const float4 pc = sd.pc[row + x];
+        const float a2 = p0.x * p0.x + p0.y * p0.y;
+        sphi += a2;
+        mphi = fmaxf(mphi, a2);
+        spi += (double)(pc.x * pc.x + pc.y * pc.y);
+        const float dx = p1.x - p0.x, dy = p1.y - p0.y;
+        sgrad += (double)(dx * dx + dy * dy);
+        pierced += (crossing(p0, p1) + crossing(p1, p2) + crossing(p2, p3) + crossing(p3, p0)) != 0;
+    }
+    f[10] = (float)(sphi / 8.0);
+    f[11] = mphi;
+    f[12] = (float)(spi / 8.0);
+    f[13] = pierced / 8.0f;
+    f[14] = (float)(sgrad / 8.0) * sd.q.inv_dx2;
+    f[15] = 0.0f;
+    if (prev_trace) {
+        const unsigned long long t0 = prev_trace[2 * (size_t)g], t1 = prev_trace[2 * (size_t)g + 1];
+        if (t1 > t0) f[15] = (float)((double)(t1 - t0) * 1e-3 / 20.0);
+    }
+    float4 *o = reinterpret_cast<float4 *>(X + 16 * (size_t)g);
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+}
+
+cudaError_t launch_features(const RegionArgs &a, const float4 *simf, const unsigned long long *prev_trace, float *X,
+                            cudaStream_t st)
+{
+    if (a.total == 0) return cudaSuccess;
+    feature_kernel<<<(a.total + 127) / 128, 128, 0, st>>>(a, simf, prev_trace, X);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st)
 {
     const unsigned blocks = (a.total + 255) / 256;
     reset_kernel<<<blocks ? blocks : 1, 256, 0, st>>>(a);
+    if (a.prio && a.n_seed > 0) {
+        seed_count_kernel<<<(a.n_seed + 255) / 256, 256, 0, st>>>(a);
+        seed_kernel<<<(a.n_seed + 255) / 256, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

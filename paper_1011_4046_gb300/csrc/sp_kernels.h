@@ -7,6 +7,9 @@
 namespace sp {
 
 cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st);
+// 16 cost-model features per region of the launch into X [total][16].
+cudaError_t launch_features(const RegionArgs &a, const float4 *simf, const unsigned long long *prev_trace, float *X,
+                            cudaStream_t st);
 size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units);
 cudaError_t region_occupancy(int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st);

@@ -38,6 +38,7 @@ SP_MONOLITHIC = 2
 SP_RESTART = 4
 SP_TRACE = 8
 SP_TIMING = 16
+SP_FEATURES = 32
 
 SP_SURF_STATE = 0
 SP_SURF_DIAG = 1
@@ -45,6 +46,9 @@ SP_SURF_TRACE = 2
 SP_SURF_WINDING = 3
 SP_SURF_PLAN = 4
 SP_SURF_TIMING = 5
+SP_SURF_FEATURES = 6
+SP_MODEL_FEATURES = 16
+SP_MODEL_PARAMS = 5313
 
 SP_AUTOTUNE = -1
 SP_ORDER_STATIC = 0
@@ -146,8 +150,22 @@ def load(build_if_missing: bool = False):
         lib.sp_sweep_noalloc.argtypes = [ctypes.POINTER(sp_params), vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
         lib.sp_strerror.argtypes = [ctypes.c_int]
         lib.sp_strerror.restype = ctypes.c_char_p
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.sp_model_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+        lib.sp_model_destroy.argtypes = [vp]
+        lib.sp_model_get_params.argtypes = [vp, fp, fp]
+        lib.sp_model_set_params.argtypes = [vp, fp, fp]
+        lib.sp_model_predict.argtypes = [vp, vp, ctypes.c_int64, vp]
+        lib.sp_model_grad.argtypes = [vp, vp, vp, ctypes.c_int64, fp, ctypes.POINTER(ctypes.c_double)]
+        lib.sp_model_adam_step.argtypes = [vp, fp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        lib.sp_model_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), fp]
+        lib.sp_model_save.argtypes = [vp, ctypes.c_char_p]
+        lib.sp_model_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
         for f in ("sp_grid_create", "sp_region_plan", "sp_evolve", "sp_read_surface", "sp_write_surface",
-                  "sp_destroy", "sp_sweep_noalloc"):
+                  "sp_destroy", "sp_sweep_noalloc", "sp_model_create", "sp_model_destroy", "sp_model_get_params",
+                  "sp_model_set_params", "sp_model_predict", "sp_model_grad", "sp_model_adam_step", "sp_model_train",
+                  "sp_model_save", "sp_model_load"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -226,6 +244,81 @@ def unpack_state(buf, shape):
     return phi, pic[:, 0].reshape(shape).copy(), pic[:, 1].reshape(shape).copy()
 
 
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Model:
+    """The region cost model (include/sp.h, sp_model_*): device parameters,
+    trained and evaluated by the library's kernels.  Inputs of predict, grad
+    and train are device addresses (e.g. torch tensors' data_ptr())."""
+
+    def __init__(self, seed=0, stream=None, path=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        lib = load()
+        if path is None:
+            rc = lib.sp_model_create(int(seed), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        else:
+            rc = lib.sp_model_load(str(path).encode(), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(rc, "sp_model_create")
+        self.h = h
+
+    def params(self):
+        p = np.empty(SP_MODEL_PARAMS, dtype=np.float32)
+        t = np.empty(3, dtype=np.float32)
+        _check(load().sp_model_get_params(self.h, _fptr(p), _fptr(t)), "sp_model_get_params")
+        return p, t
+
+    def set_params(self, params, thresholds=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        t = None if thresholds is None else np.ascontiguousarray(thresholds, dtype=np.float32)
+        _check(load().sp_model_set_params(self.h, _fptr(p), None if t is None else _fptr(t)), "sp_model_set_params")
+
+    def predict(self, x_ptr, n, y_ptr):
+        _check(load().sp_model_predict(self.h, ctypes.c_void_p(int(x_ptr)), int(n), ctypes.c_void_p(int(y_ptr))),
+               "sp_model_predict")
+
+    def grad(self, x_ptr, y_ptr, n):
+        g = np.empty(SP_MODEL_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load().sp_model_grad(self.h, ctypes.c_void_p(int(x_ptr)), ctypes.c_void_p(int(y_ptr)), int(n),
+                                    _fptr(g), ctypes.byref(loss)), "sp_model_grad")
+        return float(loss.value), g
+
+    def adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        _check(load().sp_model_adam_step(self.h, _fptr(g), lr, beta1, beta2, eps), "sp_model_adam_step")
+
+    def train(self, x_ptr, y_ptr, n, epochs, batch, lr=1e-3, order_seed=0, order=None):
+        steps = epochs * ((n + batch - 1) // batch)
+        losses = np.empty(steps, dtype=np.float32)
+        o = None
+        if order is not None:
+            o = np.ascontiguousarray(np.concatenate(order), dtype=np.int32)
+            o = o.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        _check(load().sp_model_train(self.h, ctypes.c_void_p(int(x_ptr)), ctypes.c_void_p(int(y_ptr)), int(n),
+                                     int(epochs), int(batch), float(lr), int(order_seed), o, _fptr(losses)),
+               "sp_model_train")
+        return losses
+
+    def save(self, path):
+        _check(load().sp_model_save(self.h, str(path).encode()), "sp_model_save")
+
+    def close(self):
+        if self.h:
+            load().sp_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _check(rc, what):
     if rc != SP_OK:
         raise SpError(rc, what)
@@ -295,6 +388,12 @@ class Grid:
         out = np.zeros(3, dtype=np.float64)
         _check(sp_read_surface(self.h, 0, SP_SURF_TIMING, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
         return tuple(out.tolist())
+
+    def features(self, sim, n_regions):
+        """Cost-model features [n_regions, 16] of the last SP_FEATURES call."""
+        out = np.empty((n_regions, SP_MODEL_FEATURES), dtype=np.float32)
+        _check(sp_read_surface(self.h, sim, SP_SURF_FEATURES, out.ctypes.data, out.nbytes, 0), "sp_read_surface")
+        return out
 
     def trace(self, sim, n_regions):
         out = np.empty((n_regions, 2), dtype=np.uint64)

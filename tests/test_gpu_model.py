@@ -1,0 +1,229 @@
+"""The region cost model on the GPU: its kernels against the FP64 oracle
+(oracle/mlp.py), and the learned ordering of the device queue.
+
+Bars:
+* initial parameters: bit-identical to the seeded input generator;
+* forward pass, gradient and Adam step (FP32, fixed summation order) against
+  the FP64 oracle on the same FP32 inputs: every entry within 1e-4 of the
+  largest magnitude of its kind plus 1e-4 relative (FP32 sums of up to a few
+  hundred terms stay near 1e-6 relative; 1e-4 leaves two orders of margin);
+* training: the per-minibatch losses of a short run track the oracle's run
+  from the same start within 1e-3 relative, and the host-generated and
+  library-generated minibatch orders give bit-identical parameters;
+* learned ordering: bit-identical fields to the static order; its measured
+  time is printed next to the static one (the gain it shows is reported,
+  and bench.py records it).
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp  # noqa: E402
+from paper_1011_4046_gb300 import inputs, sp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sp.load()
+
+
+def _data(seed, n):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.0, 1.0, (n, 16)).astype(np.float32)
+    y = (X @ rng.uniform(-1, 1, 16) + 0.3 * np.sin(3 * X[:, 0])).astype(np.float32)
+    return X, y
+
+
+def _close(got, ref, what, rtol=1e-4, scale_tol=1e-4):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    tol = scale_tol * np.max(np.abs(ref)) + rtol * np.abs(ref)
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), f"{what}: {bad.sum()} entries off, worst {np.max(np.abs(got - ref) - tol):.3e}"
+
+
+def test_initial_parameters_match_the_input_generator():
+    m = sp.Model(seed=5)
+    try:
+        p, _ = m.params()
+    finally:
+        m.close()
+    assert np.array_equal(p.view(np.uint32), inputs.mlp_init(5).view(np.uint32))
+
+
+def test_forward_matches_oracle():
+    theta = inputs.mlp_init(3) + np.float32(0.05) * np.random.default_rng(1).standard_normal(5313).astype(np.float32)
+    X, _ = _data(2, 1000)
+    m = sp.Model()
+    try:
+        m.set_params(theta)
+        xd = torch.from_numpy(X).cuda()
+        yd = torch.empty(len(X), dtype=torch.float32, device="cuda")
+        m.predict(xd.data_ptr(), len(X), yd.data_ptr())
+        got = yd.cpu().numpy()
+    finally:
+        m.close()
+    ref, _ = mlp.forward(theta.astype(np.float64), X.astype(np.float64))
+    _close(got, ref, "forward")
+
+
+@pytest.mark.parametrize("n", [1, 128, 300])
+def test_gradient_matches_oracle(n):
+    """n spans one sample, one full gradient block and a ragged third block."""
+    theta = inputs.mlp_init(8) + np.float32(0.05) * np.random.default_rng(2).standard_normal(5313).astype(np.float32)
+    X, y = _data(3, n)
+    m = sp.Model()
+    try:
+        m.set_params(theta)
+        xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+        loss, g = m.grad(xd.data_ptr(), yd.data_ptr(), n)
+    finally:
+        m.close()
+    ref_loss, ref_g = mlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss) + 1e-7
+    for name, sl in (("W1", slice(0, 1024)), ("b1", slice(1024, 1088)), ("W2", slice(1088, 5184)),
+                     ("b2", slice(5184, 5248)), ("W3", slice(5248, 5312)), ("b3", slice(5312, 5313))):
+        _close(g[sl], ref_g[sl], name)
+
+
+def test_adam_steps_match_oracle():
+    theta = inputs.mlp_init(9)
+    rng = np.random.default_rng(4)
+    m = sp.Model()
+    try:
+        m.set_params(theta)
+        ref = theta.astype(np.float64)
+        mm, vv = np.zeros(5313), np.zeros(5313)
+        for t in range(1, 4):
+            g = rng.standard_normal(5313).astype(np.float32)
+            m.adam_step(g, lr=1e-2)
+            ref, mm, vv = mlp.adam_step(ref, g.astype(np.float64), mm, vv, t, lr=1e-2)
+        got, _ = m.params()
+    finally:
+        m.close()
+    _close(got, ref, "theta after 3 Adam steps", rtol=1e-5, scale_tol=1e-6)
+
+
+def test_training_tracks_oracle_and_orders_agree():
+    X, y = _data(6, 256)
+    theta = inputs.mlp_init(12)
+    order = inputs.epoch_orders(12, len(y), 3)
+    xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    runs = []
+    for explicit in (True, False):
+        m = sp.Model()
+        try:
+            m.set_params(theta)
+            losses = m.train(xd.data_ptr(), yd.data_ptr(), len(y), epochs=3, batch=32, lr=3e-3, order_seed=12,
+                             order=order if explicit else None)
+            runs.append((losses, m.params()[0]))
+        finally:
+            m.close()
+    assert np.array_equal(runs[0][1].view(np.uint32), runs[1][1].view(np.uint32))
+    assert np.array_equal(runs[0][0].view(np.uint32), runs[1][0].view(np.uint32))
+    ref_theta, ref_losses = mlp.train(theta, X, y, order, batch=32, lr=3e-3)
+    assert np.allclose(runs[0][0], ref_losses, rtol=1e-3, atol=1e-6)
+    _close(runs[0][1], ref_theta, "theta after training", rtol=1e-3, scale_tol=1e-4)
+
+
+def test_save_load_roundtrip(tmp_path):
+    X, y = _data(7, 200)
+    xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    m = sp.Model(seed=2)
+    try:
+        m.train(xd.data_ptr(), yd.data_ptr(), len(y), epochs=2, batch=50)
+        p, t = m.params()
+        m.save(tmp_path / "model.bin")
+    finally:
+        m.close()
+    m2 = sp.Model(path=tmp_path / "model.bin")
+    try:
+        p2, t2 = m2.params()
+    finally:
+        m2.close()
+    assert np.array_equal(p, p2) and np.array_equal(t, t2)
+    assert t[0] >= t[1] >= t[2]
+
+
+# ------------------------------------------------------------ learned ordering
+def _region_samples(g, info, steps):
+    """(features, log region time in us) of every region of the last call."""
+    nreg = info["regions_per_band"] * (steps // (info["base_B"] // 2))
+    f = g.features(0, nreg)
+    tr = g.trace(0, nreg).astype(np.int64)
+    us = np.maximum(tr[:, 1] - tr[:, 0], 1) / 1e3
+    return f, np.log(us).astype(np.float32)
+
+
+def test_learned_order_is_bit_identical_and_timed(tmp_path):
+    """Train the network on measured region times of the plain-method and
+    128^3 matter-era workloads (features from SP_FEATURES, times from
+    SP_TRACE), then evolve the 128^3 workload in static and in learned order:
+    the fields are bit-identical; both times are printed."""
+    s = torch.cuda.Stream()
+    Xs, ys = [], []
+    with torch.cuda.stream(s):
+        for n, nu, B, steps, kind in ((32, 0.0, 8, 64, "gaussian"), (128, 2.0, 16, 256, "phase")):
+            tau0 = 10.0 if nu > 0 else 1.0
+            p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=nu, tau0=tau0, tau_ref=tau0 + steps * 0.25)
+            st = inputs.initial_state((n, n, n), 0, kind, sigma=0.3)
+            g = sp.Grid([p], stream=s)
+            try:
+                g.plan(base_B=B)
+                info = g.plan_info(0)
+                for rep in range(2):
+                    g.write_state(0, *st)
+                    g.evolve(steps, sp.SP_RESTART | sp.SP_TRACE | sp.SP_FEATURES)
+                    f, t = _region_samples(g, info, steps)
+                    assert np.all(np.isfinite(f)) and f.shape[1] == 16
+                    Xs.append(f)
+                    ys.append(t)
+            finally:
+                g.close()
+        X = np.concatenate(Xs)
+        y = np.concatenate(ys)
+        xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+        m = sp.Model(seed=1, stream=s)
+        try:
+            losses = m.train(xd.data_ptr(), yd.data_ptr(), len(y), epochs=8, batch=256, lr=1e-3, order_seed=1)
+            path = str(tmp_path / "cost_model.bin")
+            m.save(path)
+        finally:
+            m.close()
+        assert float(np.mean(losses[-50:])) < float(np.mean(losses[:50]))
+
+        n, steps = 128, 256
+        p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=2.0, tau0=10.0, tau_ref=10.0 + steps * 0.25)
+        st = inputs.initial_state((n, n, n), 0, "phase")
+        res, times = {}, {}
+        for order in (sp.SP_ORDER_STATIC, sp.SP_ORDER_LEARNED):
+            g = sp.Grid([p], stream=s)
+            try:
+                g.plan(base_B=16, order=order, model_path=path if order == sp.SP_ORDER_LEARNED else None)
+                ms = []
+                for rep in range(4):
+                    g.write_state(0, *st)
+                    g.evolve(steps, sp.SP_RESTART | sp.SP_TIMING)
+                    ms.append(sum(g.timing()))
+                res[order] = g.read_state(0)
+                times[order] = float(np.median(ms[1:]))
+            finally:
+                g.close()
+    for a, b in zip(res[sp.SP_ORDER_STATIC], res[sp.SP_ORDER_LEARNED]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    gain = times[sp.SP_ORDER_STATIC] / times[sp.SP_ORDER_LEARNED]
+    print(f"\n128^3 x 256: static order {times[sp.SP_ORDER_STATIC]:.3f} ms, learned order "
+          f"{times[sp.SP_ORDER_LEARNED]:.3f} ms, gain x{gain:.3f}")
+    out = os.environ.get("SP_LEARNED_ORDER_REPORT")
+    if out:
+        with open(out, "w") as fh:
+            fh.write(f"static_ms {times[sp.SP_ORDER_STATIC]:.4f}\nlearned_ms {times[sp.SP_ORDER_LEARNED]:.4f}\n"
+                     f"gain {gain:.4f}\nsamples {len(y)}\nfinal_loss {float(np.mean(losses[-50:])):.5f}\n")
+    assert gain > 0.5  # the learned schedule may not be pathological
