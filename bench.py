@@ -143,6 +143,22 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def whole_job_rate(local_ms, units_per_rank, ws, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units in local_ms; the job took the slowest rank's time.
+    Returns (units/s over all ranks, max ms).  With ws > 1 this needs an
+    initialised process group (NCCL on the GPUs, gloo on the host)."""
+    t = float(local_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return ws * units_per_rank / (t / 1e3), t
+
+
 def flush_l2(buf):
     buf.zero_()
 
@@ -219,12 +235,7 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * updates * args.steps / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(sum(step_ms), updates * args.steps, ws, dev)
     ms_per_step = total_ms / args.steps
 
     # correctness guard on the benchmarked result: finite field

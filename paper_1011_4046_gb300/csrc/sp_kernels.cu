@@ -222,6 +222,9 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
 // table entries are loaded into registers before the compute.
 constexpr int kWorkerBarrier = 1;
 
+// Batches of up to this many simulations keep their descriptors in shared memory.
+constexpr int kSimsInSmem = 8;
+
 // Export entries of a level are loaded into registers before the compute of
 // the next level (up to kExportPrefetch per worker thread, which covers every
 // level of B <= 16 with 480 workers); any remainder is read in batches.
@@ -405,8 +408,12 @@ __global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int ma
     float2 *phi_buf1 = phi_buf0 + P3;
     float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + P3);
     TablesDev *s_tabs = reinterpret_cast<TablesDev *>(pc_s + B3);
-    SimDev *s_sims = reinterpret_cast<SimDev *>(s_tabs + a.n_tabs);
-    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_sims + a.n_sims);
+    // simulation descriptors: copied to shared memory for small batches, read
+    // through L1 from global memory for large ones
+    const int n_sims_smem = a.n_sims <= kSimsInSmem ? a.n_sims : 0;
+    SimDev *s_sims_copy = reinterpret_cast<SimDev *>(s_tabs + a.n_tabs);
+    const SimDev *s_sims = n_sims_smem ? s_sims_copy : a.sims;
+    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_sims_copy + n_sims_smem);
 
     {  // the launch's tables and simulation descriptors, once
         const int4 *src = reinterpret_cast<const int4 *>(a.tabs);
@@ -414,8 +421,8 @@ __global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int ma
         const int nt = a.n_tabs * (int)(sizeof(TablesDev) / 16);
         for (int i = tid; i < nt; i += NW + 32) dst[i] = src[i];
         const int4 *src2 = reinterpret_cast<const int4 *>(a.sims);
-        int4 *dst2 = reinterpret_cast<int4 *>(s_sims);
-        const int ns = a.n_sims * (int)(sizeof(SimDev) / 16);
+        int4 *dst2 = reinterpret_cast<int4 *>(s_sims_copy);
+        const int ns = n_sims_smem * (int)(sizeof(SimDev) / 16);
         for (int i = tid; i < ns; i += NW + 32) dst2[i] = src2[i];
         if (tid == 0) {
             s_handoff = 0;
@@ -834,7 +841,8 @@ size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units)
 {
     const int P = max_B + 2;
     return (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4) +
-           (size_t)n_tabs * sizeof(TablesDev) + (size_t)n_sims * sizeof(SimDev) + kMaxH * sizeof(LevelCoef) +
+           (size_t)n_tabs * sizeof(TablesDev) + (size_t)(n_sims <= kSimsInSmem ? n_sims : 0) * sizeof(SimDev) +
+           kMaxH * sizeof(LevelCoef) +
            (size_t)imp_units * sizeof(unsigned short);
 }
 
