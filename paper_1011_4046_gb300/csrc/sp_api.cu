@@ -543,7 +543,14 @@ int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool t
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-bool valid_threads(int t) { return t == 128 || t == 256 || t == 480 || t == 512 || t == 768; }
+// Worker counts of the region kernel: 128, 256, 480, 512, 768 (every worker
+// does every step), or an odd value w + 1 for the warp-specialised kernel with
+// w workers (193: 128 compute + 64 movement; 321: 256 + 64; 385: 256 + 128).
+bool valid_threads(int t)
+{
+    return t == 128 || t == 256 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
+}
+
 
 // Builds the plan for fixed region bases (one per simulation) and worker
 // count (0 = default for the largest base).
@@ -662,9 +669,9 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         if (block_shape != SP_AUTOTUNE)
             shapes.push_back(block_shape ? block_shape : default_threads(maxB));
         else if (maxB <= 8)
-            shapes = {128, 256};
+            shapes = {128, 193, 256};
         else
-            shapes = {256, 480, 512};
+            shapes = {256, 321, 385, 480, 512};
         for (int nt : shapes) {
             rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr);
             if (rc == SP_EINVAL) continue;  // does not fit this device
@@ -1072,7 +1079,7 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         sp_plan_info info;
         std::memset(&info, 0, sizeof info);
         info.base_B = g->B[sim];
-        info.threads = g->threads;
+        info.threads = g->threads;  // an odd value names the warp-specialised kernel
         info.ctas_per_sm = g->ctas_per_sm;
         info.grid = g->grid;
         info.regions_per_band = ps.regions_per_band;
