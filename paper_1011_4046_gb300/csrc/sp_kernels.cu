@@ -230,6 +230,7 @@ constexpr int kSimsInSmem = 8;
 // level of B <= 16 with 480 workers); any remainder is read in batches.
 constexpr int kExportPrefetch = 6;
 constexpr int kExportBatch = 4;
+constexpr int kCellsPerStep = 4;  // independent cell updates in flight per worker thread
 
 __device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, float2 *const *mb_of,
                                            const float2 *__restrict__ phi, const float4 *__restrict__ pc)
@@ -310,6 +311,55 @@ __device__ __forceinline__ void evolve_cell(int i, const Box3 &A, int w0, int w1
                                     prev_buf[pidx + P], prev_buf[pidx - PP], prev_buf[pidx + PP], pi, cc, co, q);
     cur[pidx] = nphi;
     pc_s[cidx] = make_float4(pi.x, pi.y, cc.x, cc.y);
+}
+
+// U cells of level k, linear indices i, i + stride, ... (all < cnt): every
+// input is loaded before any result is stored, so the U updates are
+// independent instruction streams (the compiler cannot prove that a store to
+// one cell's (pi, c) does not alias another cell's load).
+template <int U>
+__device__ __forceinline__ void evolve_cells(int i, int stride, const Box3 &A, int w0, int w1, float r0, float r1,
+                                             int P, int PP, int B, const float2 *__restrict__ prev_buf,
+                                             float2 *__restrict__ cur, float4 *__restrict__ pc_s, const LevelCoef &co,
+                                             const PhysConst &q)
+{
+    int pidx[U], cidx[U];
+    float2 c[U], xm[U], xp[U], ym[U], yp[U], zm[U], zp[U];
+    float4 pc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int j = i + u * stride;
+        const int t1 = fdiv(j, r0);
+        const int t2 = fdiv(t1, r1);
+        const int ux = A.lo[0] + j - t1 * w0;
+        const int uy = A.lo[1] + t1 - t2 * w1;
+        const int uz = A.lo[2] + t2;
+        pidx[u] = (uz * P + uy) * P + ux;
+        cidx[u] = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int p = pidx[u];
+        c[u] = prev_buf[p];
+        xm[u] = prev_buf[p - 1];
+        xp[u] = prev_buf[p + 1];
+        ym[u] = prev_buf[p - P];
+        yp[u] = prev_buf[p + P];
+        zm[u] = prev_buf[p - PP];
+        zp[u] = prev_buf[p + PP];
+        pc[u] = pc_s[cidx[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float2 pi = make_float2(pc[u].x, pc[u].y), cc = make_float2(pc[u].z, pc[u].w);
+        c[u] = site_update(c[u], xm[u], xp[u], ym[u], yp[u], zm[u], zp[u], pi, cc, co, q);
+        pc[u] = make_float4(pi.x, pi.y, cc.x, cc.y);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        cur[pidx[u]] = c[u];
+        pc_s[cidx[u]] = pc[u];
+    }
 }
 
 // Manager warp: hand regions to the worker, release finished ones.
@@ -541,18 +591,16 @@ __global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int ma
             prefetch_entries<NW>(el, ne, pre, wt);
             cp_async_wait_pending(2);  // groups 0..k-1 (base, coefficients, levels < k) have landed
             named_barrier(kWorkerBarrier, NW);
-            // ---- evolve the cells of level k, two independent cells per step ----
+            // ---- evolve the cells of level k, kCellsPerStep independent cells per step ----
             const LevelCoef co = s_coef[k - 1];
             const Box3 A = M.active[k];
             const float r0 = M.rcp_active[k][0], r1 = M.rcp_active[k][1];
             const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
             const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
             int i = wt;
-            for (; i + NW < cnt; i += 2 * NW) {
-                evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
-                evolve_cell(i + NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
-            }
-            if (i < cnt) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+            for (; i + (kCellsPerStep - 1) * NW < cnt; i += kCellsPerStep * NW)
+                evolve_cells<kCellsPerStep>(i, NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+            for (; i < cnt; i += NW) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
             // ---- final surface of level k-1 (read-only data of level k-1) ----
             if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, wt);
         }
