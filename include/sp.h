@@ -70,6 +70,8 @@ extern "C" {
 #define SP_SURF_PLAN 4    /* one sp_plan_info */
 #define SP_SURF_TIMING 5  /* double[3]: ms of the queue reset, the region kernel and the
                              remainder sweep of the last SP_TIMING call (events on the stream) */
+#define SP_SURF_LEVEL 7    /* int64 (host memory): the simulation's current level n; readable and
+                              writable -- a checkpoint is SP_SURF_STATE plus SP_SURF_LEVEL */
 #define SP_SURF_FEATURES 6 /* float[regions][SP_MODEL_FEATURES]: cost-model inputs of the sim's regions
                               in the last SP_FEATURES (or learned-order) call, in region-id order
                               (the order of SP_SURF_TRACE) */
@@ -80,6 +82,15 @@ extern "C" {
 /* ---- region ordering of sp_region_plan ---- */
 #define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
 #define SP_ORDER_LEARNED 1 /* cost-model priority (results are identical) */
+
+/* ---- sp_set_option ---- */
+#define SP_OPT_WAIT_LIMIT_NS 1      /* bound of every device-side wait, ns (default 2e9; 1e6 .. 6e10) */
+#define SP_OPT_FAULT_DROP_RELEASE 2 /* inject a failure: the region with this id in the next region
+                                       launches (ids as in SP_SURF_TRACE, simulations concatenated)
+                                       finishes but never releases its successors, so the launch ends
+                                       with SP_ETIMEOUT after the wait limit; -1 clears */
+#define SP_OPT_GRAPHS 3             /* 1 (default): capture region calls into CUDA graphs on
+                                       non-legacy streams; 0: launch directly */
 
 /* ---- region cost model ---- */
 #define SP_MODEL_FEATURES 16
@@ -190,6 +201,12 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags);
 
 /*
+ * sp_set_option -- set one of the SP_OPT_* options above.
+ * Errors: SP_EINVAL.
+ */
+int sp_set_option(sp_grid *g, int32_t option, int64_t value);
+
+/*
  * sp_read_surface -- copy out one simulation's state or diagnostics.
  *   what : SP_SURF_STATE, SP_SURF_DIAG, SP_SURF_TRACE, SP_SURF_WINDING or
  *          SP_SURF_PLAN; dst_bytes must be at least the size of that item.
@@ -201,8 +218,11 @@ int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size
 
 /*
  * sp_write_surface -- load one simulation's state (what = SP_SURF_STATE:
- * phi then pic, 24 * sites bytes) from host or device memory.
- * Enqueued on the grid's stream.  Errors: SP_EINVAL, SP_ECUDA.
+ * phi then pic, 24 * sites bytes) from host or device memory, enqueued on the
+ * grid's stream; or set its current level (what = SP_SURF_LEVEL, one int64 in
+ * host memory), which selects tau, a and the friction of the next steps.
+ * Restoring SP_SURF_STATE and SP_SURF_LEVEL from a checkpoint resumes a run
+ * bit-exactly.  Errors: SP_EINVAL, SP_ECUDA.
  */
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device);
 

@@ -189,6 +189,7 @@ struct sp_grid {
     bool prev_trace_ok = false;  // this call's features may read d_trace
     int use_graphs = 1;  // capture launch sequences on non-legacy streams
     unsigned long long wait_limit_ns = 2000000000ull;
+    int fault_drop = -1;  // SP_OPT_FAULT_DROP_RELEASE
     // what is already on the device (uploads are skipped when unchanged)
     std::vector<sp::LevelCoef> up_coef;
     std::vector<sp::SimDev> up_sims;
@@ -952,6 +953,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             a.ctl = g->d_ctl;
             a.trace = trace ? g->d_trace : nullptr;
             a.prio = learned ? g->d_prio : nullptr;
+            a.fault_drop = g->fault_drop;
             prev_trace_ok = g->trace_total == total;  // the trace buffer still holds a call of this layout
             if (trace) g->trace_total = total;
             g->last_traced = trace;
@@ -986,9 +988,39 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
     return SP_OK;
 }
 
+int sp_set_option(sp_grid *g, int32_t option, int64_t value)
+{
+    if (!g) return SP_EINVAL;
+    switch (option) {
+    case SP_OPT_WAIT_LIMIT_NS:
+        if (value < 1000000 || value > 60000000000ll) return SP_EINVAL;
+        g->wait_limit_ns = (unsigned long long)value;
+        return SP_OK;
+    case SP_OPT_FAULT_DROP_RELEASE:
+        if (value < -1 || value > 0x7fffffffll) return SP_EINVAL;
+        g->fault_drop = (int)value;
+        return SP_OK;
+    case SP_OPT_GRAPHS:
+        if (value != 0 && value != 1) return SP_EINVAL;
+        g->use_graphs = (int)value;
+        return SP_OK;
+    default:
+        return SP_EINVAL;
+    }
+}
+
 int sp_write_surface(sp_grid *g, int32_t sim, int32_t what, const void *src, size_t src_bytes, int32_t src_is_device)
 {
-    if (!g || sim < 0 || sim >= g->n_sims || !src || what != SP_SURF_STATE) return SP_EINVAL;
+    if (!g || sim < 0 || sim >= g->n_sims || !src) return SP_EINVAL;
+    if (what == SP_SURF_LEVEL) {
+        if (src_bytes < sizeof(int64_t) || src_is_device) return SP_EINVAL;
+        int64_t level;
+        std::memcpy(&level, src, sizeof level);
+        if (level < 0) return SP_EINVAL;
+        g->level[sim] = level;
+        return SP_OK;
+    }
+    if (what != SP_SURF_STATE) return SP_EINVAL;
     const size_t sites = (size_t)sites_of(g->p[sim]);
     if (src_bytes < 24 * sites) return SP_EINVAL;
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -1011,6 +1043,12 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         if (rc != SP_OK) return rc;
     }
     switch (what) {
+    case SP_SURF_LEVEL: {
+        if (dst_bytes < sizeof(int64_t) || dst_is_device) return SP_EINVAL;
+        const int64_t level = g->level[sim];
+        std::memcpy(dst, &level, sizeof level);
+        return SP_OK;
+    }
     case SP_SURF_STATE: {
         if (dst_bytes < (size_t)(24 * sites)) return SP_EINVAL;
         char *b = (char *)dst;

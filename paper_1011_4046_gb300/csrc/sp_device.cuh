@@ -104,6 +104,10 @@ struct RegionArgs {
     // With it the seeds are queued bucket by bucket and the successors that
     // one finished region makes ready are pushed bucket by bucket.
     const unsigned char *prio;
+    // Host-injected failure (failure-detection tests): the region with this
+    // launch id finishes but never releases its successors; -1 = none.
+    int fault_drop;
+    int pad_;
 };
 
 static_assert(sizeof(TablesDev) % 16 == 0, "tables are copied in 16-byte units");

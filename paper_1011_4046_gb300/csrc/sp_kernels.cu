@@ -140,6 +140,10 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
                                    int lane, unsigned long long t_start, int g)
 {
     __threadfence();
+    if (g == a.fault_drop) {  // injected failure: completion is never reported downstream
+        if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
+        return;
+    }
     const int n_same = T.type[r.S].n_same_succ;
     const int n_next = (r.S == kTypes - 1 && r.band + 1 < sd.nbands) ? kMaxNextSucc : 0;
     bool ready = false;
@@ -184,7 +188,6 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
     }
     if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
     (void)t_start;
-    (void)g;
 }
 
 // ------------------------------------------------------------ region kernel

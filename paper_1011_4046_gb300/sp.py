@@ -47,6 +47,10 @@ SP_SURF_WINDING = 3
 SP_SURF_PLAN = 4
 SP_SURF_TIMING = 5
 SP_SURF_FEATURES = 6
+SP_SURF_LEVEL = 7
+SP_OPT_WAIT_LIMIT_NS = 1
+SP_OPT_FAULT_DROP_RELEASE = 2
+SP_OPT_GRAPHS = 3
 SP_MODEL_FEATURES = 16
 SP_MODEL_PARAMS = 5313
 
@@ -148,6 +152,7 @@ def load(build_if_missing: bool = False):
         lib.sp_write_surface.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_size_t, ctypes.c_int32]
         lib.sp_destroy.argtypes = [vp]
         lib.sp_sweep_noalloc.argtypes = [ctypes.POINTER(sp_params), vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
+        lib.sp_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
         lib.sp_strerror.argtypes = [ctypes.c_int]
         lib.sp_strerror.restype = ctypes.c_char_p
         fp = ctypes.POINTER(ctypes.c_float)
@@ -165,7 +170,7 @@ def load(build_if_missing: bool = False):
         for f in ("sp_grid_create", "sp_region_plan", "sp_evolve", "sp_read_surface", "sp_write_surface",
                   "sp_destroy", "sp_sweep_noalloc", "sp_model_create", "sp_model_destroy", "sp_model_get_params",
                   "sp_model_set_params", "sp_model_predict", "sp_model_grad", "sp_model_adam_step", "sp_model_train",
-                  "sp_model_save", "sp_model_load"):
+                  "sp_model_save", "sp_model_load", "sp_set_option"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -348,6 +353,18 @@ class Grid:
 
     def plan(self, base_B=0, threads=0, order=SP_ORDER_STATIC, model_path=None):
         _check(sp_region_plan(self.h, base_B, threads, order, model_path), "sp_region_plan")
+
+    def set_option(self, option, value):
+        _check(load().sp_set_option(self.h, int(option), int(value)), "sp_set_option")
+
+    def level(self, sim=0):
+        out = ctypes.c_int64()
+        _check(sp_read_surface(self.h, sim, SP_SURF_LEVEL, ctypes.addressof(out), 8, 0), "sp_read_surface")
+        return int(out.value)
+
+    def set_level(self, sim, level):
+        v = ctypes.c_int64(int(level))
+        _check(sp_write_surface(self.h, sim, SP_SURF_LEVEL, ctypes.addressof(v), 8, 0), "sp_write_surface")
 
     def evolve(self, n_steps, flags=0):
         _check(sp_evolve(self.h, n_steps, flags), "sp_evolve")
