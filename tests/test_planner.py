@@ -57,7 +57,7 @@ def test_tiling_dag_and_hazards(rx, B, n, bands):
     assert ok == 1, msg.value.decode()
 
 
-def test_traffic_counts_match_the_brute_force_survey_figures(rx):
+def test_traffic_counts_match_the_brute_force_figures(rx):
     """Read bytes per site-update reproduce the independent brute-force count
     (25.2 / 13.8 / 7.2 B at B = 8 / 16 / 32).  Writes are higher than a
     write-once design because a face cell is written into each consumer's
