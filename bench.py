@@ -46,6 +46,11 @@ SEED = 0
 # consumer).
 ALG_BYTES_PER_UPDATE = {8: 42.8, 16: 25.3, 32: 13.8}
 MONO_BYTES_PER_UPDATE = 48.0
+# On-chip (shared-memory) bytes per site-update of the region kernel: seven
+# phi reads (8 B) and one phi write, one (pi, c) read and write (16 B each).
+SMEM_BYTES_PER_UPDATE = 7 * 8 + 8 + 2 * 16
+# Shared-memory bandwidth of one GB300, nominal: 128 B per clock per SM.
+SMS, SMEM_BYTES_PER_CLOCK = 152, 128
 WORKLOAD = (f"{N}^3 matter era (nu=2, tau0=10, tau_ref=74), lambda=2, eta=1, dx=1, dt=0.25, random-phase "
             f"init seed 0, {STEPS} leapfrog steps, region base B={B}")
 METRIC = "lattice site-updates/s"
@@ -143,6 +148,18 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
                 "reasons": sorted(reasons)}
+
+
+def smem_roofline(updates, kernel_ms, clk):
+    """On-chip line of the region kernel: its shared-memory bytes per launch
+    over the launch time, against the nominal bandwidth at the SM clock
+    sampled during the timed region (or the maximum clock)."""
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = SMS * SMEM_BYTES_PER_CLOCK * mhz * 1e6 / 1e9
+    achieved = SMEM_BYTES_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e9
+    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": f"nominal (152 SMs x 128 B/clock at {mhz:.0f} MHz)",
+            "bytes_per_update": SMEM_BYTES_PER_UPDATE}
 
 
 def whole_job_rate(local_ms, units_per_rank, ws, device=None):
@@ -303,6 +320,7 @@ def run_ours(args):
                      "kernel": "region_kernel", "kernel_ms": kern_mean,
                      "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
                      "design_bytes_per_update": info["bytes_per_update"]},
+        "roofline_smem": smem_roofline(updates, kern_mean, clk),
         "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
         "gpu_launches": 2 * args.steps,
