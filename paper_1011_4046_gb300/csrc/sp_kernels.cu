@@ -233,7 +233,12 @@ constexpr int kSimsInSmem = 8;
 // level of B <= 16 with 480 workers); any remainder is read in batches.
 constexpr int kExportPrefetch = 6;
 constexpr int kExportBatch = 4;
-constexpr int kCellsPerStep = 4;  // independent cell updates in flight per worker thread
+// Per worker count: independent cell updates in flight per thread, and the
+// CTAs per SM the registers are budgeted for.  128 workers serve base 8,
+// whose small regions fit several CTAs per SM; 256 and more serve base 16,
+// one CTA per SM.
+__host__ __device__ constexpr int region_cells_per_step(int nw) { return nw <= 128 ? 2 : 4; }
+__host__ __device__ constexpr int region_min_blocks(int nw) { return nw <= 128 ? 4 : 1; }
 
 __device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, float2 *const *mb_of,
                                            const float2 *__restrict__ phi, const float4 *__restrict__ pc)
@@ -450,7 +455,7 @@ __device__ void manager_loop(const RegionArgs &a, const SimDev *s_sims, const Ta
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int max_P)
+__global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(RegionArgs a, int max_P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_slot[2], s_handoff, s_done;
@@ -594,15 +599,16 @@ __global__ void __launch_bounds__(NW + 32, 1) region_kernel(RegionArgs a, int ma
             prefetch_entries<NW>(el, ne, pre, wt);
             cp_async_wait_pending(2);  // groups 0..k-1 (base, coefficients, levels < k) have landed
             named_barrier(kWorkerBarrier, NW);
-            // ---- evolve the cells of level k, kCellsPerStep independent cells per step ----
+            // ---- evolve the cells of level k, several independent cells per step ----
             const LevelCoef co = s_coef[k - 1];
             const Box3 A = M.active[k];
             const float r0 = M.rcp_active[k][0], r1 = M.rcp_active[k][1];
             const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
             const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
             int i = wt;
-            for (; i + (kCellsPerStep - 1) * NW < cnt; i += kCellsPerStep * NW)
-                evolve_cells<kCellsPerStep>(i, NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+            constexpr int U = region_cells_per_step(NW);
+            for (; i + (U - 1) * NW < cnt; i += U * NW)
+                evolve_cells<U>(i, NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
             for (; i < cnt; i += NW) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
             // ---- final surface of level k-1 (read-only data of level k-1) ----
             if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, wt);
