@@ -56,3 +56,34 @@ def test_struct_layouts_match_the_header(lib):
     # sp_params: 3 int32 + 7 double + 2 int32 with natural alignment
     assert ctypes.sizeof(sp.sp_params) == 12 + 4 + 7 * 8 + 8
     assert ctypes.sizeof(sp.sp_diag) == 8 + 6 * 8 + 3 * 8 + 8 + 3 * 8 + 8
+
+
+def test_model_entry_points_reject_bad_input_without_a_gpu(lib, tmp_path):
+    out = ctypes.c_void_p()
+    assert lib.sp_model_load(None, None, ctypes.byref(out)) == sp.SP_EINVAL
+    bad = tmp_path / "not_a_model.bin"
+    bad.write_bytes(b"NOTAMODEL" + bytes(64))
+    assert lib.sp_model_load(str(bad).encode(), None, ctypes.byref(out)) == sp.SP_EINVAL and not out.value
+    truncated = tmp_path / "truncated.bin"
+    truncated.write_bytes(b"SPMLP001" + (5313).to_bytes(4, "little") + bytes(100))
+    assert lib.sp_model_load(str(truncated).encode(), None, ctypes.byref(out)) == sp.SP_EINVAL
+    assert lib.sp_model_destroy(None) == sp.SP_EINVAL
+    assert lib.sp_model_predict(None, None, 0, None) == sp.SP_EINVAL
+    assert lib.sp_model_train(None, None, None, 0, 1, 1, ctypes.c_float(1e-3), 0, None, None) == sp.SP_EINVAL
+
+
+def test_options_and_levels_reject_null_handles(lib):
+    assert lib.sp_set_option(None, sp.SP_OPT_WAIT_LIMIT_NS, 10 ** 9) == sp.SP_EINVAL
+    v = ctypes.c_int64(3)
+    assert lib.sp_write_surface(None, 0, sp.SP_SURF_LEVEL, ctypes.byref(v), 8, 0) == sp.SP_EINVAL
+
+
+def test_header_constants_match_the_binding():
+    text = open(sp.HEADER).read()
+    import re
+    for name in ("SP_AUTOTUNE", "SP_FEATURES", "SP_SURF_FEATURES", "SP_SURF_LEVEL", "SP_OPT_WAIT_LIMIT_NS",
+                 "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_MODEL_PARAMS", "SP_MODEL_FEATURES",
+                 "SP_ORDER_STATIC", "SP_ORDER_LEARNED", "SP_TIMING", "SP_TRACE"):
+        m = re.search(r"#define\s+" + name + r"\s+\(?(-?\d+)u?\)?", text)
+        assert m, name
+        assert int(m.group(1)) == getattr(sp, name), name
