@@ -225,8 +225,7 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
 // table entries are loaded into registers before the compute.
 constexpr int kWorkerBarrier = 1;
 
-// Batches of up to this many simulations keep their descriptors in shared memory.
-constexpr int kSimsInSmem = 8;
+static_assert(sizeof(SimDev) / 16 <= 32, "the manager warp copies a descriptor with one int4 per lane");
 
 // Export entries of a level are loaded into registers before the compute of
 // the next level (up to kExportPrefetch per worker thread, which covers every
@@ -371,8 +370,8 @@ __device__ __forceinline__ void evolve_cells(int i, int stride, const Box3 &A, i
 }
 
 // Manager warp: hand regions to the worker, release finished ones.
-__device__ void manager_loop(const RegionArgs &a, const SimDev *s_sims, const TablesDev *s_tabs, int *s_slot,
-                             int *s_handoff, int *s_done)
+__device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *s_slot, SimDev *s_sd,
+                             RegionInfo *s_ri, int *s_handoff, int *s_done)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long limit = a.ctl->wait_limit_ns;
@@ -414,18 +413,30 @@ __device__ void manager_loop(const RegionArgs &a, const SimDev *s_sims, const Ta
         const int have = __shfl_sync(0xffffffffu, got, 0);
         if (done && have) {
             const int next = __shfl_sync(0xffffffffu, v, 0);
+            RegionInfo ni = pend_info;
+            if (next >= 0) {
+                // hand over the decoded region and its simulation's descriptor in
+                // shared memory, with the region id
+                ni = decode_region(a.sims, a.n_sims, next);
+                const int slot = (seq + 1) & 1;
+                const int4 *src = reinterpret_cast<const int4 *>(a.sims + ni.sim);
+                int4 *dst = reinterpret_cast<int4 *>(s_sd + slot);
+                if (lane < (int)(sizeof(SimDev) / 16)) dst[lane] = src[lane];
+                if (lane == 0) s_ri[slot] = ni;
+                __syncwarp();
+            }
             if (lane == 0) {
                 s_slot[(seq + 1) & 1] = next;
                 st_release_cta_shared(s_handoff, seq + 1);
             }
             ++seq;
             if (pending >= 0) {
-                const SimDev &sd = s_sims[pend_info.sim];
+                const SimDev &sd = a.sims[pend_info.sim];
                 release_successors(a, sd, s_tabs[sd.tab_index], pend_info, lane, 0ull, pending);
             }
             pending = next;
             if (next < 0) break;
-            pend_info = decode_region(s_sims, a.n_sims, next);
+            pend_info = ni;
             if (lane == 0) {
                 got = 0;
                 idx = atomicAdd(&a.ctl->head, 1u);
@@ -436,7 +447,7 @@ __device__ void manager_loop(const RegionArgs &a, const SimDev *s_sims, const Ta
         }
         if (done && pending >= 0) {
             // the next region is not ready yet: it may wait on this release
-            const SimDev &sd = s_sims[pend_info.sim];
+            const SimDev &sd = a.sims[pend_info.sim];
             release_successors(a, sd, s_tabs[sd.tab_index], pend_info, lane, 0ull, pending);
             pending = -1;
             if (lane == 0) t_progress = globaltimer_ns();
@@ -459,6 +470,8 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_slot[2], s_handoff, s_done;
+    __shared__ SimDev s_sd[2];      // descriptor of the region handed over in each slot
+    __shared__ RegionInfo s_ri[2];  // and the region, decoded
     __shared__ float2 *s_mb[64];  // consumer code (type | offset bits << 3) -> mailbox base
     const int tid = threadIdx.x;
     const int P3 = max_P * max_P * max_P, B3 = (max_P - 2) * (max_P - 2) * (max_P - 2);
@@ -466,22 +479,13 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
     float2 *phi_buf1 = phi_buf0 + P3;
     float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + P3);
     TablesDev *s_tabs = reinterpret_cast<TablesDev *>(pc_s + B3);
-    // simulation descriptors: copied to shared memory for small batches, read
-    // through L1 from global memory for large ones
-    const int n_sims_smem = a.n_sims <= kSimsInSmem ? a.n_sims : 0;
-    SimDev *s_sims_copy = reinterpret_cast<SimDev *>(s_tabs + a.n_tabs);
-    const SimDev *s_sims = n_sims_smem ? s_sims_copy : a.sims;
-    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_sims_copy + n_sims_smem);
+    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_tabs + a.n_tabs);
 
     {  // the launch's tables and simulation descriptors, once
         const int4 *src = reinterpret_cast<const int4 *>(a.tabs);
         int4 *dst = reinterpret_cast<int4 *>(s_tabs);
         const int nt = a.n_tabs * (int)(sizeof(TablesDev) / 16);
         for (int i = tid; i < nt; i += NW + 32) dst[i] = src[i];
-        const int4 *src2 = reinterpret_cast<const int4 *>(a.sims);
-        int4 *dst2 = reinterpret_cast<int4 *>(s_sims_copy);
-        const int ns = n_sims_smem * (int)(sizeof(SimDev) / 16);
-        for (int i = tid; i < ns; i += NW + 32) dst2[i] = src2[i];
         if (tid == 0) {
             s_handoff = 0;
             s_done = 0;
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
     }
     __syncthreads();
     if (tid < 32) {
-        manager_loop(a, s_sims, s_tabs, s_slot, &s_handoff, &s_done);
+        manager_loop(a, s_tabs, s_slot, s_sd, s_ri, &s_handoff, &s_done);
         return;
     }
     const int wt = tid - 32;  // worker thread index
@@ -521,8 +525,8 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
         if (g < 0) break;
         if (a.trace && wt == 0) a.trace[2 * (size_t)g] = globaltimer_ns();
 
-        const RegionInfo r = decode_region(s_sims, a.n_sims, g);
-        const SimDev &sd = s_sims[r.sim];
+        const RegionInfo r = s_ri[seq & 1];  // decoded by the manager at the handoff
+        const SimDev &sd = s_sd[seq & 1];
         const TablesDev &T = s_tabs[sd.tab_index];
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band, jl = r.jl;
@@ -672,6 +676,8 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
     constexpr int NW = NC + ND;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_slot[2], s_handoff, s_done;
+    __shared__ SimDev s_sd[2];      // descriptor of the region handed over in each slot
+    __shared__ RegionInfo s_ri[2];  // and the region, decoded
     __shared__ float2 *s_mb[64];  // consumer code (type | offset bits << 3) -> mailbox base
     const int tid = threadIdx.x;
     const int P3 = max_P * max_P * max_P, B3 = (max_P - 2) * (max_P - 2) * (max_P - 2);
@@ -679,20 +685,13 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
     float2 *phi_buf1 = phi_buf0 + P3;
     float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + P3);
     TablesDev *s_tabs = reinterpret_cast<TablesDev *>(pc_s + B3);
-    const int n_sims_smem = a.n_sims <= kSimsInSmem ? a.n_sims : 0;
-    SimDev *s_sims_copy = reinterpret_cast<SimDev *>(s_tabs + a.n_tabs);
-    const SimDev *s_sims = n_sims_smem ? s_sims_copy : a.sims;
-    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_sims_copy + n_sims_smem);
+    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_tabs + a.n_tabs);
 
     {  // the launch's tables and simulation descriptors, once
         const int4 *src = reinterpret_cast<const int4 *>(a.tabs);
         int4 *dst = reinterpret_cast<int4 *>(s_tabs);
         const int nt = a.n_tabs * (int)(sizeof(TablesDev) / 16);
         for (int i = tid; i < nt; i += NW + 32) dst[i] = src[i];
-        const int4 *src2 = reinterpret_cast<const int4 *>(a.sims);
-        int4 *dst2 = reinterpret_cast<int4 *>(s_sims_copy);
-        const int ns = n_sims_smem * (int)(sizeof(SimDev) / 16);
-        for (int i = tid; i < ns; i += NW + 32) dst2[i] = src2[i];
         if (tid == 0) {
             s_handoff = 0;
             s_done = 0;
@@ -707,7 +706,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
     }
     __syncthreads();
     if (tid < 32) {
-        manager_loop(a, s_sims, s_tabs, s_slot, &s_handoff, &s_done);
+        manager_loop(a, s_tabs, s_slot, s_sd, s_ri, &s_handoff, &s_done);
         return;
     }
     const int wt = tid - 32;            // worker index
@@ -734,8 +733,8 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
         if (g < 0) break;
         if (a.trace && wt == 0) a.trace[2 * (size_t)g] = globaltimer_ns();
 
-        const RegionInfo r = decode_region(s_sims, a.n_sims, g);
-        const SimDev &sd = s_sims[r.sim];
+        const RegionInfo r = s_ri[seq & 1];  // decoded by the manager at the handoff
+        const SimDev &sd = s_sd[seq & 1];
         const TablesDev &T = s_tabs[sd.tab_index];
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band;
@@ -1129,10 +1128,10 @@ static cudaError_t region_launch_t(const RegionArgs &a, int max_B, size_t smem, 
 
 size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units)
 {
+    (void)n_sims;  // descriptors travel with the handoff (static shared memory)
     const int P = max_B + 2;
     return (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4) +
-           (size_t)n_tabs * sizeof(TablesDev) + (size_t)(n_sims <= kSimsInSmem ? n_sims : 0) * sizeof(SimDev) +
-           kMaxH * sizeof(LevelCoef) +
+           (size_t)n_tabs * sizeof(TablesDev) + kMaxH * sizeof(LevelCoef) +
            (size_t)imp_units * sizeof(unsigned short);
 }
 
