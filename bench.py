@@ -162,6 +162,20 @@ def smem_roofline(updates, kernel_ms, clk):
             "bytes_per_update": SMEM_BYTES_PER_UPDATE}
 
 
+def trace_utilisation(trace, ctas):
+    """GPU analogues of the paper's CPU utilisation and degree of parallelism
+    (Sec. 6) from per-region (start, end) globaltimer stamps: the fraction of
+    the persistent CTAs' time spent inside regions, and the mean number of
+    regions in flight."""
+    tr = np.asarray(trace, dtype=np.int64)
+    start, end = tr[:, 0], tr[:, 1]
+    span = float(end.max() - start.min())
+    busy = float((end - start).sum())
+    return {"regions": int(len(tr)), "cta_busy_fraction": busy / (ctas * span),
+            "mean_regions_in_flight": busy / span, "mean_region_us": busy / len(tr) / 1e3,
+            "makespan_ms": span / 1e6}
+
+
 def whole_job_rate(local_ms, units_per_rank, ws, device=None):
     """Whole-job throughput of independent replicas: every rank processed
     units_per_rank units in local_ms; the job took the slowest rank's time.
@@ -261,6 +275,14 @@ def run_ours(args):
     phi_end = g.read_state(0)[0]
     finite = bool(np.all(np.isfinite(phi_end)))
 
+    # the paper's utilisation figures (Sec. 6), from one traced call outside the timed region
+    restore()
+    rc = sp.sp_evolve(g.h, STEPS, sp.SP_RESTART | sp.SP_TRACE)
+    if rc != 0:
+        raise sp.SpError(rc, "sp_evolve (trace)")
+    utilisation = trace_utilisation(g.trace(0, int(info["regions_per_band"] * (STEPS // (info["base_B"] // 2)))),
+                                    info["grid"])
+
     # ---- monolithic sweep on the same inputs (the comparator) ----
     for _ in range(max(1, args.warmup // 2)):
         one_step(sp.SP_MONOLITHIC)
@@ -324,6 +346,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
         "gpu_launches": 2 * args.steps,
+        "utilisation": utilisation,
         "clocks": clk,
         "wall_s_timed_region": wall,
         "field_finite": finite,
