@@ -382,6 +382,8 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
     if (lane == 0) idx = atomicAdd(&a.ctl->head, 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
     int got = 0, v = -1;
+    int prepared = 0;  // the next region's descriptor is in its handoff slot
+    RegionInfo ni = pend_info;
     unsigned long long t0 = globaltimer_ns();
     unsigned long long t_progress = t0;  // last handoff or release
     for (unsigned spin = 0;; ++spin) {
@@ -407,16 +409,13 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
                     }
                 }
             }
-            done = ld_acquire_cta_shared(s_done) == seq;
         }
-        done = __shfl_sync(0xffffffffu, done, 0);
         const int have = __shfl_sync(0xffffffffu, got, 0);
-        if (done && have) {
-            const int next = __shfl_sync(0xffffffffu, v, 0);
-            RegionInfo ni = pend_info;
+        const int next = __shfl_sync(0xffffffffu, v, 0);
+        if (have && !prepared) {
+            // while the worker is still busy: decode the next region and put it
+            // and its simulation's descriptor into the free handoff slot
             if (next >= 0) {
-                // hand over the decoded region and its simulation's descriptor in
-                // shared memory, with the region id
                 ni = decode_region(a.sims, a.n_sims, next);
                 const int slot = (seq + 1) & 1;
                 const int4 *src = reinterpret_cast<const int4 *>(a.sims + ni.sim);
@@ -425,6 +424,11 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
                 if (lane == 0) s_ri[slot] = ni;
                 __syncwarp();
             }
+            prepared = 1;
+        }
+        if (lane == 0) done = ld_acquire_cta_shared(s_done) == seq;
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done && have) {
             if (lane == 0) {
                 s_slot[(seq + 1) & 1] = next;
                 st_release_cta_shared(s_handoff, seq + 1);
@@ -437,6 +441,7 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
             pending = next;
             if (next < 0) break;
             pend_info = ni;
+            prepared = 0;
             if (lane == 0) {
                 got = 0;
                 idx = atomicAdd(&a.ctl->head, 1u);
@@ -461,7 +466,7 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
             stuck = 1;
         }
         if (__shfl_sync(0xffffffffu, stuck, 0)) break;
-        __nanosleep(32);
+        if (!have) __nanosleep(32);  // waiting on the queue backs off; waiting on the worker polls shared memory
     }
 }
 
@@ -507,7 +512,8 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
     __shared__ int s_abort;
     for (int seq = 1;; ++seq) {
         if (wt == 0) {
-            // bounded wait for the manager's handoff
+            // bounded wait for the manager's handoff (a shared-memory poll: the
+            // handoff normally follows within a microsecond)
             s_abort = 0;
             const unsigned long long t0 = globaltimer_ns(), limit = 8 * a.ctl->wait_limit_ns;
             for (unsigned spin = 0; ld_acquire_cta_shared(&s_handoff) < seq; ++spin) {
@@ -516,7 +522,6 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
                     s_abort = 1;
                     break;
                 }
-                __nanosleep(20);
             }
         }
         named_barrier(kWorkerBarrier, NW);
@@ -715,7 +720,8 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
     __shared__ int s_abort;
     for (int seq = 1;; ++seq) {
         if (wt == 0) {
-            // bounded wait for the manager's handoff
+            // bounded wait for the manager's handoff (a shared-memory poll: the
+            // handoff normally follows within a microsecond)
             s_abort = 0;
             const unsigned long long t0 = globaltimer_ns(), limit = 8 * a.ctl->wait_limit_ns;
             for (unsigned spin = 0; ld_acquire_cta_shared(&s_handoff) < seq; ++spin) {
@@ -724,7 +730,6 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     s_abort = 1;
                     break;
                 }
-                __nanosleep(20);
             }
         }
         named_barrier(kBarAll, NW);
