@@ -161,7 +161,7 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  * sp_region_plan -- build the region tiling, the dependency DAG and the
  * surface routing tables (paper Sec. 2 geometry and Sec. 3 sizing), and size
  * the persistent launch.
- *   base_B     : region base in cells (8 or 16; B/2 steps per band); 0 to
+ *   base_B     : region base in cells (4, 8 or 16; B/2 steps per band); 0 to
  *                take 16 where it divides every side of a simulation, else 8;
  *                SP_AUTOTUNE to time both policies (all 8, 16 where
  *                possible) and keep the faster.  Every n[d] must be a

@@ -798,7 +798,8 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
 int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t order, const char *model_path)
 {
     if (!g) return SP_EINVAL;
-    if (base_B != 0 && base_B != SP_AUTOTUNE && (base_B % 2 != 0 || base_B < 4 || base_B > 16)) return SP_EINVAL;
+    // bases are powers of two: the kernels decode cell indices with shifts
+    if (base_B != 0 && base_B != SP_AUTOTUNE && base_B != 4 && base_B != 8 && base_B != 16) return SP_EINVAL;
     if (block_shape != 0 && block_shape != SP_AUTOTUNE && !valid_threads(block_shape)) return SP_EINVAL;
     if (order != SP_ORDER_STATIC && order != SP_ORDER_LEARNED) return SP_EINVAL;
     g->tune = TuneReport();

@@ -290,10 +290,10 @@ __device__ __forceinline__ void import_level(const float2 *__restrict__ mb, int 
                                              const unsigned short *fl, const unsigned short *pl, float2 *dst,
                                              float4 *pc_s, int B, int P, float rcp_B, int wt)
 {
+    const int lgB = 31 - __clz(B);  // B is a power of two (4, 8 or 16)
     for (int i = wt; i < nf; i += NW) {
         const int c = fl[i];
-        const int t1 = fdiv(c, rcp_B), t2 = fdiv(t1, rcp_B);
-        const int pidx = ((t2 + 1) * P + (t1 - t2 * B + 1)) * P + (c - t1 * B + 1);
+        const int pidx = (((c >> (2 * lgB)) + 1) * P + ((c >> lgB) & (B - 1)) + 1) * P + (c & (B - 1)) + 1;
         cp_async16(pc_s + c, mb + 2 * i);
         cp_async8(dst + pidx, mb + 2 * nf + i);
     }

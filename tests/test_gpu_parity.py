@@ -262,6 +262,9 @@ def test_bad_base_is_rejected():
             g.plan(base_B=16)  # 24 is not a multiple of 16
         assert e.value.code == sp.SP_EINVAL
         with pytest.raises(sp.SpError) as e:
+            g.plan(base_B=12)  # divides 24, but bases are powers of two
+        assert e.value.code == sp.SP_EINVAL
+        with pytest.raises(sp.SpError) as e:
             g.evolve(8)
         assert e.value.code == sp.SP_ENOTPLANNED
     finally:
