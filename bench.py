@@ -414,15 +414,18 @@ def run_batched(args):
             "data": "synthetic (seeded random-phase / Gaussian fields)",
             "config": {"workload": "batched: 64 simulations, N uniform over multiples of 8 in [48,160], "
                                    "nu in {0,1,2}, seeds 0-63, 192 steps each, one autotuned persistent launch "
-                                   "replayed from a CUDA graph",
-                       "site_updates": updates, "region_bases": bases, "threads_per_cta": infos[0]["threads"],
+                                   "per region base, replayed from a CUDA graph",
+                       "site_updates": updates, "region_bases": bases,
+                       "threads_per_cta": {str(b): next(i["threads"] for i in infos if i["base_B"] == b)
+                                           for b in bases},
+                       "ctas": {str(b): next(i["grid"] for i in infos if i["base_B"] == b) for b in bases},
                        "autotune_s": tune_s, "autotune_candidates": infos[0]["tune_candidates"],
                        "l2": "flushed (512 MiB write) before every step; states restored on device outside timing",
                        "parallelism": "1 GPU"},
             "monolithic": {"value": res["monolithic"][0], "unit": "site-updates/s",
                            "ms_per_step": res["monolithic"][1],
                            "speedup_of_regions": res["regions"][0] / res["monolithic"][0]},
-            "gpu_launches": 2 * args.steps}
+            "gpu_launches": 2 * len(bases) * args.steps}  # per base: queue reset + region kernel
 
 
 def cpu_baseline(budget_s, n_steps_cap=STEPS):

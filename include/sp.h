@@ -127,7 +127,8 @@ typedef struct {
     double string_length;   /* (pierced[0] + pierced[1] + pierced[2]) * dx */
 } sp_diag;
 
-/* Plan summary of one simulation (traffic is of this design, per band). */
+/* Plan summary of one simulation (traffic is of this design, per band;
+ * threads, ctas_per_sm and grid are those of the launch of its base). */
 typedef struct {
     int32_t base_B, threads, ctas_per_sm, grid;
     int64_t regions_per_band;
@@ -172,9 +173,10 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *                256 + 128 compute + data-movement workers, the movement
  *                threads moving level k's surfaces while level k+1 is
  *                computed); one manager warp is added.  0 for the default
- *                (128 when every base is 8, else 256); SP_AUTOTUNE to time
- *                the candidates (128, 193, 256 for base 8; 256, 321, 385,
- *                480, 512 for base 16).
+ *                of each base (128 for bases 4 and 8, 256 for 16); SP_AUTOTUNE
+ *                to time the candidates for the largest base (128, 193, 256
+ *                for base 8; 256, 321, 385, 480, 512 for base 16), smaller
+ *                bases keeping their default.  A value applies to every base.
  *                The autotuner runs 16-step calls on scratch copies of the
  *                current state (sides above 128 cells are cut to 128 or 120),
  *                on the grid's stream; the state itself is not modified.
@@ -190,7 +192,8 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 
 /*
  * sp_evolve -- advance every simulation by n_steps leapfrog steps.
- * Whole bands of B/2 steps run as regions in one persistent launch; a
+ * Whole bands of B/2 steps run as regions in one persistent launch per
+ * distinct base (largest base first, each launch sized for its base); a
  * remainder of fewer than B/2 steps runs as whole-grid steps with the same
  * arithmetic.  SP_MONOLITHIC runs every step as a whole-grid sweep (bit-exact
  * with the region path).  Unless SP_ASYNC is given the call synchronises the

@@ -28,11 +28,28 @@ namespace {
 
 struct TablesOnDevice {
     sp::TileTables host;
-    sp::TablesDev dev;  // host copy of the device descriptor
-    int index = 0;      // position in the launch's table array
+    sp::TablesDev dev;             // host copy of the device descriptor
+    sp::TablesDev *d_dev = nullptr;  // device copy (the only table of its launch)
     unsigned short *d_imp = nullptr;
     int2 *d_exp = nullptr;
 };
+
+// One persistent launch per region base: simulations of the same base share a
+// launch sized (shared memory, CTAs per SM) for that base alone.
+struct GroupCfg {
+    int B = 0, threads = 0, ctas_per_sm = 0, grid = 0;
+    size_t smem = 0;
+};
+
+// A group's launch in one call.
+struct GroupLaunch {
+    GroupCfg cfg;
+    sp::RegionArgs a;
+    size_t sim_off = 0;  // first descriptor of the group in the call's array
+    unsigned roff = 0;   // first region id of the group (trace, features, buckets)
+};
+
+constexpr int kMaxGroups = 4;  // distinct region bases of a plan (4, 8, 16)
 
 struct SweepGraph {
     cudaGraphExec_t exec = nullptr;
@@ -142,13 +159,10 @@ struct sp_grid {
     std::vector<int64_t> level;
     // plan
     bool planned = false;
-    int threads = 0, max_B = 0, ctas_per_sm = 0, grid = 0, order = 0;
-    size_t smem = 0;
+    int threads = 0, max_B = 0, order = 0;
     std::vector<int> B;
     std::map<int, TablesOnDevice> tables;
-    sp::TablesDev *d_tabs = nullptr;
-    int n_tabs = 0;
-    int imp_smem_units = 0;  // 16-bit import entries of all tables
+    std::vector<GroupCfg> groups;  // one per distinct base, largest first
     std::vector<float2 *> mbox;
     std::vector<long long> mb_slot;
     std::vector<std::array<long long, sp::kTypes>> mb_type_off;
@@ -333,24 +347,17 @@ int build_device_tables(sp_grid *g, int B)
 
 // One contiguous device array of every table the plan uses; SimDev::tab_index
 // picks the entry (the region kernel copies the array into shared memory).
-int upload_table_array(sp_grid *g)
+int upload_tables(sp_grid *g)
 {
-    std::vector<sp::TablesDev> arr;
-    int idx = 0, imp_smem = 0;
     for (auto &kv : g->tables) {
-        kv.second.index = idx++;
-        kv.second.dev.imp_smem = imp_smem;
-        imp_smem += kv.second.dev.imp_n;
-        arr.push_back(kv.second.dev);
+        TablesOnDevice &td = kv.second;
+        if (td.d_dev) continue;
+        td.dev.imp_smem = 0;  // the only table of its launch: import lists at the start of the area
+        cudaError_t e = cudaMalloc((void **)&td.d_dev, sizeof(sp::TablesDev));
+        if (e == cudaSuccess) e = cudaMemcpy(td.d_dev, &td.dev, sizeof(sp::TablesDev), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return SP_ENOMEM;
     }
-    g->imp_smem_units = imp_smem;
-    cudaFree(g->d_tabs);
-    g->d_tabs = nullptr;
-    cudaError_t e = cudaMalloc((void **)&g->d_tabs, arr.size() * sizeof(sp::TablesDev));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(g->d_tabs, arr.data(), arr.size() * sizeof(sp::TablesDev), cudaMemcpyHostToDevice);
-    g->n_tabs = (int)arr.size();
-    return e == cudaSuccess ? SP_OK : SP_ENOMEM;
+    return SP_OK;
 }
 
 void free_plan(sp_grid *g)
@@ -358,11 +365,10 @@ void free_plan(sp_grid *g)
     for (auto &kv : g->tables) {
         cudaFree(kv.second.d_imp);
         cudaFree(kv.second.d_exp);
+        cudaFree(kv.second.d_dev);
     }
     g->tables.clear();
-    cudaFree(g->d_tabs);
-    g->d_tabs = nullptr;
-    g->n_tabs = 0;
+    g->groups.clear();
     for (float2 *m : g->mbox) cudaFree(m);
     g->mbox.clear();
     if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);
@@ -389,12 +395,14 @@ int default_threads(int B) { return B <= 8 ? 128 : 256; }
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
 {
-    sp::Ctl ctl;
-    cudaError_t e = cudaMemcpyAsync(&ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, g->stream);
+    sp::Ctl ctl[kMaxGroups];
+    cudaError_t e = cudaMemcpyAsync(ctl, g->d_ctl, sizeof ctl, cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return SP_ECUDA;
-    if (ctl.error == sp::kDevTimeout) return SP_ETIMEOUT;
-    if (ctl.error != 0) return SP_ECUDA;
+    for (const sp::Ctl &c : ctl)
+        if (c.error == sp::kDevTimeout) return SP_ETIMEOUT;
+    for (const sp::Ctl &c : ctl)
+        if (c.error != 0) return SP_ECUDA;
     return SP_OK;
 }
 
@@ -455,10 +463,13 @@ int sweep_steps(sp_grid *g, int s, int64_t nsteps, int64_t first_local, const sp
     return cudaGraphLaunch(sg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-// The launches of one region-path call: reset + persistent region kernel over
-// all simulations' whole bands, then each simulation's remainder steps as
-// whole-grid steps.  Timing events 1 and 2 bracket the region kernel.
-int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool feats, bool capturing)
+// The launches of one region-path call: per region base, the cost-model
+// features and buckets (when asked for), the queue reset and the persistent
+// region kernel over its simulations' whole bands; then each simulation's
+// remainder steps as whole-grid steps.  Timing events 1 and 2 bracket the
+// region kernels.
+int enqueue_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t n_steps, bool timing, bool feats,
+                        bool capturing)
 {
     cudaError_t e = cudaSuccess;
     auto mark = [&](cudaEvent_t ev) {
@@ -466,21 +477,24 @@ int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bo
             e = capturing ? cudaEventRecordWithFlags(ev, g->stream, cudaEventRecordExternal)
                           : cudaEventRecord(ev, g->stream);
     };
-    if (a) {
+    for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
+        const GroupLaunch &gl = groups[gi];
+        const sp::RegionArgs &a = gl.a;
         if (feats) {
             // the previous call's trace feeds feature 15 when it covered the same regions
-            const unsigned long long *prev = g->prev_trace_ok ? g->d_trace : nullptr;
-            e = sp::launch_features(*a, g->d_simf, prev, g->d_feat, g->stream);
-            if (e == cudaSuccess && a->prio) e = sp::model_buckets(g->model, g->d_feat, a->total, g->d_prio, g->stream);
+            const unsigned long long *prev = g->prev_trace_ok ? g->d_trace + 2 * (size_t)gl.roff : nullptr;
+            e = sp::launch_features(a, g->d_simf + gl.sim_off, prev, g->d_feat + (size_t)SP_MODEL_FEATURES * gl.roff,
+                                    g->stream);
+            if (e == cudaSuccess && a.prio)
+                e = sp::model_buckets(g->model, g->d_feat + (size_t)SP_MODEL_FEATURES * gl.roff, a.total,
+                                      g->d_prio + gl.roff, g->stream);
         }
-        if (e == cudaSuccess) e = sp::launch_reset(*a, g->stream);
-        if (timing) mark(g->ev[1]);
-        if (e == cudaSuccess) e = sp::launch_region(*a, g->threads, g->max_B, g->smem, g->grid, g->stream);
-        if (timing) mark(g->ev[2]);
-    } else if (timing) {
-        mark(g->ev[1]);
-        mark(g->ev[2]);
+        if (e == cudaSuccess) e = sp::launch_reset(a, g->stream);
+        if (timing && gi == 0) mark(g->ev[1]);
+        if (e == cudaSuccess) e = sp::launch_region(a, gl.cfg.threads, gl.cfg.B, gl.cfg.smem, gl.cfg.grid, g->stream);
     }
+    if (groups.empty() && timing) mark(g->ev[1]);
+    if (timing) mark(g->ev[2]);
     if (e != cudaSuccess) return SP_ECUDA;
     for (int s = 0; s < g->n_sims; ++s) {
         const int H = g->B[s] / 2;
@@ -495,9 +509,9 @@ int enqueue_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bo
 // Runs the region-path call.  On a capturable stream the launch sequence is
 // recorded once into a CUDA graph and replayed while every by-value launch
 // parameter is unchanged, so a repeated call costs one graph launch.
-int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool timing, bool feats)
+int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t n_steps, bool timing, bool feats)
 {
-    if (g->stream == nullptr || !g->use_graphs) return enqueue_region_call(g, a, n_steps, timing, feats, false);
+    if (g->stream == nullptr || !g->use_graphs) return enqueue_region_call(g, groups, n_steps, timing, feats, false);
     std::vector<unsigned char> key;
     append_key(&key, n_steps);
     append_key(&key, timing);
@@ -506,12 +520,13 @@ int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool t
     append_key(&key, g->d_simf);
     append_key(&key, g->d_prio);
     append_key(&key, g->prev_trace_ok);
-    append_key(&key, a != nullptr);
-    if (a) append_key(&key, *a);
-    append_key(&key, g->threads);
-    append_key(&key, g->max_B);
-    append_key(&key, g->smem);
-    append_key(&key, g->grid);
+    append_key(&key, groups.size());
+    for (const GroupLaunch &gl : groups) {
+        append_key(&key, gl.a);
+        append_key(&key, gl.cfg);
+        append_key(&key, gl.sim_off);
+        append_key(&key, gl.roff);
+    }
     append_key(&key, g->d_tmp);
     append_key(&key, g->d_coef);
     for (int s = 0; s < g->n_sims; ++s) {
@@ -527,7 +542,7 @@ int run_region_call(sp_grid *g, const sp::RegionArgs *a, int64_t n_steps, bool t
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return SP_ECUDA;
-        const int rc = enqueue_region_call(g, a, n_steps, timing, feats, true);
+        const int rc = enqueue_region_call(g, groups, n_steps, timing, feats, true);
         e = cudaStreamEndCapture(g->stream, &graph);
         if (rc != SP_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -554,8 +569,10 @@ bool valid_threads(int t)
 
 
 // Builds the plan for fixed region bases (one per simulation) and worker
-// count (0 = default for the largest base).
-int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, const char *model_path)
+// count: threads = 0 gives every base its default; otherwise every base gets
+// threads, or only the largest base when largest_only is set.
+int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, const char *model_path,
+               bool largest_only = false)
 {
     free_plan(g);
     if (g->model) sp_model_destroy(g->model);
@@ -572,14 +589,26 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
         int rc = build_device_tables(g, Bs[s]);
         if (rc != SP_OK) return rc;
     }
-    int rct = upload_table_array(g);
+    int rct = upload_tables(g);
     if (rct != SP_OK) return rct;
-    g->threads = threads ? threads : default_threads(g->max_B);
-    g->smem = sp::region_smem_bytes(g->max_B, g->n_tabs, g->n_sims, g->imp_smem_units);
-    if (g->smem > 227 * 1024) return SP_EINVAL;
-    cudaError_t e = sp::region_occupancy(g->threads, g->smem, &g->ctas_per_sm);
-    if (e != cudaSuccess || g->ctas_per_sm < 1) return SP_EINVAL;
-    g->grid = g->ctas_per_sm * g->sm_count;
+    // one launch configuration per base, largest base first
+    cudaError_t e = cudaSuccess;
+    g->threads = threads;
+    for (auto it = g->tables.rbegin(); it != g->tables.rend(); ++it) {
+        GroupCfg c;
+        c.B = it->first;
+        const bool mine = threads && (!largest_only || c.B == g->max_B);
+        c.threads = mine ? threads : default_threads(c.B);
+        int n_in = 0;
+        for (int s = 0; s < g->n_sims; ++s) n_in += g->B[s] == c.B;
+        c.smem = sp::region_smem_bytes(c.B, 1, n_in, it->second.dev.imp_n);
+        if (c.smem > 227 * 1024) return SP_EINVAL;
+        e = sp::region_occupancy(c.threads, c.smem, &c.ctas_per_sm);
+        if (e != cudaSuccess || c.ctas_per_sm < 1) return SP_EINVAL;
+        c.grid = c.ctas_per_sm * g->sm_count;
+        g->groups.push_back(c);
+    }
+    if ((int)g->groups.size() > kMaxGroups) return SP_EINVAL;
     g->order = order;
     // mailbox ring: two band slots per simulation
     g->mb_slot.assign(g->n_sims, 0);
@@ -674,7 +703,7 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         else
             shapes = {256, 321, 385, 480, 512};
         for (int nt : shapes) {
-            rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr);
+            rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr, block_shape == SP_AUTOTUNE);
             if (rc == SP_EINVAL) continue;  // does not fit this device
             float ms = 0.0f;
             for (int rep = 0; rep < 3 && rc == SP_OK; ++rep) {
@@ -783,8 +812,8 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
             return SP_ENOMEM;
         }
     }
-    e = cudaMalloc((void **)&g->d_ctl, sizeof(sp::Ctl));
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_ctl, 0, sizeof(sp::Ctl), g->stream);
+    e = cudaMalloc((void **)&g->d_ctl, kMaxGroups * sizeof(sp::Ctl));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_ctl, 0, kMaxGroups * sizeof(sp::Ctl), g->stream);
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_eout, 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_wcount, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -805,7 +834,8 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
     g->tune = TuneReport();
     std::vector<int> Bs(g->n_sims);
     int threads = block_shape;
-    if (base_B == SP_AUTOTUNE || block_shape == SP_AUTOTUNE) {
+    const bool tune_shape = block_shape == SP_AUTOTUNE;
+    if (base_B == SP_AUTOTUNE || tune_shape) {
         const int rc = autotune(g, base_B, block_shape, &Bs, &threads);
         if (rc != SP_OK) return rc;
     } else {
@@ -814,7 +844,7 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
             if (Bs[s] < 0) return SP_EINVAL;
         }
     }
-    return plan_fixed(g, Bs, threads, order, model_path);
+    return plan_fixed(g, Bs, threads, order, model_path, tune_shape);
 }
 
 int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
@@ -860,63 +890,92 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
         for (int s = 0; s < g->n_sims && rc == SP_OK; ++s)
             rc = sweep_steps(g, s, n_steps, 0, g->d_coef + (size_t)s * n_steps);
     } else {
-        // whole bands as regions, in one persistent launch over all simulations
-        sp::RegionArgs launch;
-        bool have_region = false, feats = false, prev_trace_ok = false;
+        // whole bands as regions: one persistent launch per region base over all
+        // simulations of that base; region ids run on across the groups
+        bool feats = false, prev_trace_ok = false;
         std::vector<sp::SimDev> sims;
         std::vector<int> sim_of;
-        unsigned total = 0, seeds = 0;
+        std::vector<GroupLaunch> launches;
+        unsigned all_total = 0, max_total = 0;
         g->last_tile_base.assign(g->n_sims, 0);
         g->last_tiles.assign(g->n_sims, 0);
-        for (int s = 0; s < g->n_sims; ++s) {
-            const int B = g->B[s], H = B / 2;
+        const bool learned = g->order == SP_ORDER_LEARNED && g->model;
+        const bool trace = (flags & SP_TRACE) != 0;
+        feats = learned || (flags & SP_FEATURES) != 0;
+        for (const GroupCfg &c : g->groups) {
+            const int B = c.B, H = B / 2;
             const int64_t nb = n_steps / H;
             if (nb == 0) continue;
-            const TablesOnDevice &td = g->tables[B];
-            sp::SimDev d;
-            std::memset(&d, 0, sizeof d);
-            for (int k = 0; k < 3; ++k) {
-                d.n[k] = g->p[s].n[k];
-                d.J[k] = d.n[k] / B;
+            GroupLaunch gl;
+            gl.cfg = c;
+            gl.sim_off = sims.size();
+            gl.roff = all_total;
+            unsigned total = 0, seeds = 0;
+            for (int s = 0; s < g->n_sims; ++s) {
+                if (g->B[s] != B) continue;
+                sp::SimDev d;
+                std::memset(&d, 0, sizeof d);
+                for (int k = 0; k < 3; ++k) {
+                    d.n[k] = g->p[s].n[k];
+                    d.J[k] = d.n[k] / B;
+                }
+                d.Jtot = d.J[0] * d.J[1] * d.J[2];
+                d.B = B;
+                d.H = H;
+                d.P = B + 2;
+                d.nbands = (int)nb;
+                const unsigned long long tiles = (unsigned long long)nb * 8ull * (unsigned long long)d.Jtot;
+                if ((unsigned long long)all_total + total + tiles > 0x7fffffffull) return SP_EINVAL;
+                d.tile_base = total;
+                d.tiles = (unsigned)tiles;
+                d.seed_base = seeds;
+                d.coef = g->d_coef + (size_t)s * n_steps;
+                d.q = phys_const(g->p[s]);
+                d.phi = g->phi[s];
+                d.pc = g->pc[s];
+                d.mbox = g->mbox[s];
+                d.mb_slot = g->mb_slot[s];
+                for (int S = 0; S < sp::kTypes; ++S) d.mb_type_off[S] = g->mb_type_off[s][S];
+                d.tab = g->tables[B].d_dev;
+                d.tab_index = 0;
+                g->last_tile_base[s] = all_total + total;
+                g->last_tiles[s] = d.tiles;
+                total += d.tiles;
+                seeds += (unsigned)d.Jtot;
+                sims.push_back(d);
+                sim_of.push_back(s);
             }
-            d.Jtot = d.J[0] * d.J[1] * d.J[2];
-            d.B = B;
-            d.H = H;
-            d.P = B + 2;
-            d.nbands = (int)nb;
-            const unsigned long long tiles = (unsigned long long)nb * 8ull * (unsigned long long)d.Jtot;
-            if ((unsigned long long)total + tiles > 0x7fffffffull) return SP_EINVAL;
-            d.tile_base = total;
-            d.tiles = (unsigned)tiles;
-            d.seed_base = seeds;
-            d.coef = g->d_coef + (size_t)s * n_steps;
-            d.q = phys_const(g->p[s]);
-            d.phi = g->phi[s];
-            d.pc = g->pc[s];
-            d.mbox = g->mbox[s];
-            d.mb_slot = g->mb_slot[s];
-            for (int S = 0; S < sp::kTypes; ++S) d.mb_type_off[S] = g->mb_type_off[s][S];
-            d.tab = g->d_tabs + td.index;
-            d.tab_index = td.index;
-            g->last_tile_base[s] = total;
-            g->last_tiles[s] = d.tiles;
-            total += d.tiles;
-            seeds += (unsigned)d.Jtot;
-            sims.push_back(d);
-            sim_of.push_back(s);
+            if (total == 0) continue;
+            sp::RegionArgs &ra = gl.a;
+            std::memset(&ra, 0, sizeof ra);  // padding too: the bytes are a graph key
+            ra.tabs = g->tables[B].d_dev;
+            ra.n_tabs = 1;
+            ra.n_sims = (int)(sims.size() - gl.sim_off);
+            ra.total = total;
+            ra.n_seed = seeds;
+            ra.ctl = g->d_ctl + launches.size();
+            const long long fd = (long long)g->fault_drop - (long long)all_total;
+            ra.fault_drop = (g->fault_drop >= 0 && fd >= 0 && fd < (long long)total) ? (int)fd : -1;
+            launches.push_back(gl);
+            all_total += total;
+            max_total = std::max(max_total, total);
         }
-        if (!sims.empty()) {
+        if (!launches.empty()) {
             e = grow(&g->d_sims, &g->cap_sims, sims.size());
-            if (e == cudaSuccess) e = grow(&g->d_counters, &g->cap_counters, total);
-            const bool learned = g->order == SP_ORDER_LEARNED && g->model;
-            feats = learned || (flags & SP_FEATURES) != 0;
-            if (e == cudaSuccess) e = grow(&g->d_queue, &g->cap_queue, total);
-            const bool trace = (flags & SP_TRACE) != 0;
-            if (e == cudaSuccess && trace) e = grow(&g->d_trace, &g->cap_trace, 2 * (size_t)total);
-            if (e == cudaSuccess && feats) e = grow(&g->d_feat, &g->cap_feat, (size_t)SP_MODEL_FEATURES * total);
+            if (e == cudaSuccess) e = grow(&g->d_counters, &g->cap_counters, max_total);
+            if (e == cudaSuccess) e = grow(&g->d_queue, &g->cap_queue, max_total);
+            if (e == cudaSuccess && trace) e = grow(&g->d_trace, &g->cap_trace, 2 * (size_t)all_total);
+            if (e == cudaSuccess && feats) e = grow(&g->d_feat, &g->cap_feat, (size_t)SP_MODEL_FEATURES * all_total);
             if (e == cudaSuccess && feats) e = grow(&g->d_simf, &g->cap_simf, sims.size());
-            if (e == cudaSuccess && learned) e = grow(&g->d_prio, &g->cap_prio, (size_t)total);
+            if (e == cudaSuccess && learned) e = grow(&g->d_prio, &g->cap_prio, (size_t)all_total);
             if (e != cudaSuccess) return SP_ENOMEM;
+            for (GroupLaunch &gl : launches) {  // device addresses, now that the buffers exist
+                gl.a.sims = g->d_sims + gl.sim_off;
+                gl.a.counters = g->d_counters;
+                gl.a.queue = g->d_queue;
+                gl.a.trace = trace ? g->d_trace + 2 * (size_t)gl.roff : nullptr;
+                gl.a.prio = learned ? g->d_prio + gl.roff : nullptr;
+            }
             if (feats) {
                 std::vector<float4> simf(sims.size());
                 for (size_t i = 0; i < sims.size(); ++i) {
@@ -937,32 +996,18 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             }
             if (g->up_limit != g->wait_limit_ns) {
                 unsigned long long lim = g->wait_limit_ns;
-                e = cudaMemcpyAsync(&g->d_ctl->wait_limit_ns, &lim, sizeof lim, cudaMemcpyHostToDevice, g->stream);
+                for (int i = 0; i < kMaxGroups && e == cudaSuccess; ++i)
+                    e = cudaMemcpyAsync(&g->d_ctl[i].wait_limit_ns, &lim, sizeof lim, cudaMemcpyHostToDevice,
+                                        g->stream);
                 if (e != cudaSuccess) return SP_ECUDA;
                 g->up_limit = lim;
             }
-            sp::RegionArgs a;
-            std::memset(&a, 0, sizeof a);  // padding too: the bytes are a graph key
-            a.sims = g->d_sims;
-            a.tabs = g->d_tabs;
-            a.n_tabs = g->n_tabs;
-            a.n_sims = (int)sims.size();
-            a.total = total;
-            a.n_seed = seeds;
-            a.counters = g->d_counters;
-            a.queue = g->d_queue;
-            a.ctl = g->d_ctl;
-            a.trace = trace ? g->d_trace : nullptr;
-            a.prio = learned ? g->d_prio : nullptr;
-            a.fault_drop = g->fault_drop;
-            prev_trace_ok = g->trace_total == total;  // the trace buffer still holds a call of this layout
-            if (trace) g->trace_total = total;
+            prev_trace_ok = g->trace_total == all_total;  // the trace buffer still holds a call of this layout
+            if (trace) g->trace_total = all_total;
             g->last_traced = trace;
             g->last_features = feats;
-            g->last_total = total;
-            launch = a;
+            g->last_total = all_total;
         }
-        have_region = !sims.empty();
         // remainder steps of each simulation: whole-grid steps, same arithmetic
         for (int s = 0; s < g->n_sims; ++s) {
             const int H = g->B[s] / 2;
@@ -973,7 +1018,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
             }
         }
         g->prev_trace_ok = prev_trace_ok;
-        rc = run_region_call(g, have_region ? &launch : nullptr, n_steps, timing, feats);
+        rc = run_region_call(g, launches, n_steps, timing, feats);
     }
     if (rc != SP_OK) return rc;
     if (timing) {
@@ -1118,9 +1163,12 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         sp_plan_info info;
         std::memset(&info, 0, sizeof info);
         info.base_B = g->B[sim];
-        info.threads = g->threads;  // an odd value names the warp-specialised kernel
-        info.ctas_per_sm = g->ctas_per_sm;
-        info.grid = g->grid;
+        for (const GroupCfg &c : g->groups)
+            if (c.B == g->B[sim]) {
+                info.threads = c.threads;  // an odd value names the warp-specialised kernel
+                info.ctas_per_sm = c.ctas_per_sm;
+                info.grid = c.grid;
+            }
         info.regions_per_band = ps.regions_per_band;
         info.updates_per_band = ps.updates_per_band;
         info.bytes_read_per_band = ps.bytes_read_per_band;
