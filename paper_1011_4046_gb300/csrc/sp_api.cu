@@ -244,6 +244,24 @@ bool decode_exact(const sp::Box3 *boxes, int last, const float (*rcp)[2])
     return true;
 }
 
+// The same for the 2x2x2-block decode of the active boxes: block index
+// m < (w0/2)(w1/2)(w2/2) -> (m / (w2/2)) / (w0/2); every extent must be even.
+bool block_decode_exact(const sp::Box3 *boxes, int last, const float (*rcp)[2])
+{
+    for (int k = 0; k <= last; ++k) {
+        const sp::Box3 &b = boxes[k];
+        const int w0 = b.hi[0] - b.lo[0], w1 = b.hi[1] - b.lo[1], w2 = b.hi[2] - b.lo[2];
+        if (w0 <= 0 || w1 <= 0 || w2 <= 0) continue;
+        if ((w0 | w1 | w2) & 1) return false;
+        const int a = w0 / 2, c = w2 / 2;
+        for (int m = 0; m < a * (w1 / 2) * c; ++m) {
+            const int r = sp::fdiv(m, rcp[k][0]);
+            if (r != m / c || sp::fdiv(r, rcp[k][1]) != r / a) return false;
+        }
+    }
+    return true;
+}
+
 int build_device_tables(sp_grid *g, int B)
 {
     if (g->tables.count(B)) return SP_OK;
@@ -267,12 +285,13 @@ int build_device_tables(sp_grid *g, int B)
         m.base_phi = t.base_phi[S];
         m.base_pc = t.base_pc[S];
         for (int k = 0; k <= sp::kMaxH; ++k)
-            for (int d = 0; d < 2; ++d) {
-                int w = t.active[S][k].hi[d] - t.active[S][k].lo[d];
-                m.rcp_active[k][d] = w > 0 ? 1.0f / (float)w : 0.0f;
+            for (int q = 0; q < 2; ++q) {
+                const int d = q == 0 ? 2 : 0;  // blocks along z, then along x
+                const int w = (t.active[S][k].hi[d] - t.active[S][k].lo[d]) / 2;
+                m.rcp_active[k][q] = w > 0 ? 1.0f / (float)w : 0.0f;
             }
         for (int d = 0; d < 2; ++d) m.rcp_base[d] = 1.0f / (float)(t.base_phi[S].hi[d] - t.base_phi[S].lo[d]);
-        if (!decode_exact(m.active, t.H, m.rcp_active) || !decode_exact(&m.base_phi, 0, &m.rcp_base))
+        if (!block_decode_exact(m.active, t.H, m.rcp_active) || !decode_exact(&m.base_phi, 0, &m.rcp_base))
             return SP_EINVAL;
         for (int L = 0; L < sp::kMaxH; ++L) {
             m.mb_level_off[L] = t.mb_level_off[S][L];

@@ -16,8 +16,9 @@ struct alignas(16) TypeMeta {
     int prev_preds, pad0, pad1, pad2;
     Box3 active[kMaxH + 1];
     Box3 base_phi, base_pc;
-    // 1/w of the two inner extents of each box, rounded to FP32 (exact
-    // quotient decode, see fdiv below)
+    // exact quotient decode (see fdiv below), reciprocals rounded to FP32:
+    // of each active box, 1/(w2/2) and 1/(w0/2) (its cells are taken in
+    // 2x2x2 blocks, see block_cell); of the base box, 1/w0 and 1/w1
     float rcp_active[kMaxH + 1][2];
     float rcp_base[2];
     int imp_full_off[kMaxH], imp_full_n[kMaxH];
@@ -246,6 +247,21 @@ inline
     int fdiv(int i, float rcp)
 {
     return (int)(((float)i + 0.5f) * rcp);
+}
+
+// Shared-memory slot of the (pi, c) pair of local cell c = (z B + y) B + x
+// (B a power of two, lgB = log2 B): bits 1 and 2 of x are flipped by the
+// parities of y and z.  A row of cells keeps distinct banks (x is only
+// permuted within its row), and so does a 2x2x2 block of cells, whose eight
+// float4 slots are then eight different 16-byte bank groups.
+#if defined(__CUDACC__)
+__host__ __device__ __forceinline__
+#else
+inline
+#endif
+    int pc_slot(int c, int lgB, int B)
+{
+    return c ^ (((((c >> lgB) & 1) << 1) | (((c >> (2 * lgB)) & 1) << 2)) & (B - 1));
 }
 
 }  // namespace sp

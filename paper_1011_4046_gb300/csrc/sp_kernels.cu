@@ -240,7 +240,7 @@ __host__ __device__ constexpr int region_cells_per_step(int nw) { return nw <= 1
 __host__ __device__ constexpr int region_min_blocks(int nw) { return nw <= 128 ? 4 : 1; }
 
 __device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, float2 *const *mb_of,
-                                           const float2 *__restrict__ phi, const float4 *__restrict__ pc)
+                                           const float2 *__restrict__ phi, const float4 *__restrict__ pc, int lgB)
 {
     const int code = (e.x >> 25) & 63;
     float2 *mb = mb_of[code];
@@ -249,18 +249,19 @@ __device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, fl
         const TypeMeta &C = T.type[code & 7];
         const int off = C.mb_level_off[L];
         const int dst_pc = off + 2 * (e.y - off - 2 * C.imp_full_n[L]);
-        __stcg(reinterpret_cast<float4 *>(mb + dst_pc), pc[(e.x >> 13) & 0xFFF]);
+        __stcg(reinterpret_cast<float4 *>(mb + dst_pc), pc[pc_slot((e.x >> 13) & 0xFFF, lgB, T.B)]);
     }
 }
 
 template <int NW>
 __device__ __forceinline__ void export_entries(const int2 *__restrict__ el, int ne, const int2 (&pre)[kExportPrefetch],
                                                int L, const TablesDev &T, float2 *const *mb_of,
-                                               const float2 *__restrict__ phi, const float4 *__restrict__ pc, int wt)
+                                               const float2 *__restrict__ phi, const float4 *__restrict__ pc, int lgB,
+                                               int wt)
 {
 #pragma unroll
     for (int u = 0; u < kExportPrefetch; ++u)
-        if (wt + u * NW < ne) export_one(pre[u], L, T, mb_of, phi, pc);
+        if (wt + u * NW < ne) export_one(pre[u], L, T, mb_of, phi, pc, lgB);
     for (int base = wt + kExportPrefetch * NW; base < ne; base += kExportBatch * NW) {
         int2 e[kExportBatch];
 #pragma unroll
@@ -268,7 +269,7 @@ __device__ __forceinline__ void export_entries(const int2 *__restrict__ el, int 
             if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
 #pragma unroll
         for (int u = 0; u < kExportBatch; ++u)
-            if (base + u * NW < ne) export_one(e[u], L, T, mb_of, phi, pc);
+            if (base + u * NW < ne) export_one(e[u], L, T, mb_of, phi, pc, lgB);
     }
 }
 
@@ -294,24 +295,46 @@ __device__ __forceinline__ void import_level(const float2 *__restrict__ mb, int 
     for (int i = wt; i < nf; i += NW) {
         const int c = fl[i];
         const int pidx = (((c >> (2 * lgB)) + 1) * P + ((c >> lgB) & (B - 1)) + 1) * P + (c & (B - 1)) + 1;
-        cp_async16(pc_s + c, mb + 2 * i);
+        cp_async16(pc_s + pc_slot(c, lgB, B), mb + 2 * i);
         cp_async8(dst + pidx, mb + 2 * nf + i);
     }
     for (int i = wt; i < np; i += NW) cp_async8(dst + pl[i], mb + 3 * nf + i);
 }
 
-// One site of level k: linear index i over the active box A (x fastest).
-__device__ __forceinline__ void evolve_cell(int i, const Box3 &A, int w0, int w1, float r0, float r1, int P, int PP,
+// The cells of level k are taken in 2x2x2 blocks (every extent of an active
+// box is even): linear index j -> block m = j >> 3, counted z fastest, then x,
+// then y (a = w0/2 and c = w2/2 blocks along x and z; rc = 1/c, ra = 1/a),
+// and corner j & 7 of the block.  Eight consecutive threads then cover one
+// block: a block pair along z spans all sixteen 8-byte bank pairs of a phi
+// buffer (pitch B+2 = 2 mod 16 cells, plane pitch = 4 mod 16), and pc_slot
+// gives the block's eight (pi, c) pairs eight different bank groups.
+__device__ __forceinline__ void block_cell(int j, const Box3 &A, int a, int c, float rc, float ra, int &ux, int &uy,
+                                           int &uz)
+{
+    const int m = j >> 3;
+    const int r = fdiv(m, rc);   // m / c
+    const int jj = fdiv(r, ra);  // r / a
+    ux = A.lo[0] + 2 * (r - jj * a) + (j & 1);
+    uy = A.lo[1] + 2 * jj + ((j >> 1) & 1);
+    uz = A.lo[2] + 2 * (m - r * c) + ((j >> 2) & 1);
+}
+
+// Shared-memory slot of the (pi, c) pair of the cell at local u-coordinates.
+__device__ __forceinline__ int pc_slot_of(int ux, int uy, int uz, int B)
+{
+    const int x = ux - 1, y = uy - 1, z = uz - 1;
+    return (z * B + y) * B + (x ^ ((((y & 1) << 1) | ((z & 1) << 2)) & (B - 1)));
+}
+
+// One site of level k (linear index i, see block_cell).
+__device__ __forceinline__ void evolve_cell(int i, const Box3 &A, int a, int c, float rc, float ra, int P, int PP,
                                             int B, const float2 *__restrict__ prev_buf, float2 *__restrict__ cur,
                                             float4 *__restrict__ pc_s, const LevelCoef &co, const PhysConst &q)
 {
-    const int t1 = fdiv(i, r0);
-    const int t2 = fdiv(t1, r1);
-    const int ux = A.lo[0] + i - t1 * w0;
-    const int uy = A.lo[1] + t1 - t2 * w1;
-    const int uz = A.lo[2] + t2;
+    int ux, uy, uz;
+    block_cell(i, A, a, c, rc, ra, ux, uy, uz);
     const int pidx = (uz * P + uy) * P + ux;
-    const int cidx = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+    const int cidx = pc_slot_of(ux, uy, uz, B);
     const float4 pc = pc_s[cidx];
     float2 pi = make_float2(pc.x, pc.y), cc = make_float2(pc.z, pc.w);
     const float2 nphi = site_update(prev_buf[pidx], prev_buf[pidx - 1], prev_buf[pidx + 1], prev_buf[pidx - P],
@@ -325,7 +348,7 @@ __device__ __forceinline__ void evolve_cell(int i, const Box3 &A, int w0, int w1
 // independent instruction streams (the compiler cannot prove that a store to
 // one cell's (pi, c) does not alias another cell's load).
 template <int U>
-__device__ __forceinline__ void evolve_cells(int i, int stride, const Box3 &A, int w0, int w1, float r0, float r1,
+__device__ __forceinline__ void evolve_cells(int i, int stride, const Box3 &A, int a, int cz, float rc, float ra,
                                              int P, int PP, int B, const float2 *__restrict__ prev_buf,
                                              float2 *__restrict__ cur, float4 *__restrict__ pc_s, const LevelCoef &co,
                                              const PhysConst &q)
@@ -335,14 +358,10 @@ __device__ __forceinline__ void evolve_cells(int i, int stride, const Box3 &A, i
     float4 pc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int j = i + u * stride;
-        const int t1 = fdiv(j, r0);
-        const int t2 = fdiv(t1, r1);
-        const int ux = A.lo[0] + j - t1 * w0;
-        const int uy = A.lo[1] + t1 - t2 * w1;
-        const int uz = A.lo[2] + t2;
+        int ux, uy, uz;
+        block_cell(i + u * stride, A, a, cz, rc, ra, ux, uy, uz);
         pidx[u] = (uz * P + uy) * P + ux;
-        cidx[u] = ((uz - 1) * B + (uy - 1)) * B + (ux - 1);
+        cidx[u] = pc_slot_of(ux, uy, uz, B);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -377,7 +396,7 @@ __device__ void manager_loop(const RegionArgs &a, const TablesDev *s_tabs, int *
     const unsigned long long limit = a.ctl->wait_limit_ns;
     int seq = 0;           // handoffs made
     int pending = -1;      // region handed at seq, not yet released
-    RegionInfo pend_info;
+    RegionInfo pend_info = {};
     unsigned idx = 0;
     if (lane == 0) idx = atomicAdd(&a.ctl->head, 1u);
     idx = __shfl_sync(0xffffffffu, idx, 0);
@@ -536,6 +555,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band, jl = r.jl;
         const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
+        const int lgB = 31 - __clz(B);  // B is a power of two
         int gbase[3];  // global coordinate of local u = 0 along each axis
         for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
         const int nx = sd.n[0], ny = sd.n[1], nz = sd.n[2];
@@ -574,7 +594,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
                     if (out > 1) continue;
                     const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
                     cp_async8(phi_buf0 + (uz * P + uy) * P + ux, sd.phi + gi);
-                    if (out == 0) cp_async16(pc_s + ((uz - 1) * B + (uy - 1)) * B + (ux - 1), sd.pc + gi);
+                    if (out == 0) cp_async16(pc_s + pc_slot_of(ux, uy, uz, B), sd.pc + gi);
                 }
             }
             cp_async_commit();
@@ -611,16 +631,17 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
             // ---- evolve the cells of level k, several independent cells per step ----
             const LevelCoef co = s_coef[k - 1];
             const Box3 A = M.active[k];
-            const float r0 = M.rcp_active[k][0], r1 = M.rcp_active[k][1];
-            const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
-            const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
+            const float rc = M.rcp_active[k][0], ra = M.rcp_active[k][1];
+            const int w0 = A.hi[0] - A.lo[0], w2 = A.hi[2] - A.lo[2];
+            const int cnt = w0 * (A.hi[1] - A.lo[1]) * w2;
+            const int a = w0 >> 1, cz = w2 >> 1;  // 2x2x2 blocks along x and z
             int i = wt;
             constexpr int U = region_cells_per_step(NW);
             for (; i + (U - 1) * NW < cnt; i += U * NW)
-                evolve_cells<U>(i, NW, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
-            for (; i < cnt; i += NW) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+                evolve_cells<U>(i, NW, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
+            for (; i < cnt; i += NW) evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
             // ---- final surface of level k-1 (read-only data of level k-1) ----
-            if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, wt);
+            if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, lgB, wt);
         }
         const float2 *last = (nlev & 1) ? phi_buf1 : phi_buf0;
         if (nlev <= H - 1) {
@@ -629,7 +650,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
             const int2 *el = T.exp + M.exp_off[nlev];
             prefetch_entries<NW>(el, ne, pre, wt);
             named_barrier(kWorkerBarrier, NW);
-            export_entries<NW>(el, ne, pre, nlev, T, s_mb, last, pc_s, wt);
+            export_entries<NW>(el, ne, pre, nlev, T, s_mb, last, pc_s, lgB, wt);
         } else {
             named_barrier(kWorkerBarrier, NW);
             // ---- tops of the inverted pyramid: the next band's base ----
@@ -643,7 +664,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
                 for (int uz = 1; uz <= B; ++uz) {
                     const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
                     __stcg(sd.phi + gi, last[(uz * P + uy) * P + ux]);
-                    __stcg(sd.pc + gi, pc_s[((uz - 1) * B + (uy - 1)) * B + (ux - 1)]);
+                    __stcg(sd.pc + gi, pc_s[pc_slot_of(ux, uy, uz, B)]);
                 }
             }
         }
@@ -744,6 +765,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band;
         const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
+        const int lgB = 31 - __clz(B);  // B is a power of two
         const int nlev = M.levels;
         int gbase[3];  // global coordinate of local u = 0 along each axis
         for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
@@ -784,7 +806,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                         if (out > 1) continue;
                         const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
                         cp_async8(phi_buf0 + (uz * P + uy) * P + ux, sd.phi + gi);
-                        if (out == 0) cp_async16(pc_s + ((uz - 1) * B + (uy - 1)) * B + (ux - 1), sd.pc + gi);
+                        if (out == 0) cp_async16(pc_s + pc_slot_of(ux, uy, uz, B), sd.pc + gi);
                     }
                 }
             }
@@ -800,7 +822,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     const int ne = M.exp_n[k - 1];
                     const int2 *el = T.exp + M.exp_off[k - 1];
                     prefetch_entries<ND>(el, ne, pre, dt);
-                    if (ne > 0) export_entries<ND>(el, ne, pre, k - 1, T, s_mb, (k & 1) ? phi_buf0 : phi_buf1, pc_s, dt);
+                    if (ne > 0) export_entries<ND>(el, ne, pre, k - 1, T, s_mb, (k & 1) ? phi_buf0 : phi_buf1, pc_s, lgB, dt);
                 }
                 if (k < nlev && k <= H - 1) {  // sloped initial surface of level k
                     const int nf = M.imp_full_n[k], np = M.imp_phi_n[k];
@@ -822,15 +844,16 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                 float2 *__restrict__ cur = (k & 1) ? phi_buf1 : phi_buf0;
                 const LevelCoef co = s_coef[k - 1];
                 const Box3 A = M.active[k];
-                const float r0 = M.rcp_active[k][0], r1 = M.rcp_active[k][1];
-                const int w0 = A.hi[0] - A.lo[0], w1 = A.hi[1] - A.lo[1];
-                const int cnt = w0 * w1 * (A.hi[2] - A.lo[2]);
+                const float rc = M.rcp_active[k][0], ra = M.rcp_active[k][1];
+                const int w0 = A.hi[0] - A.lo[0], w2 = A.hi[2] - A.lo[2];
+                const int cnt = w0 * (A.hi[1] - A.lo[1]) * w2;
+                const int a = w0 >> 1, cz = w2 >> 1;  // 2x2x2 blocks along x and z
                 int i = wt;
                 for (; i + NC < cnt; i += 2 * NC) {
-                    evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
-                    evolve_cell(i + NC, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+                    evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
+                    evolve_cell(i + NC, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
                 }
-                if (i < cnt) evolve_cell(i, A, w0, w1, r0, r1, P, PP, B, prev_buf, cur, pc_s, co, q);
+                if (i < cnt) evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
                 named_arrive(kBarDone, NW);
             }
         }
@@ -847,7 +870,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
 #pragma unroll
                 for (int u = 0; u < kExportBatch; ++u)
-                    if (base + u * NW < ne) export_one(e[u], nlev, T, s_mb, last, pc_s);
+                    if (base + u * NW < ne) export_one(e[u], nlev, T, s_mb, last, pc_s, lgB);
             }
         } else {
             // ---- tops of the inverted pyramid: the next band's base ----
@@ -861,7 +884,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                 for (int uz = 1; uz <= B; ++uz) {
                     const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
                     __stcg(sd.phi + gi, last[(uz * P + uy) * P + ux]);
-                    __stcg(sd.pc + gi, pc_s[((uz - 1) * B + (uy - 1)) * B + (ux - 1)]);
+                    __stcg(sd.pc + gi, pc_s[pc_slot_of(ux, uy, uz, B)]);
                 }
             }
         }
