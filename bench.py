@@ -66,8 +66,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the region kernel and everything that shapes what it moves (tables, launch)
 KERNEL_SOURCES = ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
-                  "paper_1011_4046_gb300/csrc/sp_update.h"]
+                  "paper_1011_4046_gb300/csrc/sp_update.h", "paper_1011_4046_gb300/csrc/sp_api.cu",
+                  "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h"]
 
 
 def ncu_traffic(workload_is_default):

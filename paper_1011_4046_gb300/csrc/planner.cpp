@@ -297,6 +297,37 @@ std::string build_tables(int B, TileTables *tp)
         for (int S = 0; S < kTypes; ++S) v += t.active[S][k].volume();
         if (v != (int64_t)B * B * B) return "regions do not tile the period cell at some level";
     }
+
+    // ---- the GPU kernel's copy schedule: the sloped surface of level L lands
+    // (phi in buffer L & 1, (pi, c) in the region's array) while level L-1 is
+    // computed and the final surface of level L-2 is exported, both from
+    // that buffer; it must touch nothing they read or write ----
+    auto in_box = [](const Box3 &b, int x, int y, int z) {
+        return x >= b.lo[0] && x < b.hi[0] && y >= b.lo[1] && y < b.hi[1] && z >= b.lo[2] && z < b.hi[2];
+    };
+    for (int S = 0; S < kTypes; ++S)
+        for (int L = 1; L <= H - 1; ++L) {
+            const Box3 *A = t.active[S];
+            auto phi_ok = [&](int q) {
+                const int x = q % t.P, y = (q / t.P) % t.P, z = q / (t.P * t.P);
+                if (L - 2 >= 1 && in_box(A[L - 2], x, y, z)) return false;  // written by L-2, exported after L-1
+                if (L - 1 >= 1) {  // read by the 7-point stencil of level L-1
+                    const int nb[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+                    for (const auto &o : nb)
+                        if (in_box(A[L - 1], x + o[0], y + o[1], z + o[2])) return false;
+                }
+                return true;
+            };
+            for (int i = 0; i < t.imp_phi_n[S][L]; ++i)
+                if (!phi_ok(t.imp_phi[t.imp_phi_off[S][L] + i])) return "a sloped-surface copy overtakes a level in flight";
+            for (int i = 0; i < t.imp_full_n[S][L]; ++i) {
+                const int e = t.imp_full[t.imp_full_off[S][L] + i];
+                if (!phi_ok(e & 0xFFFF)) return "a sloped-surface copy overtakes a level in flight";
+                const int c = e >> 16, x = c % B + 1, y = (c / B) % B + 1, z = c / (B * B) + 1;
+                for (int k = std::max(1, L - 2); k <= L; ++k)
+                    if (in_box(A[k], x, y, z)) return "a (pi, c) copy overtakes a level in flight";
+            }
+        }
     return std::string();
 }
 

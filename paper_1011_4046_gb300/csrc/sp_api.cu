@@ -320,25 +320,19 @@ int build_device_tables(sp_grid *g, int B)
     h.imp_n = (int)imp.size();
     h.rcp_B = 1.0f / (float)t.B;
     std::vector<int2> ex(t.exp.size());
+    const int lgB = __builtin_ctz((unsigned)t.B);
     for (size_t i = 0; i < t.exp.size(); ++i) {
         const sp::ExportEntry &e = t.exp[i];
         const int phi = e.src & 0xFFFF, pc = (e.src >> 16) & 0xFFFF;
         const int has_pc = e.dst_pc >= 0;
-        ex[i].x = (int)((unsigned)phi | ((unsigned)(has_pc ? pc : 0) << 13) | ((unsigned)e.code << 25) |
-                        ((unsigned)has_pc << 31));
-        ex[i].y = e.dst_phi;
+        // both mailbox offsets must fit 16 bits, the (pi, c) one in float2 units
+        if (e.dst_phi < 0 || e.dst_phi > 0xFFFF || e.dst_pc > 0xFFFF) return SP_EINVAL;
+        ex[i].x = (int)((unsigned)phi | ((unsigned)(has_pc ? sp::pc_slot(pc, lgB, t.B) : 0) << 13) |
+                        ((unsigned)e.code << 25) | ((unsigned)has_pc << 31));
+        ex[i].y = (int)((unsigned)e.dst_phi | ((unsigned)(has_pc ? e.dst_pc : 0) << 16));
     }
-    // the kernel re-derives the (pi, c) destination and the phi index of a
-    // full import: check both derivations against the planner's tables
-    for (int S = 0; S < sp::kTypes; ++S)
-        for (int L = 1; L < t.H; ++L)
-            for (int i = 0; i < t.exp_n[S][L]; ++i) {
-                const sp::ExportEntry &e = t.exp[t.exp_off[S][L] + i];
-                if (e.dst_pc < 0) continue;
-                const int Sc = e.code & 7;
-                const int off = t.mb_level_off[Sc][L], nf = t.imp_full_n[Sc][L];
-                if (off + 2 * (e.dst_phi - off - 2 * nf) != e.dst_pc) return SP_EINVAL;
-            }
+    // the kernel re-derives the phi index of a full import from its (pi, c)
+    // index: check the derivation against the planner's tables
     for (size_t i = 0; i < t.imp_full.size(); ++i) {
         const int c = t.imp_full[i] >> 16, want = t.imp_full[i] & 0xFFFF;
         const int t1 = sp::fdiv(c, h.rcp_B), t2 = sp::fdiv(t1, h.rcp_B);
@@ -409,7 +403,7 @@ int choose_B(const sp_params &p, int requested)
     return -1;
 }
 
-int default_threads(int B) { return B <= 8 ? 128 : 256; }
+int default_threads(int B) { return B <= 8 ? 128 : 320; }
 
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
@@ -578,12 +572,12 @@ int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t 
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-// Worker counts of the region kernel: 128, 256, 480, 512, 768 (every worker
+// Worker counts of the region kernel: 128, 256, 320, 480, 512, 768 (every worker
 // does every step), or an odd value w + 1 for the warp-specialised kernel with
 // w workers (193: 128 compute + 64 movement; 321: 256 + 64; 385: 256 + 128).
 bool valid_threads(int t)
 {
-    return t == 128 || t == 256 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
+    return t == 128 || t == 256 || t == 320 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
 }
 
 
@@ -720,7 +714,7 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         else if (maxB <= 8)
             shapes = {128, 193, 256};
         else
-            shapes = {256, 321, 385, 480, 512};
+            shapes = {256, 320, 321, 385, 480};
         for (int nt : shapes) {
             rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr, block_shape == SP_AUTOTUNE);
             if (rc == SP_EINVAL) continue;  // does not fit this device

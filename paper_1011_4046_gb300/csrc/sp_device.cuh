@@ -36,10 +36,11 @@ struct alignas(16) TypeMeta {
 // All lists of one base size are copied into shared memory once per launch,
 // at imp_smem (16-bit units) in the kernel's import area.
 //
-// Export entries are 8 bytes: x = phi index (13 bits) | (pi, c) index << 13
-// (12 bits) | consumer code << 25 (6 bits) | has (pi, c) << 31, y = phi offset
-// in the consumer's mailbox; the (pi, c) offset follows from the consumer's
-// level layout.  This packing needs (B+2)^3 <= 8192 and B^3 <= 4096 (B <= 16).
+// Export entries are 8 bytes: x = phi index (13 bits) | (pi, c) shared-memory
+// slot (pc_slot of the cell, 12 bits) << 13 | consumer code << 25 (6 bits) |
+// has (pi, c) << 31, y = phi offset | (pi, c) offset << 16 in the consumer's
+// mailbox (float2 units).  This packing needs (B+2)^3 <= 8192, B^3 <= 4096
+// (B <= 16) and mailboxes of at most 65536 float2.
 struct alignas(16) TablesDev {
     int B, H, P, pad;
     TypeMeta type[kTypes];

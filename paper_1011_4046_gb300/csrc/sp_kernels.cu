@@ -204,19 +204,20 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
 //
 // Worker shared memory, in order: two phi buffers (levels of alternating
 // parity) of (B+2)^3 float2 for the region box plus its halo; one float4
-// (pi, c) per own cell (B^3); the launch's tables (geometry and routing per
-// region type); the simulation descriptors; the band's level coefficients.
-// The tables and descriptors are copied once per launch, so no step of a
-// region waits on a table read from global memory.
+// (pi, c) per own cell (B^3, slots permuted by pc_slot); the launch's tables
+// (geometry and routing per region type); the band's level coefficients; the
+// import lists.  The tables and import lists are copied once per launch and
+// the simulation descriptor travels with the handoff, so no step of a region
+// waits on a table read from global memory (export entries are read through
+// L1, one level ahead).
 //
-// All data a region needs is requested when it starts: the band base and the
-// band's coefficients (copy group 0) and the sloped initial surface of every
-// level L = 1..H-1 (group L), each landing directly in its final place (the
-// level-L phi buffer, L & 1, and the (pi, c) array).  This is safe because the
-// cells imported for level L have, along some inverted axis, a coordinate at
-// least two cells outside what levels L-2 and L-1 read or write; the CPU
-// scaffold executes the same order and must match the whole-grid sweep bit
-// for bit.  Before level k is computed a thread waits for groups 0..k-1.
+// Copies: the band base and the band's coefficients are requested when the
+// region starts (copy group 0), the sloped initial surface of level L
+// (group L) at the start of level L-1, each landing directly in its final
+// place (the level-L phi buffer, L & 1, and the (pi, c) array).  This is safe
+// because the cells imported for level L lie outside everything levels L-2
+// and L-1 read or write (checked on the host for every region type).  Before
+// level k is computed a thread waits for groups 0..k-1.
 //
 // One worker barrier per level.  The face cells of level k-1 are exported
 // after level k is computed, before the next barrier: they are read from the
@@ -228,40 +229,36 @@ constexpr int kWorkerBarrier = 1;
 static_assert(sizeof(SimDev) / 16 <= 32, "the manager warp copies a descriptor with one int4 per lane");
 
 // Export entries of a level are loaded into registers before the compute of
-// the next level (up to kExportPrefetch per worker thread, which covers every
-// level of B <= 16 with 480 workers); any remainder is read in batches.
-constexpr int kExportPrefetch = 6;
+// the next level (up to kExportPrefetch per worker thread); any remainder is
+// read in batches.  Three cover the average level of base 16 with 256
+// workers several times over; more cost registers and unrolled code for
+// entries that rarely exist.
+constexpr int kExportPrefetch = 3;
 constexpr int kExportBatch = 4;
-// Per worker count: independent cell updates in flight per thread, and the
-// CTAs per SM the registers are budgeted for.  128 workers serve base 8,
-// whose small regions fit several CTAs per SM; 256 and more serve base 16,
+// Per worker count: independent cell updates in flight per thread (measured:
+// one for 128 workers, two for 256 and more; four were 3 % slower at base 16),
+// and the CTAs per SM the registers are budgeted for.  128 workers serve base
+// 8, whose small regions fit several CTAs per SM; 256 and more serve base 16,
 // one CTA per SM.
-__host__ __device__ constexpr int region_cells_per_step(int nw) { return nw <= 128 ? 2 : 4; }
+__host__ __device__ constexpr int region_cells_per_step(int nw) { return nw <= 128 ? 1 : 2; }
 __host__ __device__ constexpr int region_min_blocks(int nw) { return nw <= 128 ? 4 : 1; }
 
-__device__ __forceinline__ void export_one(int2 e, int L, const TablesDev &T, float2 *const *mb_of,
-                                           const float2 *__restrict__ phi, const float4 *__restrict__ pc, int lgB)
+__device__ __forceinline__ void export_one(int2 e, float2 *const *mb_of, const float2 *__restrict__ phi,
+                                           const float4 *__restrict__ pc)
 {
-    const int code = (e.x >> 25) & 63;
-    float2 *mb = mb_of[code];
-    __stcg(mb + e.y, phi[e.x & 0x1FFF]);
-    if (e.x < 0) {
-        const TypeMeta &C = T.type[code & 7];
-        const int off = C.mb_level_off[L];
-        const int dst_pc = off + 2 * (e.y - off - 2 * C.imp_full_n[L]);
-        __stcg(reinterpret_cast<float4 *>(mb + dst_pc), pc[pc_slot((e.x >> 13) & 0xFFF, lgB, T.B)]);
-    }
+    float2 *mb = mb_of[(e.x >> 25) & 63];
+    __stcg(mb + (e.y & 0xFFFF), phi[e.x & 0x1FFF]);
+    if (e.x < 0) __stcg(reinterpret_cast<float4 *>(mb + ((unsigned)e.y >> 16)), pc[(e.x >> 13) & 0xFFF]);
 }
 
 template <int NW>
 __device__ __forceinline__ void export_entries(const int2 *__restrict__ el, int ne, const int2 (&pre)[kExportPrefetch],
-                                               int L, const TablesDev &T, float2 *const *mb_of,
-                                               const float2 *__restrict__ phi, const float4 *__restrict__ pc, int lgB,
-                                               int wt)
+                                               float2 *const *mb_of, const float2 *__restrict__ phi,
+                                               const float4 *__restrict__ pc, int wt)
 {
 #pragma unroll
     for (int u = 0; u < kExportPrefetch; ++u)
-        if (wt + u * NW < ne) export_one(pre[u], L, T, mb_of, phi, pc, lgB);
+        if (wt + u * NW < ne) export_one(pre[u], mb_of, phi, pc);
     for (int base = wt + kExportPrefetch * NW; base < ne; base += kExportBatch * NW) {
         int2 e[kExportBatch];
 #pragma unroll
@@ -269,7 +266,7 @@ __device__ __forceinline__ void export_entries(const int2 *__restrict__ el, int 
             if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
 #pragma unroll
         for (int u = 0; u < kExportBatch; ++u)
-            if (base + u * NW < ne) export_one(e[u], L, T, mb_of, phi, pc, lgB);
+            if (base + u * NW < ne) export_one(e[u], mb_of, phi, pc);
     }
 }
 
@@ -555,7 +552,6 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band, jl = r.jl;
         const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
-        const int lgB = 31 - __clz(B);  // B is a power of two
         int gbase[3];  // global coordinate of local u = 0 along each axis
         for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
         const int nx = sd.n[0], ny = sd.n[1], nz = sd.n[2];
@@ -641,7 +637,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
                 evolve_cells<U>(i, NW, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
             for (; i < cnt; i += NW) evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
             // ---- final surface of level k-1 (read-only data of level k-1) ----
-            if (ne > 0) export_entries<NW>(el, ne, pre, k - 1, T, s_mb, prev_buf, pc_s, lgB, wt);
+            if (ne > 0) export_entries<NW>(el, ne, pre, s_mb, prev_buf, pc_s, wt);
         }
         const float2 *last = (nlev & 1) ? phi_buf1 : phi_buf0;
         if (nlev <= H - 1) {
@@ -650,7 +646,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
             const int2 *el = T.exp + M.exp_off[nlev];
             prefetch_entries<NW>(el, ne, pre, wt);
             named_barrier(kWorkerBarrier, NW);
-            export_entries<NW>(el, ne, pre, nlev, T, s_mb, last, pc_s, lgB, wt);
+            export_entries<NW>(el, ne, pre, s_mb, last, pc_s, wt);
         } else {
             named_barrier(kWorkerBarrier, NW);
             // ---- tops of the inverted pyramid: the next band's base ----
@@ -765,7 +761,6 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
         const TypeMeta &M = T.type[r.S];
         const int S = r.S, band = r.band;
         const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
-        const int lgB = 31 - __clz(B);  // B is a power of two
         const int nlev = M.levels;
         int gbase[3];  // global coordinate of local u = 0 along each axis
         for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
@@ -822,7 +817,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     const int ne = M.exp_n[k - 1];
                     const int2 *el = T.exp + M.exp_off[k - 1];
                     prefetch_entries<ND>(el, ne, pre, dt);
-                    if (ne > 0) export_entries<ND>(el, ne, pre, k - 1, T, s_mb, (k & 1) ? phi_buf0 : phi_buf1, pc_s, lgB, dt);
+                    if (ne > 0) export_entries<ND>(el, ne, pre, s_mb, (k & 1) ? phi_buf0 : phi_buf1, pc_s, dt);
                 }
                 if (k < nlev && k <= H - 1) {  // sloped initial surface of level k
                     const int nf = M.imp_full_n[k], np = M.imp_phi_n[k];
@@ -870,7 +865,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
 #pragma unroll
                 for (int u = 0; u < kExportBatch; ++u)
-                    if (base + u * NW < ne) export_one(e[u], nlev, T, s_mb, last, pc_s, lgB);
+                    if (base + u * NW < ne) export_one(e[u], s_mb, last, pc_s);
             }
         } else {
             // ---- tops of the inverted pyramid: the next band's base ----
@@ -1180,6 +1175,7 @@ cudaError_t region_occupancy(int threads, size_t smem, int *blocks_per_sm)
     switch (threads) {
         SP_OCC(128)
         SP_OCC(256)
+        SP_OCC(320)
         SP_OCC(480)
         SP_OCC(512)
         SP_OCC(768)
@@ -1200,6 +1196,8 @@ cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t sm
         return region_launch_t<128>(a, max_B, smem, grid, st);
     case 256:
         return region_launch_t<256>(a, max_B, smem, grid, st);
+    case 320:
+        return region_launch_t<320>(a, max_B, smem, grid, st);
     case 480:
         return region_launch_t<480>(a, max_B, smem, grid, st);
     case 512:

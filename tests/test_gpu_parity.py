@@ -137,6 +137,8 @@ def test_gpu_matches_fp64_oracle_matter_era_64(oracle_mod):
     ((32, 48, 64), 8, 20, 2.0, 193),    # warp-specialised kernel, 128 compute + 64 movement threads
     ((48, 32, 32), 16, 27, 2.0, 321),   # warp-specialised, 256 + 64, ragged
     ((32, 32, 32), 16, 16, 1.0, 385),   # warp-specialised, 256 + 128
+    ((32, 32, 48), 16, 24, 2.0, 480),   # 480 workers
+    ((32, 32, 32), 16, 16, 0.0, 128),   # 128 workers at base 16
 ])
 def test_region_bit_exact_vs_monolithic(n, B, steps, nu, threads):
     p = params_for(n, nu, steps)
