@@ -291,6 +291,14 @@ int build_device_tables(sp_grid *g, int B)
                 m.rcp_active[k][q] = w > 0 ? 1.0f / (float)w : 0.0f;
             }
         for (int d = 0; d < 2; ++d) m.rcp_base[d] = 1.0f / (float)(t.base_phi[S].hi[d] - t.base_phi[S].lo[d]);
+        {
+            const sp::Box3 &bp = t.base_phi[S];
+            m.base_cols = (bp.hi[0] - bp.lo[0]) * (bp.hi[1] - bp.lo[1]);
+            m.base_runs = (bp.hi[2] - bp.lo[2] + 3) / 4;
+            m.rcp_cols = 1.0f / (float)m.base_cols;
+            for (int u = 0; u < m.base_cols * m.base_runs; ++u)  // the kernel's (run, column) split
+                if (sp::fdiv(u, m.rcp_cols) != u / m.base_cols) return SP_EINVAL;
+        }
         if (!block_decode_exact(m.active, t.H, m.rcp_active) || !decode_exact(&m.base_phi, 0, &m.rcp_base))
             return SP_EINVAL;
         for (int L = 0; L < sp::kMaxH; ++L) {
@@ -616,7 +624,7 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
         for (int s = 0; s < g->n_sims; ++s) n_in += g->B[s] == c.B;
         c.smem = sp::region_smem_bytes(c.B, 1, n_in, it->second.dev.imp_n);
         if (c.smem > 227 * 1024) return SP_EINVAL;
-        e = sp::region_occupancy(c.threads, c.smem, &c.ctas_per_sm);
+        e = sp::region_occupancy(c.threads, c.B, c.smem, &c.ctas_per_sm);
         if (e != cudaSuccess || c.ctas_per_sm < 1) return SP_EINVAL;
         c.grid = c.ctas_per_sm * g->sm_count;
         g->groups.push_back(c);

@@ -13,7 +13,11 @@ namespace sp {
 // so a kernel can keep it in shared memory).
 struct alignas(16) TypeMeta {
     int levels, mb_size, n_same_succ, same_preds;
-    int prev_preds, pad0, pad1, pad2;
+    int prev_preds;
+    // band-base copy in units of (column, run of up to 4 cells along z):
+    // columns of the base box, runs per column, 1/columns in FP32
+    int base_cols, base_runs;
+    float rcp_cols;
     Box3 active[kMaxH + 1];
     Box3 base_phi, base_pc;
     // exact quotient decode (see fdiv below), reciprocals rounded to FP32:

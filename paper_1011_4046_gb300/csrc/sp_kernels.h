@@ -11,7 +11,7 @@ cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st);
 cudaError_t launch_features(const RegionArgs &a, const float4 *simf, const unsigned long long *prev_trace, float *X,
                             cudaStream_t st);
 size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units);
-cudaError_t region_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm);
 cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st);
 cudaError_t launch_sweep(const float2 *phi_in, float2 *phi_out, float4 *pc, const int n[3],
                          const LevelCoef *coef, int lvl, PhysConst q, cudaStream_t st);
