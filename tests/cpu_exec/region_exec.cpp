@@ -423,4 +423,17 @@ double rx_bytes_per_update(int B, int64_t *read_per_band_cell, int64_t *write_pe
     return (double)(r + w) / (double)u;
 }
 
+// Active u-box of region type S at level k (lo[3], hi[3]) and its level count,
+// for the shared-memory bank test; returns -1 for a bad base.
+int rx_active_box(int B, int S, int k, int32_t *lohi)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return -1;
+    for (int d = 0; d < 3; ++d) {
+        lohi[d] = t.active[S][k].lo[d];
+        lohi[3 + d] = t.active[S][k].hi[d];
+    }
+    return t.levels[S];
+}
+
 }  // extern "C"

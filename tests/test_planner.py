@@ -14,40 +14,11 @@ exactly as the GPU kernel does:
   FP32 site update reproduce a whole-grid FP32 sweep bit for bit.
 """
 import ctypes
-import os
-import subprocess
 
 import numpy as np
 import pytest
 
 from paper_1011_4046_gb300 import inputs
-
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-CSRC = os.path.join(ROOT, "paper_1011_4046_gb300", "csrc")
-
-
-@pytest.fixture(scope="module")
-def rx():
-    out_dir = os.path.join(HERE, "cpu_exec", "_build")
-    os.makedirs(out_dir, exist_ok=True)
-    lib = os.path.join(out_dir, "librx.so")
-    srcs = [os.path.join(HERE, "cpu_exec", "region_exec.cpp"), os.path.join(CSRC, "planner.cpp")]
-    if not os.path.exists(lib) or any(os.path.getmtime(s) > os.path.getmtime(lib) for s in
-                                      srcs + [os.path.join(CSRC, "planner.h"), os.path.join(CSRC, "sp_update.h")]):
-        tmp = lib + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", f"-I{CSRC}", *srcs,
-                        "-o", tmp], check=True)
-        os.replace(tmp, lib)
-    L = ctypes.CDLL(lib)
-    L.rx_check.argtypes = [ctypes.c_int] * 5 + [ctypes.c_char_p, ctypes.c_int]
-    fp = ctypes.POINTER(ctypes.c_float)
-    L.rx_run.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, fp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                              fp, fp, fp, ctypes.c_char_p, ctypes.c_int]
-    L.rx_bytes_per_update.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 3
-    L.rx_bytes_per_update.restype = ctypes.c_double
-    return L
-
 
 @pytest.mark.parametrize("B,n,bands", [(8, (16, 16, 16), 4), (8, (16, 24, 32), 4), (4, (8, 8, 12), 5),
                                        (6, (12, 18, 12), 4), (16, (32, 32, 32), 3)])
