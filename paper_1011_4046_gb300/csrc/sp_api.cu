@@ -269,6 +269,8 @@ int build_device_tables(sp_grid *g, int B)
     std::string err = sp::build_tables(B, &td.host);
     if (!err.empty()) return SP_EINVAL;
     const sp::TileTables &t = td.host;
+    // the device tables and index packing serve bases up to 16
+    if (t.P * t.P * t.P > 8192 || t.B * t.B * t.B > 4096 || t.H > sp::kMaxHDev) return SP_EINVAL;
     sp::TablesDev &h = td.dev;
     std::memset(&h, 0, sizeof h);
     h.B = t.B;
@@ -281,10 +283,10 @@ int build_device_tables(sp_grid *g, int B)
         m.n_same_succ = (int)t.same_succ[S].size();
         m.same_preds = t.same_preds[S];
         m.prev_preds = t.prev_preds[S];
-        for (int k = 0; k <= sp::kMaxH; ++k) m.active[k] = t.active[S][k];
+        for (int k = 0; k <= sp::kMaxHDev; ++k) m.active[k] = t.active[S][k];
         m.base_phi = t.base_phi[S];
         m.base_pc = t.base_pc[S];
-        for (int k = 0; k <= sp::kMaxH; ++k)
+        for (int k = 0; k <= sp::kMaxHDev; ++k)
             for (int q = 0; q < 2; ++q) {
                 const int d = q == 0 ? 2 : 0;  // blocks along z, then along x
                 const int w = (t.active[S][k].hi[d] - t.active[S][k].lo[d]) / 2;
@@ -301,7 +303,7 @@ int build_device_tables(sp_grid *g, int B)
         }
         if (!block_decode_exact(m.active, t.H, m.rcp_active) || !decode_exact(&m.base_phi, 0, &m.rcp_base))
             return SP_EINVAL;
-        for (int L = 0; L < sp::kMaxH; ++L) {
+        for (int L = 0; L < sp::kMaxHDev; ++L) {
             m.mb_level_off[L] = t.mb_level_off[S][L];
             m.exp_off[L] = t.exp_off[S][L];
             m.exp_n[L] = t.exp_n[S][L];
@@ -313,10 +315,9 @@ int build_device_tables(sp_grid *g, int B)
     for (int q = 0; q < 2; ++q)
         for (size_t i = 0; i < t.next_succ[q].size(); ++i) h.next_succ[q][i] = t.next_succ[q][i];
     // compact device tables (see sp_device.cuh for the packing)
-    if (t.P * t.P * t.P > 8192 || t.B * t.B * t.B > 4096) return SP_EINVAL;
     std::vector<unsigned short> imp;
     for (int S = 0; S < sp::kTypes; ++S)
-        for (int L = 0; L < sp::kMaxH; ++L) {
+        for (int L = 0; L < sp::kMaxHDev; ++L) {
             sp::TypeMeta &m = h.type[S];
             m.imp_full_off[L] = (int)imp.size();
             for (int i = 0; i < t.imp_full_n[S][L]; ++i)
@@ -411,7 +412,7 @@ int choose_B(const sp_params &p, int requested)
     return -1;
 }
 
-int default_threads(int B) { return B <= 8 ? 128 : 320; }
+int default_threads(int B) { return B <= 8 ? 64 : 320; }
 
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
@@ -580,12 +581,12 @@ int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t 
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-// Worker counts of the region kernel: 128, 256, 320, 480, 512, 768 (every worker
+// Worker counts of the region kernel: 64, 128, 256, 320, 480, 512, 768 (every worker
 // does every step), or an odd value w + 1 for the warp-specialised kernel with
 // w workers (193: 128 compute + 64 movement; 321: 256 + 64; 385: 256 + 128).
 bool valid_threads(int t)
 {
-    return t == 128 || t == 256 || t == 320 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
+    return t == 64 || t == 128 || t == 256 || t == 320 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
 }
 
 
@@ -720,7 +721,7 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         if (block_shape != SP_AUTOTUNE)
             shapes.push_back(block_shape ? block_shape : default_threads(maxB));
         else if (maxB <= 8)
-            shapes = {128, 193, 256};
+            shapes = {64, 128, 193};
         else
             shapes = {256, 320, 321, 385, 480};
         for (int nt : shapes) {

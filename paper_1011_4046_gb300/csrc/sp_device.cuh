@@ -9,6 +9,10 @@
 
 namespace sp {
 
+// Levels per band the device tables hold: bases up to 16 (the kernels decode
+// cell indices with shifts of at most 4 bits per axis).
+constexpr int kMaxHDev = 8;
+
 // Per-type geometry and routing of one base size (one block per region type,
 // so a kernel can keep it in shared memory).
 struct alignas(16) TypeMeta {
@@ -18,17 +22,17 @@ struct alignas(16) TypeMeta {
     // columns of the base box, runs per column, 1/columns in FP32
     int base_cols, base_runs;
     float rcp_cols;
-    Box3 active[kMaxH + 1];
+    Box3 active[kMaxHDev + 1];
     Box3 base_phi, base_pc;
     // exact quotient decode (see fdiv below), reciprocals rounded to FP32:
     // of each active box, 1/(w2/2) and 1/(w0/2) (its cells are taken in
     // 2x2x2 blocks, see block_cell); of the base box, 1/w0 and 1/w1
-    float rcp_active[kMaxH + 1][2];
+    float rcp_active[kMaxHDev + 1][2];
     float rcp_base[2];
-    int imp_full_off[kMaxH], imp_full_n[kMaxH];
-    int imp_phi_off[kMaxH], imp_phi_n[kMaxH];
-    int mb_level_off[kMaxH];
-    int exp_off[kMaxH], exp_n[kMaxH];
+    int imp_full_off[kMaxHDev], imp_full_n[kMaxHDev];
+    int imp_phi_off[kMaxHDev], imp_phi_n[kMaxHDev];
+    int mb_level_off[kMaxHDev];
+    int exp_off[kMaxHDev], exp_n[kMaxHDev];
     Succ same_succ[kMaxSameSucc];
     int pad3[2];
 };

@@ -236,12 +236,13 @@ static_assert(sizeof(SimDev) / 16 <= 32, "the manager warp copies a descriptor w
 constexpr int kExportPrefetch = 3;
 constexpr int kExportBatch = 4;
 // Per worker count: independent cell updates in flight per thread (measured:
-// one for 128 workers, two for 256 and more; four were 3 % slower at base 16),
-// and the CTAs per SM the registers are budgeted for.  128 workers serve base
-// 8, whose small regions fit several CTAs per SM; 256 and more serve base 16,
-// one CTA per SM.
+// one up to 128 workers, two for 256 and more; four were 3 % slower at base
+// 16), and the CTAs per SM the registers are budgeted for.  64 and 128 workers
+// serve base 8, whose small regions fit six and four CTAs per SM (an SM's
+// throughput grows almost linearly with the regions it holds); 256 and more
+// serve base 16, one CTA per SM.
 __host__ __device__ constexpr int region_cells_per_step(int nw) { return nw <= 128 ? 1 : 2; }
-__host__ __device__ constexpr int region_min_blocks(int nw) { return nw <= 128 ? 4 : 1; }
+__host__ __device__ constexpr int region_min_blocks(int nw) { return nw <= 64 ? 6 : nw <= 128 ? 4 : 1; }
 
 __device__ __forceinline__ void export_one(int2 e, float2 *const *mb_of, const float2 *__restrict__ phi,
                                            const float4 *__restrict__ pc)
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
         }
     }
     __syncthreads();
-    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxH);
+    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxHDev);
     for (int t = 0; t < a.n_tabs; ++t) {  // every import list of the launch, once
         const int4 *src = reinterpret_cast<const int4 *>(s_tabs[t].imp);
         int4 *dst = reinterpret_cast<int4 *>(s_imp + s_tabs[t].imp_smem);
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
         }
     }
     __syncthreads();
-    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxH);
+    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxHDev);
     for (int t = 0; t < a.n_tabs; ++t) {  // every import list of the launch, once
         const int4 *src = reinterpret_cast<const int4 *>(s_tabs[t].imp);
         int4 *dst = reinterpret_cast<int4 *>(s_imp + s_tabs[t].imp_smem);
@@ -1203,7 +1204,7 @@ size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units)
     (void)n_sims;  // descriptors travel with the handoff (static shared memory)
     const int P = max_B + 2;
     return (size_t)2 * P * P * P * sizeof(float2) + (size_t)max_B * max_B * max_B * sizeof(float4) +
-           (size_t)n_tabs * sizeof(TablesDev) + kMaxH * sizeof(LevelCoef) +
+           (size_t)n_tabs * sizeof(TablesDev) + kMaxHDev * sizeof(LevelCoef) +
            (size_t)imp_units * sizeof(unsigned short);
 }
 
@@ -1220,6 +1221,7 @@ cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm
         if (e != cudaSuccess) return e;                                                                          \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, region_ws_kernel<NC, ND>, NC + ND + 32, smem);
     switch (threads) {
+        SP_OCC(64)
         SP_OCC(128)
         SP_OCC(256)
         SP_OCC(320)
@@ -1239,6 +1241,8 @@ cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm
 cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st)
 {
     switch (threads) {
+    case 64:
+        return region_launch_nw<64>(a, max_B, smem, grid, st);
     case 128:
         return region_launch_nw<128>(a, max_B, smem, grid, st);
     case 256:

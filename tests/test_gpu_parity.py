@@ -134,6 +134,7 @@ def test_gpu_matches_fp64_oracle_matter_era_64(oracle_mod):
     ((32, 32, 32), 16, 16, 1.0, 0),     # B = 16, 2 bands
     ((48, 32, 32), 16, 27, 2.0, 256),   # ragged: 3 bands + 3 remainder steps, 256 threads
     ((24, 24, 24), 8, 3, 0.0, 128),     # fewer steps than a band: all remainder
+    ((32, 48, 64), 8, 20, 2.0, 128),    # 128 workers at base 8 (the default is 64)
     ((32, 48, 64), 8, 20, 2.0, 193),    # warp-specialised kernel, 128 compute + 64 movement threads
     ((48, 32, 32), 16, 27, 2.0, 321),   # warp-specialised, 256 + 64, ragged
     ((32, 32, 32), 16, 16, 1.0, 385),   # warp-specialised, 256 + 128
