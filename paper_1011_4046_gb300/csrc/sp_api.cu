@@ -327,7 +327,6 @@ int build_device_tables(sp_grid *g, int B)
         }
     while (imp.size() % 8) imp.push_back(0);
     h.imp_n = (int)imp.size();
-    h.rcp_B = 1.0f / (float)t.B;
     std::vector<int2> ex(t.exp.size());
     const int lgB = __builtin_ctz((unsigned)t.B);
     for (size_t i = 0; i < t.exp.size(); ++i) {
@@ -341,12 +340,12 @@ int build_device_tables(sp_grid *g, int B)
         ex[i].y = (int)((unsigned)e.dst_phi | ((unsigned)(has_pc ? e.dst_pc : 0) << 16));
     }
     // the kernel re-derives the phi index of a full import from its (pi, c)
-    // index: check the derivation against the planner's tables
+    // index with shifts (B a power of two): check the derivation against the
+    // planner's tables
     for (size_t i = 0; i < t.imp_full.size(); ++i) {
         const int c = t.imp_full[i] >> 16, want = t.imp_full[i] & 0xFFFF;
-        const int t1 = sp::fdiv(c, h.rcp_B), t2 = sp::fdiv(t1, h.rcp_B);
-        const int ux = c - t1 * t.B + 1, uy = t1 - t2 * t.B + 1, uz = t2 + 1;
-        if ((uz * t.P + uy) * t.P + ux != want) return SP_EINVAL;
+        const int pidx = (((c >> (2 * lgB)) + 1) * t.P + ((c >> lgB) & (t.B - 1)) + 1) * t.P + (c & (t.B - 1)) + 1;
+        if (pidx != want) return SP_EINVAL;
     }
     cudaError_t e = cudaSuccess;
     auto up = [&](void **dst, const void *src, size_t bytes) {

@@ -55,8 +55,7 @@ struct alignas(16) TablesDev {
     Succ next_succ[2][kMaxNextSucc];
     int imp_n;      // 16-bit import entries of this base size (padded to 8)
     int imp_smem;   // their offset in the shared import area (16-bit units)
-    float rcp_B;    // 1/B in FP32 (exact quotient decode)
-    int pad2;
+    int pad2, pad3;
     const unsigned short *imp;  // all import lists, global memory
     const int2 *exp;            // all export entries, global memory
 };

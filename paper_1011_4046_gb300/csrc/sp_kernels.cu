@@ -287,7 +287,7 @@ __device__ __forceinline__ void prefetch_entries(const int2 *__restrict__ el, in
 template <int NW>
 __device__ __forceinline__ void import_level(const float2 *__restrict__ mb, int nf, int np,
                                              const unsigned short *fl, const unsigned short *pl, float2 *dst,
-                                             float4 *pc_s, int B, int P, float rcp_B, int wt)
+                                             float4 *pc_s, int B, int P, int wt)
 {
     const int lgB = 31 - __clz(B);  // B is a power of two (4, 8 or 16)
     for (int i = wt; i < nf; i += NW) {
@@ -617,8 +617,7 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
                 const int nf = M.imp_full_n[L], np = M.imp_phi_n[L];
                 if (nf + np > 0)
                     import_level<NW>(mb_self + M.mb_level_off[L], nf, np, s_imp_t + M.imp_full_off[L],
-                                     s_imp_t + M.imp_phi_off[L], (L & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, T.rcp_B,
-                                     wt);
+                                     s_imp_t + M.imp_phi_off[L], (L & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, wt);
             }
             cp_async_commit();  // one group per level, empty or not
         };
@@ -836,8 +835,7 @@ __global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a
                     const int nf = M.imp_full_n[k], np = M.imp_phi_n[k];
                     if (nf + np > 0)
                         import_level<ND>(mb_self + M.mb_level_off[k], nf, np, s_imp_t + M.imp_full_off[k],
-                                         s_imp_t + M.imp_phi_off[k], (k & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, T.rcp_B,
-                                         dt);
+                                         s_imp_t + M.imp_phi_off[k], (k & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, dt);
                     cp_async_commit();
                     cp_async_wait_all();
                 }
