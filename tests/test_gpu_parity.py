@@ -130,6 +130,8 @@ def test_gpu_matches_fp64_oracle_matter_era_64(oracle_mod):
 # ------------------------------------------------------- region == sweep
 @pytest.mark.parametrize("n,B,steps,nu,threads", [
     ((16, 16, 16), 8, 12, 0.0, 0),      # smallest grid (2 regions per axis)
+    ((16, 16, 16), 4, 11, 0.0, 0),      # base 4 (64 workers): 5 bands + 1 remainder step
+    ((8, 12, 16), 4, 10, 2.0, 128),     # base 4, anisotropic, smallest sides
     ((32, 48, 64), 8, 20, 2.0, 0),      # anisotropic, 5 bands
     ((32, 32, 32), 16, 16, 1.0, 0),     # B = 16, 2 bands
     ((48, 32, 32), 16, 27, 2.0, 256),   # ragged: 3 bands + 3 remainder steps, 256 threads
