@@ -29,6 +29,10 @@ namespace {
 struct TablesOnDevice {
     sp::TileTables host;
     sp::TablesDev dev;             // host copy of the device descriptor
+    // band-0 regions of types 0 .. seed_types-1 have no predecessor and are
+    // queued at reset (1 for bases of 8 and more: the pyramids; at base 4 every
+    // type but the inverted pyramid computes one level and imports nothing)
+    int seed_types = 1;
     sp::TablesDev *d_dev = nullptr;  // device copy (the only table of its launch)
     unsigned short *d_imp = nullptr;
     int2 *d_exp = nullptr;
@@ -271,6 +275,13 @@ int build_device_tables(sp_grid *g, int B)
     const sp::TileTables &t = td.host;
     // the device tables and index packing serve bases up to 16
     if (t.P * t.P * t.P > 8192 || t.B * t.B * t.B > 4096 || t.H > sp::kMaxHDev) return SP_EINVAL;
+    // the seeds (band-0 regions without predecessors) must be the leading
+    // region types: the queue reset takes the first Jtot * seed_types ids
+    td.seed_types = 0;
+    while (td.seed_types < sp::kTypes && t.same_preds[td.seed_types] == 0) ++td.seed_types;
+    for (int S = td.seed_types; S < sp::kTypes; ++S)
+        if (t.same_preds[S] == 0) return SP_EINVAL;
+    if (td.seed_types == 0) return SP_EINVAL;
     sp::TablesDev &h = td.dev;
     std::memset(&h, 0, sizeof h);
     h.B = t.B;
@@ -962,7 +973,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
                 g->last_tile_base[s] = all_total + total;
                 g->last_tiles[s] = d.tiles;
                 total += d.tiles;
-                seeds += (unsigned)d.Jtot;
+                seeds += (unsigned)d.Jtot * (unsigned)g->tables[B].seed_types;
                 sims.push_back(d);
                 sim_of.push_back(s);
             }
