@@ -423,6 +423,19 @@ double rx_bytes_per_update(int B, int64_t *read_per_band_cell, int64_t *write_pe
     return (double)(r + w) / (double)u;
 }
 
+// Region types without same-band predecessors: their count if they are the
+// leading types 0 .. m-1 (what the GPU queue reset seeds), else -1.
+int rx_seed_types(int B)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return -2;
+    int m = 0;
+    while (m < 8 && t.same_preds[m] == 0) ++m;
+    for (int S = m; S < 8; ++S)
+        if (t.same_preds[S] == 0) return -1;
+    return m;
+}
+
 // Active u-box of region type S at level k (lo[3], hi[3]) and its level count,
 // for the shared-memory bank test; returns -1 for a bad base.
 int rx_active_box(int B, int S, int k, int32_t *lohi)

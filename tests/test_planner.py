@@ -78,3 +78,13 @@ def test_region_executor_bit_exact_vs_sweep(rx, B, n, steps, seed):
         got = run(1, order_seed)
         for a, b in zip(ref, got):
             assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("B,seeds", [(4, 7), (6, 1), (8, 1), (16, 1)])
+def test_predecessor_free_types_lead(rx, B, seeds):
+    """The band-0 regions that are ready at the start are those of the leading
+    region types (the GPU queue reset seeds the first Jtot * m region ids).  At
+    base 4 every type but the inverted pyramid computes a single level and
+    imports nothing, so seven types are seeds; from base 6 on only the
+    pyramid is."""
+    assert rx.rx_seed_types(B) == seeds
