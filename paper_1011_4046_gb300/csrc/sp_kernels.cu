@@ -138,10 +138,15 @@ __device__ __forceinline__ RegionInfo decode_region(const SimDev *sims, int n_si
 
 // One lane per successor: acq_rel decrement of its counter, push at zero.
 // Called by the 32 lanes of one warp after the whole CTA finished the region.
+// Ordering: the workers' surface writes precede (bar.sync, then a CTA-scope
+// release/acquire of the done flag) lane 0's observation of the done flag;
+// __syncwarp extends that to every lane, and each lane's GPU-scope acq_rel
+// decrement (and the release store of a push) carries it to the successor's
+// CTA, so no separate fence is needed.
 __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const TablesDev &T, const RegionInfo &r,
                                    int lane, unsigned long long t_start, int g)
 {
-    __threadfence();
+    __syncwarp();
     if (g == a.fault_drop) {  // injected failure: completion is never reported downstream
         if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
         return;
