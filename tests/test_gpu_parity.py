@@ -153,6 +153,33 @@ def test_region_bit_exact_vs_monolithic(n, B, steps, nu, threads):
     assert_bit_equal(reg, mono)
 
 
+def _random_cases(seed, count):
+    """Seeded random configurations: base, per-axis sides (multiples of the
+    base, 2 to 5 regions per axis), step counts with ragged remainders, eras
+    and worker counts."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(count):
+        B = int(rng.choice([4, 8, 16]))
+        n = tuple(int(B * rng.integers(2, 6 if B < 16 else 4)) for _ in range(3))
+        steps = int(rng.integers(1, 4 * B))
+        nu = float(rng.choice([0.0, 1.0, 2.0]))
+        threads = int(rng.choice({4: [0, 64, 128], 8: [0, 64, 128, 256], 16: [0, 256, 320, 480]}[B]))
+        cases.append((n, B, steps, nu, threads))
+    return cases
+
+
+@pytest.mark.parametrize("n,B,steps,nu,threads", _random_cases(2026, 12))
+def test_random_configurations_bit_exact(n, B, steps, nu, threads):
+    """Region path == monolithic sweep, bit for bit, on seeded random shapes,
+    step counts (whole bands plus any remainder), eras and block shapes."""
+    p = params_for(n, nu, steps)
+    st = inputs.initial_state(n, steps, "gaussian", sigma=0.3)
+    reg = run_gpu(p, st, steps, base_B=B, threads=threads)
+    assert all(np.all(np.isfinite(a)) for a in reg)
+    assert_bit_equal(reg, run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC))
+
+
 def test_full_size_matter_era_workload(oracle_mod):
     """128^3, matter era, random phases, 256 steps, B = 16: the benchmark
     workload, on the full grid (region == sweep bit for bit inside)."""
