@@ -167,15 +167,15 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *                SP_AUTOTUNE to time both policies (all 8, 16 where
  *                possible) and keep the faster.  Every n[d] must be a
  *                multiple of B with n[d] / B >= 2.
- *   block_shape: worker threads per CTA (64, 128, 256, 320, 480, 512 or 768, every
+ *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768, every
  *                worker taking every step of a region; or 193, 321, 385 for
  *                the warp-specialised kernel with 128 + 64, 256 + 64,
  *                256 + 128 compute + data-movement workers, the movement
  *                threads moving level k's surfaces while level k+1 is
  *                computed); one manager warp is added.  0 for the default
- *                of each base (64 for bases 4 and 8, 320 for 16); SP_AUTOTUNE
+ *                of each base (64 for bases 4 and 8, 384 for 16); SP_AUTOTUNE
  *                to time the candidates for the largest base (64, 128, 193
- *                for base 8; 256, 320, 321, 385, 480 for base 16), smaller
+ *                for base 8; 320, 321, 384, 385, 480 for base 16), smaller
  *                bases keeping their default.  A value applies to every base.
  *                The autotuner runs 16-step calls on scratch copies of the
  *                current state (sides above 128 cells are cut to 128 or 120),

@@ -422,7 +422,7 @@ int choose_B(const sp_params &p, int requested)
     return -1;
 }
 
-int default_threads(int B) { return B <= 8 ? 64 : 320; }
+int default_threads(int B) { return B <= 8 ? 64 : 384; }
 
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
@@ -591,12 +591,12 @@ int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t 
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-// Worker counts of the region kernel: 64, 128, 256, 320, 480, 512, 768 (every worker
+// Worker counts of the region kernel: 64, 128, 256, 320, 384, 480, 512, 768 (every worker
 // does every step), or an odd value w + 1 for the warp-specialised kernel with
 // w workers (193: 128 compute + 64 movement; 321: 256 + 64; 385: 256 + 128).
 bool valid_threads(int t)
 {
-    return t == 64 || t == 128 || t == 256 || t == 320 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
+    return t == 64 || t == 128 || t == 256 || t == 320 || t == 384 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
 }
 
 
@@ -733,7 +733,7 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         else if (maxB <= 8)
             shapes = {64, 128, 193};
         else
-            shapes = {256, 320, 321, 385, 480};
+            shapes = {320, 321, 384, 385, 480};
         for (int nt : shapes) {
             rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr, block_shape == SP_AUTOTUNE);
             if (rc == SP_EINVAL) continue;  // does not fit this device

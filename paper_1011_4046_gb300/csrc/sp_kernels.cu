@@ -1264,6 +1264,7 @@ cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm
         SP_OCC(128)
         SP_OCC(256)
         SP_OCC(320)
+        SP_OCC(384)
         SP_OCC(480)
         SP_OCC(512)
         SP_OCC(768)
@@ -1288,6 +1289,8 @@ cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t sm
         return region_launch_nw<256>(a, max_B, smem, grid, st);
     case 320:
         return region_launch_nw<320>(a, max_B, smem, grid, st);
+    case 384:
+        return region_launch_nw<384>(a, max_B, smem, grid, st);
     case 480:
         return region_launch_nw<480>(a, max_B, smem, grid, st);
     case 512:
