@@ -79,19 +79,26 @@ def gaussian_field(n, seed: int, sigma: float = 0.5) -> np.ndarray:
     return out.astype(np.complex64).reshape(nz, ny, nx)
 
 
-def random_phase_field(n, seed: int, eta: float = 1.0) -> np.ndarray:
-    """phi = eta * exp(i theta), theta = 2 pi u, u uniform from counter i.
+def random_phase_slab(n, seed: int, z0: int, z1: int, eta: float = 1.0) -> np.ndarray:
+    """Planes z0 <= z < z1 of the random-phase field: phi = eta * exp(i theta),
+    theta = 2 pi u, u uniform from counter i (the global site index).
 
     cos and sin come from the host maths library in FP64; the result is
-    rounded to FP32 once.  Returns complex64 (nz, ny, nx).
+    rounded to FP32 once.  Returns complex64 (z1 - z0, ny, nx).
     """
-    nx, ny, nz = (int(v) for v in n)
-    s = _sites(n)
-    theta = 2.0 * np.pi * uniform01(seed, np.arange(s, dtype=np.uint64))
-    out = np.empty(s, dtype=np.complex128)
+    nx, ny, _ = (int(v) for v in n)
+    plane = nx * ny
+    i = np.arange(z0 * plane, z1 * plane, dtype=np.uint64)
+    theta = 2.0 * np.pi * uniform01(seed, i)
+    out = np.empty(i.size, dtype=np.complex128)
     out.real = eta * np.cos(theta)
     out.imag = eta * np.sin(theta)
-    return out.astype(np.complex64).reshape(nz, ny, nx)
+    return out.astype(np.complex64).reshape(z1 - z0, ny, nx)
+
+
+def random_phase_field(n, seed: int, eta: float = 1.0) -> np.ndarray:
+    """The whole random-phase field, complex64 (nz, ny, nx); see random_phase_slab."""
+    return random_phase_slab(n, seed, 0, int(n[2]), eta)
 
 
 def initial_state(n, seed: int, kind: str, sigma: float = 0.5, eta: float = 1.0):
