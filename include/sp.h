@@ -91,6 +91,13 @@ extern "C" {
                                        with SP_ETIMEOUT after the wait limit; -1 clears */
 #define SP_OPT_GRAPHS 3             /* 1 (default): capture region calls into CUDA graphs on
                                        non-legacy streams; 0: launch directly */
+#define SP_OPT_MAILBOX_SLOTS 4      /* sloped-surface mailboxes, applied by the next sp_region_plan:
+                                       2: a ring of two band slots; 1: one slot for every band, half
+                                       the memory (sp_plan_info.mailbox_bytes), with each region also
+                                       waiting for the previous band's readers of the mailboxes it
+                                       writes (results identical); 0 (default): one slot at base 16
+                                       or where the ring would not fit in free device memory, else
+                                       the ring */
 
 /* ---- region cost model ---- */
 #define SP_MODEL_FEATURES 16

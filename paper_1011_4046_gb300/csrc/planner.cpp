@@ -263,6 +263,14 @@ std::string build_tables(int B, TileTables *tp)
         for (int d = 0; d < 3; ++d) expect_same *= inverted(S, d) ? 3 : 1;
         if (t.same_preds[S] > expect_same - 1) return "more same-band predecessors than 3^|S| - 1";
         if (t.prev_preds[S] != (1 << __builtin_popcount(S))) return "previous-band predecessor count is not 2^|S|";
+        for (auto &s : preds[S]) {
+            Succ x;
+            x.type = (int8_t)std::get<0>(s);
+            x.e[0] = (int8_t)std::get<1>(s);
+            x.e[1] = (int8_t)std::get<2>(s);
+            x.e[2] = (int8_t)std::get<3>(s);
+            t.reuse_succ[S].push_back(x);
+        }
         for (auto &s : succs[S]) {
             Succ x;
             x.type = (int8_t)std::get<0>(s);
@@ -290,6 +298,13 @@ std::string build_tables(int B, TileTables *tp)
         return "inverted pyramid does not have 27 next-band successors";
     for (int S = 0; S < kTypes; ++S)
         if ((int)t.same_succ[S].size() > kMaxSameSucc) return "too many same-band successors";
+    // every same-band edge Sp -> S, mirrored one band later, is one reuse edge S -> Sp
+    for (int Sp = 0; Sp < kTypes; ++Sp) {
+        int n = 0;
+        for (int S = 0; S < kTypes; ++S)
+            for (const Succ &x : t.reuse_succ[S]) n += x.type == Sp;
+        if (n != (int)t.same_succ[Sp].size()) return "mailbox-reuse edges do not mirror the same-band edges";
+    }
 
     // ---- exact cover of one period cell at every level ----
     for (int k = 1; k <= H; ++k) {

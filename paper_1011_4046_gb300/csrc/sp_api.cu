@@ -36,6 +36,7 @@ struct TablesOnDevice {
     sp::TablesDev *d_dev = nullptr;  // device copy (the only table of its launch)
     unsigned short *d_imp = nullptr;
     int2 *d_exp = nullptr;
+    sp::Succ *d_reuse = nullptr;  // mailbox-reuse successors, kMaxSameSucc per type
 };
 
 // One persistent launch per region base: simulations of the same base share a
@@ -168,7 +169,9 @@ struct sp_grid {
     std::map<int, TablesOnDevice> tables;
     std::vector<GroupCfg> groups;  // one per distinct base, largest first
     std::vector<float2 *> mbox;
-    std::vector<long long> mb_slot;
+    std::vector<long long> mb_slot;   // float2 offset of band slot 1 (0: one slot for every band)
+    std::vector<long long> mb_elems;  // float2 elements per slot
+    int mb_slots = 0;                 // SP_OPT_MAILBOX_SLOTS (0: by base and free memory), applied by sp_region_plan
     std::vector<std::array<long long, sp::kTypes>> mb_type_off;
     // launch scratch
     int *d_counters = nullptr, *d_queue = nullptr;
@@ -364,13 +367,21 @@ int build_device_tables(sp_grid *g, int B)
         e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
         if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     };
+    std::vector<sp::Succ> reuse((size_t)sp::kTypes * sp::kMaxSameSucc, sp::Succ{0, {0, 0, 0}});
+    for (int S = 0; S < sp::kTypes; ++S) {
+        if ((int)t.reuse_succ[S].size() != t.same_preds[S] || t.same_preds[S] > sp::kMaxSameSucc) return SP_EINVAL;
+        for (int i = 0; i < t.same_preds[S]; ++i) reuse[(size_t)S * sp::kMaxSameSucc + i] = t.reuse_succ[S][i];
+    }
     up((void **)&td.d_imp, imp.data(), imp.size() * sizeof(unsigned short));
     up((void **)&td.d_exp, ex.data(), ex.size() * sizeof(int2));
+    up((void **)&td.d_reuse, reuse.data(), reuse.size() * sizeof(sp::Succ));
     h.imp = td.d_imp;
     h.exp = td.d_exp;
+    h.reuse = td.d_reuse;
     if (e != cudaSuccess) {
         cudaFree(td.d_imp);
         cudaFree(td.d_exp);
+        cudaFree(td.d_reuse);
         return e == cudaErrorMemoryAllocation ? SP_ENOMEM : SP_ECUDA;
     }
     g->tables[B] = td;
@@ -397,6 +408,7 @@ void free_plan(sp_grid *g)
     for (auto &kv : g->tables) {
         cudaFree(kv.second.d_imp);
         cudaFree(kv.second.d_exp);
+        cudaFree(kv.second.d_reuse);
         cudaFree(kv.second.d_dev);
     }
     g->tables.clear();
@@ -642,8 +654,16 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
     }
     if ((int)g->groups.size() > kMaxGroups) return SP_EINVAL;
     g->order = order;
-    // mailbox ring: two band slots per simulation
+    // mailboxes: a ring of two band slots per simulation, or one slot for
+    // every band (half the memory; regions then also wait for the previous
+    // band's readers of the mailboxes they write).  By default one slot at
+    // base 16 (measured as fast as the ring at 128^3) and wherever the ring
+    // would not fit in free device memory; the ring at bases 4 and 8 (whose
+    // managers measured 1.4 % slower with the extra releases).
     g->mb_slot.assign(g->n_sims, 0);
+    g->mb_elems.assign(g->n_sims, 0);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
     g->mb_type_off.assign(g->n_sims, {});
     for (int s = 0; s < g->n_sims; ++s) {
         const sp::TileTables &t = g->tables[g->B[s]].host;
@@ -654,9 +674,17 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
             g->mb_type_off[s][S] = off;
             off += J * t.mb_size[S];
         }
-        g->mb_slot[s] = off;
+        int slots = g->mb_slots;
+        if (slots == 0) {
+            const size_t ring = 2 * (size_t)off * sizeof(float2);
+            slots = (g->B[s] >= 16 || ring > free_b / 10 * 9) ? 1 : 2;
+        }
+        g->mb_elems[s] = off;
+        g->mb_slot[s] = slots == 2 ? off : 0;
+        const size_t bytes = std::max<size_t>((size_t)slots * off * sizeof(float2), 16);
+        free_b = free_b > bytes ? free_b - bytes : 0;
         float2 *m = nullptr;
-        e = cudaMalloc((void **)&m, std::max<size_t>(2 * off * sizeof(float2), 16));
+        e = cudaMalloc((void **)&m, bytes);
         if (e != cudaSuccess) {
             free_plan(g);
             return SP_ENOMEM;
@@ -711,6 +739,7 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
     sp_grid *t = nullptr;
     int rc = sp_grid_create(tp.data(), g->n_sims, nullptr, g->stream, &t);
     if (rc != SP_OK) return rc;
+    t->mb_slots = g->mb_slots;
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < g->n_sims && e == cudaSuccess; ++s) {
         const size_t sites = (size_t)sites_of(tp[s]);
@@ -967,6 +996,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
                 d.pc = g->pc[s];
                 d.mbox = g->mbox[s];
                 d.mb_slot = g->mb_slot[s];
+                d.mb_reuse = g->mb_slot[s] == 0;
                 for (int S = 0; S < sp::kTypes; ++S) d.mb_type_off[S] = g->mb_type_off[s][S];
                 d.tab = g->tables[B].d_dev;
                 d.tab_index = 0;
@@ -1081,6 +1111,10 @@ int sp_set_option(sp_grid *g, int32_t option, int64_t value)
     case SP_OPT_GRAPHS:
         if (value != 0 && value != 1) return SP_EINVAL;
         g->use_graphs = (int)value;
+        return SP_OK;
+    case SP_OPT_MAILBOX_SLOTS:
+        if (value < 0 || value > 2) return SP_EINVAL;
+        g->mb_slots = (int)value;
         return SP_OK;
     default:
         return SP_EINVAL;
@@ -1206,7 +1240,7 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         info.bytes_read_per_band = ps.bytes_read_per_band;
         info.bytes_written_per_band = ps.bytes_written_per_band;
         info.bytes_per_update = ps.bytes_per_update;
-        info.mailbox_bytes = 2 * g->mb_slot[sim] * (int64_t)sizeof(float2);
+        info.mailbox_bytes = (g->mb_slot[sim] ? 2 : 1) * g->mb_elems[sim] * (int64_t)sizeof(float2);
         info.autotuned = g->tune.autotuned;
         info.tune_candidates = g->tune.candidates;
         info.tune_best_ms = g->tune.best_ms;

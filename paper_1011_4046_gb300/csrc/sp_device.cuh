@@ -55,7 +55,9 @@ struct alignas(16) TablesDev {
     Succ next_succ[2][kMaxNextSucc];
     int imp_n;      // 16-bit import entries of this base size (padded to 8)
     int imp_smem;   // their offset in the shared import area (16-bit units)
-    int pad2, pad3;
+    // mailbox-reuse successors of a type-S region, reuse[S * kMaxSameSucc + i]
+    // for i < same_preds (used with a single mailbox slot), global memory
+    const Succ *reuse;
     const unsigned short *imp;  // all import lists, global memory
     const int2 *exp;            // all export entries, global memory
 };
@@ -74,12 +76,14 @@ struct alignas(16) SimDev {
     PhysConst q;
     float2 *phi;            // caller-owned state, x fastest: phi
     float4 *pc;             // and (pi.re, pi.im, c.re, c.im)
-    float2 *mbox;           // mailbox ring (2 band slots)
-    long long mb_slot;      // float2 elements per band slot
+    float2 *mbox;           // mailboxes: a ring of 2 band slots, or 1 slot for every band
+    long long mb_slot;      // float2 offset of band slot 1 (0 with a single slot)
     long long mb_type_off[kTypes];
     const TablesDev *tab;
     int tab_index;  // which of the launch's tables (RegionArgs::tabs) this is
-    int pad;
+    // 1: one mailbox slot for every band; a region also waits for the
+    // previous band's readers of the mailboxes it writes (reuse edges)
+    int mb_reuse;
 };
 
 // Priority buckets of the learned ordering (bucket 0 is queued first).

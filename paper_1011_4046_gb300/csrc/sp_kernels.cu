@@ -75,7 +75,7 @@ __global__ void reset_kernel(RegionArgs a)
     const unsigned per_band = 8u * (unsigned)sd.Jtot;
     const unsigned band = local / per_band;
     const int S = (int)((local - band * per_band) / (unsigned)sd.Jtot);
-    a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds : 0);
+    a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds + (sd.mb_reuse ? M[S].n_same_succ : 0) : 0);
     // queue position t: the first n_seed positions hold the seeds (with the
     // learned ordering seed_kernel writes them, bucket by bucket)
     a.queue[t] = (t < a.n_seed && !a.prio) ? seed_region(a, t) : -1;
@@ -151,46 +151,55 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
         if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
         return;
     }
+    // successors: same band, then the next band's (an inverted pyramid's
+    // 27), then with a single mailbox slot the next band's writers of this
+    // region's mailbox; one lane each, in passes of 32
     const int n_same = T.type[r.S].n_same_succ;
     const int n_next = (r.S == kTypes - 1 && r.band + 1 < sd.nbands) ? kMaxNextSucc : 0;
-    bool ready = false;
-    int region = -1;
-    if (lane < n_same + n_next) {
-        Succ su;
-        int nb;
-        if (lane < n_same) {
-            su = T.type[r.S].same_succ[lane];
-            nb = r.band;
-        } else {
-            su = T.next_succ[(r.band + 1) & 1][lane - n_same];
-            nb = r.band + 1;
-        }
-        int jc = 0, mul = 1;
-        for (int d = 0; d < 3; ++d) {
-            int v = r.j[d] + su.e[d];
-            v += (v < 0) ? sd.J[d] : 0;
-            v -= (v >= sd.J[d]) ? sd.J[d] : 0;
-            jc += v * mul;
-            mul *= sd.J[d];
-        }
-        const unsigned t = sd.tile_base + (unsigned)((nb * 8 + su.type) * sd.Jtot + jc);
-        const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
-        ready = old == 1;
-        region = (int)t;
-        if (a.prio == nullptr && ready) {
-            const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
-            st_release_gpu(a.queue + pos, (int)t);
-        }
-    }
-    if (a.prio) {
-        // learned ordering: the successors made ready here are queued bucket by bucket
-        const int b = ready ? a.prio[region] : kBuckets;
-        for (int q = 0; q < kBuckets; ++q) {
-            if (b == q) {
-                const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
-                st_release_gpu(a.queue + pos, region);
+    const int n_reuse = (sd.mb_reuse && r.band + 1 < sd.nbands) ? T.type[r.S].same_preds : 0;
+    const int n_all = n_same + n_next + n_reuse;
+    for (int p = 0; p < n_all; p += 32) {
+        const int i = p + lane;
+        bool ready = false;
+        int region = -1;
+        if (i < n_all) {
+            Succ su;
+            int nb = r.band + 1;
+            if (i < n_same) {
+                su = T.type[r.S].same_succ[i];
+                nb = r.band;
+            } else if (i < n_same + n_next) {
+                su = T.next_succ[(r.band + 1) & 1][i - n_same];
+            } else {
+                su = T.reuse[r.S * kMaxSameSucc + (i - n_same - n_next)];
             }
-            __syncwarp();
+            int jc = 0, mul = 1;
+            for (int d = 0; d < 3; ++d) {
+                int v = r.j[d] + su.e[d];
+                v += (v < 0) ? sd.J[d] : 0;
+                v -= (v >= sd.J[d]) ? sd.J[d] : 0;
+                jc += v * mul;
+                mul *= sd.J[d];
+            }
+            const unsigned t = sd.tile_base + (unsigned)((nb * 8 + su.type) * sd.Jtot + jc);
+            const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
+            ready = old == 1;
+            region = (int)t;
+            if (a.prio == nullptr && ready) {
+                const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
+                st_release_gpu(a.queue + pos, (int)t);
+            }
+        }
+        if (a.prio) {
+            // learned ordering: the successors made ready here are queued bucket by bucket
+            const int b = ready ? a.prio[region] : kBuckets;
+            for (int q = 0; q < kBuckets; ++q) {
+                if (b == q) {
+                    const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
+                    st_release_gpu(a.queue + pos, region);
+                }
+                __syncwarp();
+            }
         }
     }
     if (lane == 0) atomicAdd(&a.ctl->completed, 1u);

@@ -51,6 +51,7 @@ SP_SURF_LEVEL = 7
 SP_OPT_WAIT_LIMIT_NS = 1
 SP_OPT_FAULT_DROP_RELEASE = 2
 SP_OPT_GRAPHS = 3
+SP_OPT_MAILBOX_SLOTS = 4
 SP_MODEL_FEATURES = 16
 SP_MODEL_PARAMS = 5313
 

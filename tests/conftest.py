@@ -49,10 +49,10 @@ def rx():
                         "-o", tmp], check=True)
         os.replace(tmp, lib)
     L = ctypes.CDLL(lib)
-    L.rx_check.argtypes = [ctypes.c_int] * 5 + [ctypes.c_char_p, ctypes.c_int]
+    L.rx_check.argtypes = [ctypes.c_int] * 5 + [ctypes.c_char_p, ctypes.c_int, ctypes.c_int]
     fp = ctypes.POINTER(ctypes.c_float)
     L.rx_run.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, fp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                              fp, fp, fp, ctypes.c_char_p, ctypes.c_int]
+                                              fp, fp, fp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int]
     L.rx_bytes_per_update.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 3
     L.rx_bytes_per_update.restype = ctypes.c_double
     L.rx_active_box.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]

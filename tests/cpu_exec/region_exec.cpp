@@ -5,8 +5,9 @@
 //   * checks on a concrete periodic grid that every (site, level) is computed
 //     by exactly one region, that every read of a region is produced by one
 //     of its predecessors, and that no write can overtake a read it would
-//     clobber (main arrays and the two-slot mailbox ring), by reachability in
-//     the dependency DAG the kernel releases;
+//     clobber (main arrays and the mailboxes: a ring of two band slots, or
+//     one slot for every band), by reachability in the dependency DAG the
+//     kernel releases;
 //   * executes the regions one at a time in a seeded random topological
 //     order with the same FP32 site update, so the result can be compared bit
 //     for bit with a whole-grid CPU sweep.
@@ -47,8 +48,9 @@ struct Grid {
 
 int wrap(int p, int n) { return ((p % n) + n) % n; }
 
-// successors exactly as the kernel releases them
-std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t r)
+// successors exactly as the kernel releases them; reuse: with the
+// mailbox-reuse edges of a single mailbox slot
+std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t r, bool reuse)
 {
     int band, S, j[3];
     g.decode(r, &band, &S, j);
@@ -64,10 +66,21 @@ std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t 
             for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + s.e[d], g.J[d]);
             out.push_back(g.id(band + 1, s.type, jc));
         }
+    if (reuse && band + 1 < g.nbands)
+        for (const sp::Succ &s : t.reuse_succ[S]) {
+            int jc[3];
+            for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + s.e[d], g.J[d]);
+            out.push_back(g.id(band + 1, s.type, jc));
+        }
     return out;
 }
 
-int initial_count(const sp::TileTables &t, int band, int S) { return t.same_preds[S] + (band > 0 ? t.prev_preds[S] : 0); }
+int initial_count(const sp::TileTables &t, int band, int S, bool reuse)
+{
+    int n = t.same_preds[S];
+    if (band > 0) n += t.prev_preds[S] + (reuse ? (int)t.same_succ[S].size() : 0);
+    return n;
+}
 
 // global coordinate of local u along axis d
 int gcoord(const Grid &g, int band, int S, const int j[3], int d, int u)
@@ -102,7 +115,9 @@ bool setup(int B, const int n[3], int nbands, Grid *g, sp::TileTables *t, std::s
 extern "C" {
 
 // Structural checks on a concrete grid.  Returns 0 and fills msg on failure.
-int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
+// slots: 2 (ring of two band slots), 1 (one slot, with the reuse edges), or
+// -1 (one slot without them: a DAG the hazard check must reject).
+int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen, int slots)
 {
     int n[3] = {nx, ny, nz};
     Grid g;
@@ -113,6 +128,9 @@ int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
         return 0;
     };
     if (!setup(B, n, nbands, &g, &t, &err)) return fail(err);
+    if (slots != 1 && slots != 2 && slots != -1) return fail("slots must be 2, 1 or -1");
+    const bool reuse = slots == 1;
+    if (slots < 0) slots = 1;
     const int64_t R = g.regions(), sites = g.sites();
 
     // 1) exact cover: every (site, level) computed by exactly one region
@@ -140,13 +158,13 @@ int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
     std::vector<std::vector<int64_t>> succ(R);
     std::vector<int> indeg(R, 0);
     for (int64_t r = 0; r < R; ++r) {
-        succ[r] = successors(t, g, r);
+        succ[r] = successors(t, g, r, reuse);
         for (int64_t s : succ[r]) indeg[s]++;
     }
     for (int64_t r = 0; r < R; ++r) {
         int band, S, j[3];
         g.decode(r, &band, &S, j);
-        if (indeg[r] != initial_count(t, band, S)) return fail("predecessor count differs from releases");
+        if (indeg[r] != initial_count(t, band, S, reuse)) return fail("predecessor count differs from releases");
     }
     // reachability (descendants) by DFS from each region
     std::vector<std::vector<uint8_t>> reach(R, std::vector<uint8_t>(R, 0));
@@ -201,7 +219,9 @@ int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
     }
 
     // 4) mailbox hazards: writer of a mailbox word is a predecessor of its
-    //    reader; writers two bands later (same slot) are its descendants
+    //    reader; the writers of the next band that uses the same slot (two
+    //    bands later with a ring of two, the next band with one slot) are
+    //    its descendants
     for (int64_t r = 0; r < R; ++r) {
         int band, S, j[3];
         g.decode(r, &band, &S, j);
@@ -214,8 +234,8 @@ int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
                 for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + ((e.code >> (3 + d)) & 1), g.J[d]);
                 const int64_t consumer = g.id(band, e.code & 7, jc);
                 if (!reach[r][consumer]) return fail("mailbox writer is not a predecessor of its reader");
-                if (band >= 2) {
-                    const int64_t old_reader = g.id(band - 2, e.code & 7, jc);
+                if (band >= slots) {
+                    const int64_t old_reader = g.id(band - slots, e.code & 7, jc);
                     if (!reach[old_reader][r]) return fail("mailbox slot reused before its reader finished");
                 }
             }
@@ -251,7 +271,7 @@ int rx_check(int B, int nx, int ny, int nz, int nbands, char *msg, int msglen)
 // interleaved floats).  mode 0: whole-grid sweep; mode 1: regions in a random
 // topological order drawn from order_seed.  coef holds one LevelCoef per level.
 int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_seed, const float *coef4,
-           float dt, float inv_dx2, float eta2, float *phi, float *pi, float *c, char *msg, int msglen)
+           float dt, float inv_dx2, float eta2, float *phi, float *pi, float *c, char *msg, int msglen, int slots)
 {
     int n[3] = {nx, ny, nz};
     Grid g;
@@ -263,6 +283,7 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     };
     if (nsteps % (B / 2)) return fail("nsteps must be a multiple of B/2");
     if (!setup(B, n, nsteps / (B / 2), &g, &t, &err)) return fail(err);
+    if (slots != 1 && slots != 2) return fail("slots must be 1 or 2");
     const sp::LevelCoef *coef = reinterpret_cast<const sp::LevelCoef *>(coef4);
     sp::PhysConst q{dt, inv_dx2, eta2, 0.0f};
     f2 *F = reinterpret_cast<f2 *>(phi), *V = reinterpret_cast<f2 *>(pi), *K = reinterpret_cast<f2 *>(c);
@@ -304,7 +325,7 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     for (int64_t r = 0; r < R; ++r) {
         int band, S, j[3];
         g.decode(r, &band, &S, j);
-        count[r] = initial_count(t, band, S);
+        count[r] = initial_count(t, band, S, slots == 1);
         if (count[r] == 0) ready.push_back(r);
     }
     std::mt19937_64 rng(order_seed);
@@ -342,7 +363,7 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                         cs[ci] = K[s];
                     }
                 }
-        std::vector<f2> &mb = mbox[band & 1];
+        std::vector<f2> &mb = mbox[slots == 2 ? band & 1 : 0];
         const int64_t self = type_off[S] + (int64_t)(j[0] + g.J[0] * (j[1] + g.J[1] * j[2])) * t.mb_size[S];
         // every sloped-surface import of every level lands at region start, as
         // in the kernel: level k goes to the level-k phi buffer (k & 1)
@@ -398,7 +419,7 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                             K[s] = cs[ci];
                         }
         }
-        for (int64_t s : successors(t, g, r))
+        for (int64_t s : successors(t, g, r, slots == 1))
             if (--count[s] == 0) ready.push_back(s);
         ++done;
     }

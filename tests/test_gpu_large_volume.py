@@ -1,0 +1,112 @@
+"""The large-volume workload on one GPU: a 1280^3 matter-era network (nu = 2,
+lambda = 2, eta = 1, random phases, 2048 steps, energy and string length
+every 128 steps), region base 16.
+
+With the ring of two mailbox slots the sloped-surface mailboxes of this grid
+would take 2 x 160 GB, which with the 50 GB state does not fit in the GPU's
+memory; with one slot for every band (the default at base 16) they take
+160 GB.  The FP64 oracle of this size is out of reach (67 GB of host state and
+4.4e12 site-updates), so parity at full size is the property that holds at
+any size: the region path equals the monolithic sweep bit for bit (phi, pi
+and c), with the energy and string diagnostics finite along the way.
+"""
+import concurrent.futures as cf
+import os
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1011_4046_gb300 import inputs, sp  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+N = 1280
+STEPS = 2048
+EVERY = 128
+SLAB = 16  # z-planes generated per host task
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sp.load()
+
+
+def fill_random_phase(phi, n, seed):
+    """Writes the random-phase field into the device tensor phi (nz, ny, nx),
+    generated on the host slab by slab (the same values as the whole-field
+    generator)."""
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as pool:
+        jobs = {pool.submit(inputs.random_phase_slab, n, seed, z, min(z + SLAB, n[2])): z
+                for z in range(0, n[2], SLAB)}
+        for fut in cf.as_completed(jobs):
+            z = jobs[fut]
+            slab = torch.from_numpy(fut.result())
+            phi[z:z + slab.shape[0]].copy_(slab, non_blocking=False)
+
+
+def bit_equal(a, b):
+    return torch.equal(a.view(torch.float32).view(torch.int32), b.view(torch.float32).view(torch.int32))
+
+
+def test_large_volume_matter_era_region_equals_sweep():
+    n = (N, N, N)
+    sites = N ** 3
+    need = 24 * sites + 8 * sites + 160e9 + 9e9  # state, initial phi copy, one mailbox slot, counters + queue
+    free, _ = torch.cuda.mem_get_info()
+    if free < need * 1.02:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
+    p = sp.make_params(n, dx=1.0, dt=0.25, lam=2.0, eta=1.0, nu=2.0, tau0=10.0, tau_ref=10.0 + STEPS * 0.25)
+    shape = (N, N, N)
+    phi = torch.empty(shape, dtype=torch.complex64, device="cuda")
+    pic = torch.zeros(shape + (2,), dtype=torch.complex64, device="cuda")
+    t0 = time.time()
+    fill_random_phase(phi, n, 0)
+    phi0 = phi.clone()
+    t_init = time.time() - t0
+
+    g = sp.Grid([p], states=[(phi, pic)])
+    try:
+        g.plan(base_B=16, threads=0)
+        info = g.plan_info(0)
+        assert info["base_B"] == 16
+        assert 0 < info["mailbox_bytes"] < 200e9  # one slot
+        diags = []
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        region_ms = 0.0
+        for _ in range(STEPS // EVERY):
+            start.record(g.stream)
+            g.evolve(EVERY)
+            stop.record(g.stream)
+            stop.synchronize()
+            region_ms += start.elapsed_time(stop)
+            diags.append(g.diag(0))
+    finally:
+        g.close()
+
+    pic_b = torch.zeros_like(pic)
+    gb = sp.Grid([p], states=[(phi0, pic_b)])
+    try:
+        t1 = time.time()
+        gb.evolve(STEPS, sp.SP_MONOLITHIC)
+        torch.cuda.synchronize()
+        sweep_s = time.time() - t1
+    finally:
+        gb.close()
+
+    rate = sites * STEPS / (region_ms * 1e-3)
+    print(f"\n1280^3 x {STEPS}: init {t_init:.1f} s, region path {region_ms / 1e3:.2f} s "
+          f"({rate:.3e} site-updates/s, mailboxes {info['mailbox_bytes'] / 1e9:.1f} GB), sweep {sweep_s:.2f} s; "
+          f"string length {diags[0]['string_length']:.4g} -> {diags[-1]['string_length']:.4g}, "
+          f"energy {diags[0]['total']:.6g} -> {diags[-1]['total']:.6g}")
+    assert [d["level"] for d in diags] == list(range(EVERY, STEPS + 1, EVERY))
+    for d in diags:
+        assert np.isfinite(d["total"]) and d["total"] > 0
+        assert d["string_length"] > 0
+    assert bit_equal(phi, phi0), "phi differs between the region path and the sweep"
+    assert bit_equal(pic, pic_b), "(pi, c) differ between the region path and the sweep"

@@ -33,10 +33,12 @@ def params_for(n, nu, steps, dt=0.25, lam=2.0, eta=1.0, damp=0):
                           tau_ref=tau0 + (steps - damp) * dt, damp_steps=damp)
 
 
-def run_gpu(params, state, steps, flags=0, base_B=0, threads=0):
+def run_gpu(params, state, steps, flags=0, base_B=0, threads=0, slots=None):
     g = sp.Grid([params])
     try:
         g.write_state(0, *state)
+        if slots is not None:
+            g.set_option(sp.SP_OPT_MAILBOX_SLOTS, slots)
         if not flags & sp.SP_MONOLITHIC:
             g.plan(base_B=base_B, threads=threads)
         g.evolve(steps, flags)
@@ -178,6 +180,50 @@ def test_random_configurations_bit_exact(n, B, steps, nu, threads):
     reg = run_gpu(p, st, steps, base_B=B, threads=threads)
     assert all(np.all(np.isfinite(a)) for a in reg)
     assert_bit_equal(reg, run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC))
+
+
+@pytest.mark.parametrize("n,B,steps,nu,threads", [
+    ((16, 16, 16), 4, 11, 0.0, 0),      # base 4: seven seed types, remainder step
+    ((32, 48, 64), 8, 20, 2.0, 0),      # base 8, anisotropic, 5 bands
+    ((48, 32, 32), 16, 27, 2.0, 0),     # base 16, ragged
+    ((32, 48, 64), 8, 20, 2.0, 193),    # warp-specialised kernel
+    ((32, 32, 48), 16, 40, 1.0, 321),   # warp-specialised, 5 bands
+])
+def test_one_mailbox_slot_bit_exact(n, B, steps, nu, threads):
+    """One mailbox slot for every band instead of a ring of two: half the
+    mailbox memory, with each region also waiting for the previous band's
+    readers of the mailboxes it writes.  Results are bit-identical to the
+    sweep."""
+    p = params_for(n, nu, steps)
+    st = inputs.initial_state(n, 17, "gaussian", sigma=0.3)
+    reg = run_gpu(p, st, steps, base_B=B, threads=threads, slots=1)
+    assert all(np.all(np.isfinite(a)) for a in reg)
+    assert_bit_equal(reg, run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC))
+
+
+def test_one_mailbox_slot_halves_the_mailboxes_batched():
+    """Mixed bases in one call with one mailbox slot: every simulation equals
+    its sweep, and each plan holds half the mailbox bytes of the ring."""
+    specs = [((16, 16, 16), 0.0), ((32, 32, 32), 1.0), ((24, 16, 32), 2.0), ((48, 48, 48), 2.0)]
+    steps = 24
+    params = [params_for(n, nu, steps) for n, nu in specs]
+    states = [inputs.initial_state(n, 30 + i, "phase") for i, (n, _) in enumerate(specs)]
+    mb = {}
+    for slots in (2, 1):
+        g = sp.Grid(params)
+        try:
+            for i, st in enumerate(states):
+                g.write_state(i, *st)
+            g.set_option(sp.SP_OPT_MAILBOX_SLOTS, slots)
+            g.plan(base_B=0, threads=0)
+            g.evolve(steps)
+            got = [g.read_state(i) for i in range(len(specs))]
+            mb[slots] = [g.plan_info(i)["mailbox_bytes"] for i in range(len(specs))]
+        finally:
+            g.close()
+        for p, st, res in zip(params, states, got):
+            assert_bit_equal(res, run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC))
+    assert all(a == 2 * b > 0 for a, b in zip(mb[2], mb[1]))
 
 
 def test_full_size_matter_era_workload(oracle_mod):

@@ -8,8 +8,9 @@ exactly as the GPU kernel does:
 * the DAG the kernel releases is acyclic and its counters equal the
   number of releasing predecessors;
 * hazards -- every base or mailbox read is produced by a predecessor, and
-  nothing overwrites a value (band tops in the main arrays, the two-slot
-  mailbox ring) before every reader of it is done;
+  nothing overwrites a value (band tops in the main arrays, the mailboxes
+  as a ring of two band slots or as one slot for every band) before every
+  reader of it is done;
 * the regions executed one at a time in random topological orders with the
   FP32 site update reproduce a whole-grid FP32 sweep bit for bit.
 """
@@ -20,12 +21,23 @@ import pytest
 
 from paper_1011_4046_gb300 import inputs
 
+@pytest.mark.parametrize("slots", [2, 1])
 @pytest.mark.parametrize("B,n,bands", [(8, (16, 16, 16), 4), (8, (16, 24, 32), 4), (4, (8, 8, 12), 5),
                                        (6, (12, 18, 12), 4), (16, (32, 32, 32), 3)])
-def test_tiling_dag_and_hazards(rx, B, n, bands):
+def test_tiling_dag_and_hazards(rx, B, n, bands, slots):
     msg = ctypes.create_string_buffer(256)
-    ok = rx.rx_check(B, *n, bands, msg, 256)
+    ok = rx.rx_check(B, *n, bands, msg, 256, slots)
     assert ok == 1, msg.value.decode()
+
+
+@pytest.mark.parametrize("B,n", [(8, (16, 16, 16)), (4, (8, 8, 12)), (16, (32, 32, 32))])
+def test_one_slot_needs_the_reuse_edges(rx, B, n):
+    """With one mailbox slot but without the reuse edges, some writer of the
+    next band is not ordered after the reader of the mailbox it overwrites,
+    and the hazard check must say so (slots = -1 asks for exactly that DAG)."""
+    msg = ctypes.create_string_buffer(256)
+    assert rx.rx_check(B, *n, 3, msg, 256, -1) == 0
+    assert "reused before its reader finished" in msg.value.decode()
 
 
 def test_traffic_counts_match_the_brute_force_figures(rx):
@@ -63,19 +75,19 @@ def test_region_executor_bit_exact_vs_sweep(rx, B, n, steps, seed):
     coef = _coef_table(steps, 2.0, 0.25, 2.0, 10.0, 10.0 + steps * 0.25)
     fp = ctypes.POINTER(ctypes.c_float)
 
-    def run(mode, order_seed):
+    def run(mode, order_seed, slots):
         f, v, c = (np.ascontiguousarray(a, dtype=np.complex64).copy() for a in (phi0, pi0, c0))
         msg = ctypes.create_string_buffer(256)
         ok = rx.rx_run(B, *n, steps, mode, order_seed, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
                        f.view(np.float32).ctypes.data_as(fp), v.view(np.float32).ctypes.data_as(fp),
-                       c.view(np.float32).ctypes.data_as(fp), msg, 256)
+                       c.view(np.float32).ctypes.data_as(fp), msg, 256, slots)
         assert ok == 1, msg.value.decode()
         return f, v, c
 
-    ref = run(0, 0)
+    ref = run(0, 0, 2)
     assert np.all(np.isfinite(ref[0]))
-    for order_seed in (11, 12, 13):
-        got = run(1, order_seed)
+    for order_seed, slots in ((11, 2), (12, 2), (13, 1), (14, 1)):
+        got = run(1, order_seed, slots)
         for a, b in zip(ref, got):
             assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
