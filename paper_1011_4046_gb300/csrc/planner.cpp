@@ -89,6 +89,89 @@ inline bool in_u_box(int S, const int r[3], int B)
     return true;
 }
 
+// Region DAG of two consecutive bands on a non-periodic window of positions
+// |j_d| <= R around the origin: same-band edges, the inverted pyramids'
+// next-band edges (next band of parity q) and the given mailbox-reuse edges
+// (reuse[S] = (type, offset) list, one flag per entry).  Paths of the window
+// are paths of every periodic grid, so a pair found ordered here is ordered
+// there too; a pair the window misses is merely kept as an explicit edge.
+struct BandPairDag {
+    static constexpr int R = 3, W = 2 * R + 1;
+    const TileTables &t;
+    explicit BandPairDag(const TileTables &tt) : t(tt) {}
+    static int id(int band, int S, int x, int y, int z) { return (((band * kTypes + S) * W + z + R) * W + y + R) * W + x + R; }
+    // is (1, Sp, d) reachable from (0, S, 0), without pattern edge `skip`?
+    bool ordered(int q, const std::vector<std::vector<char>> &on, int S, const Succ &to, int skip_S, int skip_i) const
+    {
+        std::vector<char> seen(2 * kTypes * W * W * W, 0);
+        std::vector<int> stack = {id(0, S, 0, 0, 0)};
+        seen[stack[0]] = 1;
+        const int target = id(1, to.type, to.e[0], to.e[1], to.e[2]);
+        auto push = [&](int band, int type, int x, int y, int z) {
+            if (x < -R || x > R || y < -R || y > R || z < -R || z > R) return;
+            const int v = id(band, type, x, y, z);
+            if (!seen[v]) {
+                seen[v] = 1;
+                stack.push_back(v);
+            }
+        };
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            if (u == target) return true;
+            const int x = u % W - R, y = u / W % W - R, z = u / (W * W) % W - R;
+            const int type = u / (W * W * W) % kTypes, band = u / (W * W * W * kTypes);
+            for (const Succ &e : t.same_succ[type]) push(band, e.type, x + e.e[0], y + e.e[1], z + e.e[2]);
+            if (band == 1) continue;
+            if (type == kTypes - 1)
+                for (const Succ &e : t.next_succ[q]) push(1, e.type, x + e.e[0], y + e.e[1], z + e.e[2]);
+            for (size_t i = 0; i < t.reuse_succ[type].size(); ++i)
+                if (on[type][i] && !(type == skip_S && (int)i == skip_i)) {
+                    const Succ &e = t.reuse_succ[type][i];
+                    push(1, e.type, x + e.e[0], y + e.e[1], z + e.e[2]);
+                }
+        }
+        return false;
+    }
+};
+
+// Drops the mailbox-reuse edges that the rest of the DAG already implies, for
+// both parities of the next band: greedily, edges towards later-phase types
+// first, each removal checked on the DAG as it stands, and the end result
+// checked against every original pair (if that fails, nothing is dropped).
+// From base 6 on, eight edges remain per band position: from the inverted
+// pyramid of band b to the pyramids of band b+1 that do not build on its top,
+// since every writer of band b+1 comes after those pyramids.
+void prune_reuse(TileTables &t)
+{
+    BandPairDag dag(t);
+    std::vector<std::vector<char>> on(kTypes);
+    std::vector<std::pair<int, int>> order;
+    for (int S = 0; S < kTypes; ++S) {
+        on[S].assign(t.reuse_succ[S].size(), 1);
+        for (size_t i = 0; i < t.reuse_succ[S].size(); ++i) order.push_back({S, (int)i});
+    }
+    std::stable_sort(order.begin(), order.end(), [&](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+        return __builtin_popcount(t.reuse_succ[a.first][a.second].type) >
+               __builtin_popcount(t.reuse_succ[b.first][b.second].type);
+    });
+    for (const auto &o : order) {
+        const Succ &e = t.reuse_succ[o.first][o.second];
+        if (dag.ordered(0, on, o.first, e, o.first, o.second) && dag.ordered(1, on, o.first, e, o.first, o.second))
+            on[o.first][o.second] = 0;
+    }
+    for (int S = 0; S < kTypes; ++S)
+        for (const Succ &e : t.reuse_succ[S])
+            for (int q = 0; q < 2; ++q)
+                if (!dag.ordered(q, on, S, e, -1, -1)) return;  // keep every edge
+    for (int S = 0; S < kTypes; ++S) {
+        std::vector<Succ> kept;
+        for (size_t i = 0; i < t.reuse_succ[S].size(); ++i)
+            if (on[S][i]) kept.push_back(t.reuse_succ[S][i]);
+        t.reuse_succ[S] = kept;
+    }
+}
+
 }  // namespace
 
 std::string build_tables(int B, TileTables *tp)
@@ -304,6 +387,12 @@ std::string build_tables(int B, TileTables *tp)
         for (int S = 0; S < kTypes; ++S)
             for (const Succ &x : t.reuse_succ[S]) n += x.type == Sp;
         if (n != (int)t.same_succ[Sp].size()) return "mailbox-reuse edges do not mirror the same-band edges";
+    }
+    prune_reuse(t);
+    for (int Sp = 0; Sp < kTypes; ++Sp) {
+        t.reuse_preds[Sp] = 0;
+        for (int S = 0; S < kTypes; ++S)
+            for (const Succ &x : t.reuse_succ[S]) t.reuse_preds[Sp] += x.type == Sp;
     }
 
     // ---- exact cover of one period cell at every level ----

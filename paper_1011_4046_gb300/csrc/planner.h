@@ -87,13 +87,14 @@ struct TileTables {
     int32_t same_preds[kTypes], prev_preds[kTypes];
     std::vector<Succ> same_succ[kTypes];
     std::vector<Succ> next_succ[2];            // of an inverted pyramid, by parity of the next band
-    // Writers of a type-S mailbox, relative to the consumer (type, offset
-    // added to j): its same-band predecessors.  With one mailbox slot for all
-    // bands, region (b, S, j) must finish before the band-(b+1) regions that
-    // write the same addresses start; these are its mailbox-reuse successors
-    // (b+1, type, j + offset), and a region of type S' in band b+1 has
-    // same_succ[S'].size() mailbox-reuse predecessors.
+    // With one mailbox slot for all bands, region (b, S, j) must finish
+    // before the band-(b+1) regions that write the same addresses (its
+    // same-band predecessors' positions one band later) start.  These
+    // mailbox-reuse edges (b+1, type, j + offset) are kept only where the
+    // rest of the DAG does not already imply them; a region of type S' in
+    // band b+1 has reuse_preds[S'] of them.
     std::vector<Succ> reuse_succ[kTypes];
+    int32_t reuse_preds[kTypes];
     // traffic of this design per region, and site-updates per region
     int64_t bytes_read[kTypes], bytes_written[kTypes], updates[kTypes];
 };

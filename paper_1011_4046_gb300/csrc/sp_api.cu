@@ -297,6 +297,8 @@ int build_device_tables(sp_grid *g, int B)
         m.n_same_succ = (int)t.same_succ[S].size();
         m.same_preds = t.same_preds[S];
         m.prev_preds = t.prev_preds[S];
+        m.n_reuse = (int)t.reuse_succ[S].size();
+        m.reuse_preds = t.reuse_preds[S];
         for (int k = 0; k <= sp::kMaxHDev; ++k) m.active[k] = t.active[S][k];
         m.base_phi = t.base_phi[S];
         m.base_pc = t.base_pc[S];
@@ -369,8 +371,8 @@ int build_device_tables(sp_grid *g, int B)
     };
     std::vector<sp::Succ> reuse((size_t)sp::kTypes * sp::kMaxSameSucc, sp::Succ{0, {0, 0, 0}});
     for (int S = 0; S < sp::kTypes; ++S) {
-        if ((int)t.reuse_succ[S].size() != t.same_preds[S] || t.same_preds[S] > sp::kMaxSameSucc) return SP_EINVAL;
-        for (int i = 0; i < t.same_preds[S]; ++i) reuse[(size_t)S * sp::kMaxSameSucc + i] = t.reuse_succ[S][i];
+        if ((int)t.reuse_succ[S].size() > sp::kMaxSameSucc) return SP_EINVAL;
+        for (size_t i = 0; i < t.reuse_succ[S].size(); ++i) reuse[(size_t)S * sp::kMaxSameSucc + i] = t.reuse_succ[S][i];
     }
     up((void **)&td.d_imp, imp.data(), imp.size() * sizeof(unsigned short));
     up((void **)&td.d_exp, ex.data(), ex.size() * sizeof(int2));

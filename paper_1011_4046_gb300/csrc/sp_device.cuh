@@ -34,7 +34,9 @@ struct alignas(16) TypeMeta {
     int mb_level_off[kMaxHDev];
     int exp_off[kMaxHDev], exp_n[kMaxHDev];
     Succ same_succ[kMaxSameSucc];
-    int pad3[2];
+    // one mailbox slot: mailbox-reuse successors (in TablesDev::reuse) and
+    // predecessors of a region of this type in a band after the first
+    int n_reuse, reuse_preds;
 };
 
 // Geometry and surface-routing tables for one base size, in device memory.
@@ -56,7 +58,7 @@ struct alignas(16) TablesDev {
     int imp_n;      // 16-bit import entries of this base size (padded to 8)
     int imp_smem;   // their offset in the shared import area (16-bit units)
     // mailbox-reuse successors of a type-S region, reuse[S * kMaxSameSucc + i]
-    // for i < same_preds (used with a single mailbox slot), global memory
+    // for i < n_reuse (used with a single mailbox slot), global memory
     const Succ *reuse;
     const unsigned short *imp;  // all import lists, global memory
     const int2 *exp;            // all export entries, global memory

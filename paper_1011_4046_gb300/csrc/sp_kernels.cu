@@ -75,7 +75,7 @@ __global__ void reset_kernel(RegionArgs a)
     const unsigned per_band = 8u * (unsigned)sd.Jtot;
     const unsigned band = local / per_band;
     const int S = (int)((local - band * per_band) / (unsigned)sd.Jtot);
-    a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds + (sd.mb_reuse ? M[S].n_same_succ : 0) : 0);
+    a.counters[t] = M[S].same_preds + (band > 0 ? M[S].prev_preds + (sd.mb_reuse ? M[S].reuse_preds : 0) : 0);
     // queue position t: the first n_seed positions hold the seeds (with the
     // learned ordering seed_kernel writes them, bucket by bucket)
     a.queue[t] = (t < a.n_seed && !a.prio) ? seed_region(a, t) : -1;
@@ -156,7 +156,7 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
     // region's mailbox; one lane each, in passes of 32
     const int n_same = T.type[r.S].n_same_succ;
     const int n_next = (r.S == kTypes - 1 && r.band + 1 < sd.nbands) ? kMaxNextSucc : 0;
-    const int n_reuse = (sd.mb_reuse && r.band + 1 < sd.nbands) ? T.type[r.S].same_preds : 0;
+    const int n_reuse = (sd.mb_reuse && r.band + 1 < sd.nbands) ? T.type[r.S].n_reuse : 0;
     const int n_all = n_same + n_next + n_reuse;
     for (int p = 0; p < n_all; p += 32) {
         const int i = p + lane;

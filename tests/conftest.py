@@ -55,5 +55,6 @@ def rx():
                                               fp, fp, fp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int]
     L.rx_bytes_per_update.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 3
     L.rx_bytes_per_update.restype = ctypes.c_double
+    L.rx_reuse.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
     L.rx_active_box.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
     return L

@@ -78,7 +78,7 @@ std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t 
 int initial_count(const sp::TileTables &t, int band, int S, bool reuse)
 {
     int n = t.same_preds[S];
-    if (band > 0) n += t.prev_preds[S] + (reuse ? (int)t.same_succ[S].size() : 0);
+    if (band > 0) n += t.prev_preds[S] + (reuse ? t.reuse_preds[S] : 0);
     return n;
 }
 
@@ -424,6 +424,21 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         ++done;
     }
     if (done != R) return fail("not every region ran");
+    return 1;
+}
+
+// Mailbox-reuse edges per region type: successors n_succ[S] (and how many of
+// them go to pyramids, to_pyramid[S]) and predecessors preds[S].
+int rx_reuse(int B, int *n_succ, int *to_pyramid, int *preds)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return 0;
+    for (int S = 0; S < 8; ++S) {
+        n_succ[S] = (int)t.reuse_succ[S].size();
+        to_pyramid[S] = 0;
+        for (const sp::Succ &e : t.reuse_succ[S]) to_pyramid[S] += e.type == 0;
+        preds[S] = t.reuse_preds[S];
+    }
     return 1;
 }
 

@@ -30,6 +30,26 @@ def test_tiling_dag_and_hazards(rx, B, n, bands, slots):
     assert ok == 1, msg.value.decode()
 
 
+@pytest.mark.parametrize("B", [4, 6, 8, 16])
+def test_reuse_edges_reduce_to_the_inverted_pyramids(rx, B):
+    """Of the mailbox-reuse edges (every same-band edge mirrored one band
+    later), the planner keeps those the rest of the DAG does not imply.  From
+    base 6 on that is eight per position, all from the inverted pyramid of
+    band b to pyramids of band b+1: every writer of band b+1 comes after its
+    pyramids, and the inverted pyramid after every reader of band b.  At base
+    4 the wedges have no same-band predecessors, so the pyramids order
+    nothing and all 26 mirrored edges (all into the inverted pyramid's
+    mailbox) stay."""
+    n_succ, to_pyr, preds = ((ctypes.c_int * 8)() for _ in range(3))
+    assert rx.rx_reuse(B, n_succ, to_pyr, preds) == 1
+    assert list(n_succ)[:7] == [0] * 7
+    if B == 4:
+        assert n_succ[7] == 26 and sum(preds) == 26
+    else:
+        assert n_succ[7] == 8 and to_pyr[7] == 8
+        assert list(preds) == [8, 0, 0, 0, 0, 0, 0, 0]
+
+
 @pytest.mark.parametrize("B,n", [(8, (16, 16, 16)), (4, (8, 8, 12)), (16, (32, 32, 32))])
 def test_one_slot_needs_the_reuse_edges(rx, B, n):
     """With one mailbox slot but without the reuse edges, some writer of the
