@@ -334,6 +334,7 @@ def run_ours(args):
                    "leapfrog_steps": STEPS, "region_base": base,
                    "regions": int(info["regions_per_band"] * (STEPS // (base // 2))),
                    "threads_per_cta": info["threads"], "ctas": info["grid"],
+                   "mailbox_slots": info["mailbox_slots"], "mailbox_bytes": info["mailbox_bytes"],
                    "l2": "flushed (512 MiB write) before every step; state restored on device outside timing",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "monolithic": {"value": mono_value, "unit": "site-updates/s", "ms_per_step": sum(mono_ms) / len(mono_ms),
@@ -421,6 +422,8 @@ def run_batched(args):
                        "threads_per_cta": {str(b): next(i["threads"] for i in infos if i["base_B"] == b)
                                            for b in bases},
                        "ctas": {str(b): next(i["grid"] for i in infos if i["base_B"] == b) for b in bases},
+                       "mailbox_slots": {str(b): next(i["mailbox_slots"] for i in infos if i["base_B"] == b)
+                                         for b in bases},
                        "autotune_s": tune_s, "autotune_candidates": infos[0]["tune_candidates"],
                        "l2": "flushed (512 MiB write) before every step; states restored on device outside timing",
                        "parallelism": "1 GPU"},

@@ -92,12 +92,10 @@ extern "C" {
 #define SP_OPT_GRAPHS 3             /* 1 (default): capture region calls into CUDA graphs on
                                        non-legacy streams; 0: launch directly */
 #define SP_OPT_MAILBOX_SLOTS 4      /* sloped-surface mailboxes, applied by the next sp_region_plan:
-                                       2: a ring of two band slots; 1: one slot for every band, half
-                                       the memory (sp_plan_info.mailbox_bytes), with each region also
+                                       1 (default): one slot for every band, with each region also
                                        waiting for the previous band's readers of the mailboxes it
-                                       writes (results identical); 0 (default): one slot at base 16
-                                       or where the ring would not fit in free device memory, else
-                                       the ring */
+                                       writes; 2: a ring of two band slots, twice the memory
+                                       (sp_plan_info.mailbox_bytes).  Results are identical. */
 
 /* ---- region cost model ---- */
 #define SP_MODEL_FEATURES 16
@@ -148,6 +146,8 @@ typedef struct {
     int32_t tune_candidates; /* candidates the autotuner timed */
     double tune_best_ms;     /* its trial time of the chosen candidate (16 steps) */
     double tune_default_ms;  /* its trial time of the default choice, 0 if not timed */
+    int32_t mailbox_slots;   /* 2: ring of two band slots; 1: one slot for every band */
+    int32_t reserved;
 } sp_plan_info;
 
 /*

@@ -171,7 +171,7 @@ struct sp_grid {
     std::vector<float2 *> mbox;
     std::vector<long long> mb_slot;   // float2 offset of band slot 1 (0: one slot for every band)
     std::vector<long long> mb_elems;  // float2 elements per slot
-    int mb_slots = 0;                 // SP_OPT_MAILBOX_SLOTS (0: by base and free memory), applied by sp_region_plan
+    int mb_slots = 1;                 // SP_OPT_MAILBOX_SLOTS, applied by sp_region_plan
     std::vector<std::array<long long, sp::kTypes>> mb_type_off;
     // launch scratch
     int *d_counters = nullptr, *d_queue = nullptr;
@@ -656,16 +656,12 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
     }
     if ((int)g->groups.size() > kMaxGroups) return SP_EINVAL;
     g->order = order;
-    // mailboxes: a ring of two band slots per simulation, or one slot for
-    // every band (half the memory; regions then also wait for the previous
-    // band's readers of the mailboxes they write).  By default one slot at
-    // base 16 (measured as fast as the ring at 128^3) and wherever the ring
-    // would not fit in free device memory; the ring at bases 4 and 8 (whose
-    // managers measured 1.4 % slower with the extra releases).
+    // mailboxes: one slot for every band (the default: half the memory of
+    // the ring, measured as fast at bases 8 and 16; regions also wait for the
+    // previous band's readers of the mailboxes they write), or a ring of two
+    // band slots
     g->mb_slot.assign(g->n_sims, 0);
     g->mb_elems.assign(g->n_sims, 0);
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
     g->mb_type_off.assign(g->n_sims, {});
     for (int s = 0; s < g->n_sims; ++s) {
         const sp::TileTables &t = g->tables[g->B[s]].host;
@@ -676,15 +672,10 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
             g->mb_type_off[s][S] = off;
             off += J * t.mb_size[S];
         }
-        int slots = g->mb_slots;
-        if (slots == 0) {
-            const size_t ring = 2 * (size_t)off * sizeof(float2);
-            slots = (g->B[s] >= 16 || ring > free_b / 10 * 9) ? 1 : 2;
-        }
+        const int slots = g->mb_slots;
         g->mb_elems[s] = off;
         g->mb_slot[s] = slots == 2 ? off : 0;
         const size_t bytes = std::max<size_t>((size_t)slots * off * sizeof(float2), 16);
-        free_b = free_b > bytes ? free_b - bytes : 0;
         float2 *m = nullptr;
         e = cudaMalloc((void **)&m, bytes);
         if (e != cudaSuccess) {
@@ -1115,7 +1106,7 @@ int sp_set_option(sp_grid *g, int32_t option, int64_t value)
         g->use_graphs = (int)value;
         return SP_OK;
     case SP_OPT_MAILBOX_SLOTS:
-        if (value < 0 || value > 2) return SP_EINVAL;
+        if (value != 1 && value != 2) return SP_EINVAL;
         g->mb_slots = (int)value;
         return SP_OK;
     default:
@@ -1242,7 +1233,8 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         info.bytes_read_per_band = ps.bytes_read_per_band;
         info.bytes_written_per_band = ps.bytes_written_per_band;
         info.bytes_per_update = ps.bytes_per_update;
-        info.mailbox_bytes = (g->mb_slot[sim] ? 2 : 1) * g->mb_elems[sim] * (int64_t)sizeof(float2);
+        info.mailbox_slots = g->mb_slot[sim] ? 2 : 1;
+        info.mailbox_bytes = info.mailbox_slots * g->mb_elems[sim] * (int64_t)sizeof(float2);
         info.autotuned = g->tune.autotuned;
         info.tune_candidates = g->tune.candidates;
         info.tune_best_ms = g->tune.best_ms;

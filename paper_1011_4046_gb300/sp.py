@@ -107,6 +107,8 @@ class sp_plan_info(ctypes.Structure):
         ("tune_candidates", ctypes.c_int32),
         ("tune_best_ms", ctypes.c_double),
         ("tune_default_ms", ctypes.c_double),
+        ("mailbox_slots", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

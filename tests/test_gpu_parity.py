@@ -224,6 +224,15 @@ def test_one_mailbox_slot_halves_the_mailboxes_batched():
         for p, st, res in zip(params, states, got):
             assert_bit_equal(res, run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC))
     assert all(a == 2 * b > 0 for a, b in zip(mb[2], mb[1]))
+    # one slot is the default
+    g = sp.Grid(params[:1])
+    try:
+        g.plan(base_B=8, threads=0)
+        assert g.plan_info(0)["mailbox_slots"] == 1
+        with pytest.raises(sp.SpError):
+            g.set_option(sp.SP_OPT_MAILBOX_SLOTS, 3)
+    finally:
+        g.close()
 
 
 def test_full_size_matter_era_workload(oracle_mod):
