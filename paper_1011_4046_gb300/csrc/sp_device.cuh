@@ -91,15 +91,18 @@ struct alignas(16) SimDev {
 // Priority buckets of the learned ordering (bucket 0 is queued first).
 constexpr int kBuckets = 4;
 
-// Work-queue control block.
-struct Ctl {
+// Work-queue control block.  Every manager of the launch takes queue positions
+// from head and pushes at tail (one atomic each per region), and polls error
+// while it waits: the three sit in 128-byte lines of their own, so that the
+// atomics on one do not queue behind those on another at the same L2 slice.
+struct alignas(128) Ctl {
     unsigned int head;   // next queue position to pop
+    unsigned int pad_head[31];
     unsigned int tail;   // next queue position to push
+    unsigned int pad_tail[31];
     int error;           // first device error (0 = none)
     int error_info;
     unsigned long long wait_limit_ns;  // per-wait bound for every spin
-    unsigned int completed;            // regions finished
-    unsigned int pad;
     unsigned int bcount[kBuckets];     // learned ordering: band-0 seeds per bucket,
     unsigned int bcursor[kBuckets];    // and the next free position of each bucket's run
 };

@@ -61,7 +61,6 @@ __global__ void reset_kernel(RegionArgs a)
         a.ctl->tail = a.n_seed;
         a.ctl->error = 0;
         a.ctl->error_info = 0;
-        a.ctl->completed = 0;
         for (int b = 0; b < kBuckets; ++b) {
             a.ctl->bcount[b] = 0;
             a.ctl->bcursor[b] = 0;
@@ -147,10 +146,7 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
                                    int lane, unsigned long long t_start, int g)
 {
     __syncwarp();
-    if (g == a.fault_drop) {  // injected failure: completion is never reported downstream
-        if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
-        return;
-    }
+    if (g == a.fault_drop) return;  // injected failure: completion is never reported downstream
     // successors: same band, then the next band's (an inverted pyramid's
     // 27), then with a single mailbox slot the next band's writers of this
     // region's mailbox; one lane each, in passes of 32
@@ -202,7 +198,6 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
             }
         }
     }
-    if (lane == 0) atomicAdd(&a.ctl->completed, 1u);
     (void)t_start;
 }
 
