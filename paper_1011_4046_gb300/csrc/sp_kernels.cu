@@ -181,21 +181,19 @@ __device__ void release_successors(const RegionArgs &a, const SimDev &sd, const 
             const int old = atom_add_acq_rel_gpu(a.counters + t, -1);
             ready = old == 1;
             region = (int)t;
-            if (a.prio == nullptr && ready) {
-                const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
-                st_release_gpu(a.queue + pos, (int)t);
-            }
         }
-        if (a.prio) {
-            // learned ordering: the successors made ready here are queued bucket by bucket
-            const int b = ready ? a.prio[region] : kBuckets;
-            for (int q = 0; q < kBuckets; ++q) {
-                if (b == q) {
-                    const unsigned pos = atomicAdd(&a.ctl->tail, 1u);
-                    st_release_gpu(a.queue + pos, region);
-                }
-                __syncwarp();
-            }
+        // push the successors made ready here with one queue-tail atomic per
+        // warp (every manager of the launch pushes at the same tail); the
+        // learned ordering pushes them bucket by bucket
+        for (int q = 0; q < (a.prio ? kBuckets : 1); ++q) {
+            const bool mine = ready && (a.prio == nullptr || a.prio[region] == q);
+            const unsigned m = __ballot_sync(0xffffffffu, mine);
+            if (m == 0) continue;
+            const int leader = __ffs((int)m) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&a.ctl->tail, (unsigned)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (mine) st_release_gpu(a.queue + base + __popc(m & ((1u << lane) - 1u)), region);
         }
     }
     (void)t_start;
