@@ -56,6 +56,8 @@ def test_struct_layouts_match_the_header(lib):
     # sp_params: 3 int32 + 7 double + 2 int32 with natural alignment
     assert ctypes.sizeof(sp.sp_params) == 12 + 4 + 7 * 8 + 8
     assert ctypes.sizeof(sp.sp_diag) == 8 + 6 * 8 + 3 * 8 + 8 + 3 * 8 + 8
+    # sp_plan_info: 4 int32, 4 int64, double, int64, 2 int32, 2 double, 2 int32
+    assert ctypes.sizeof(sp.sp_plan_info) == 16 + 32 + 8 + 8 + 8 + 16 + 8
 
 
 def test_model_entry_points_reject_bad_input_without_a_gpu(lib, tmp_path):
@@ -78,11 +80,39 @@ def test_options_and_levels_reject_null_handles(lib):
     assert lib.sp_write_surface(None, 0, sp.SP_SURF_LEVEL, ctypes.byref(v), 8, 0) == sp.SP_EINVAL
 
 
+def _header_struct_fields(text, name):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    import re
+    m = re.search(r"typedef struct \{(.*?)\}\s*" + name + r"\s*;", text, re.S)
+    assert m, name
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        _, names = decl.split(None, 1)
+        for n in names.split(","):
+            fields.append(re.sub(r"\[.*\]", "", n).strip())
+    return fields
+
+
+@pytest.mark.parametrize("name", ["sp_params", "sp_diag", "sp_plan_info"])
+def test_binding_structs_mirror_the_header(name):
+    """The ctypes mirrors of the ABI structs list the header's fields in the
+    header's order (a field added on one side only would shift the rest)."""
+    text = open(sp.HEADER).read()
+    renamed = {"lambda": "lam"}  # a Python keyword
+    want = [renamed.get(f, f) for f in _header_struct_fields(text, name)]
+    assert [f for f, _ in getattr(sp, name)._fields_] == want
+
+
 def test_header_constants_match_the_binding():
     text = open(sp.HEADER).read()
     import re
     for name in ("SP_AUTOTUNE", "SP_FEATURES", "SP_SURF_FEATURES", "SP_SURF_LEVEL", "SP_OPT_WAIT_LIMIT_NS",
-                 "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_MODEL_PARAMS", "SP_MODEL_FEATURES",
+                 "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_OPT_MAILBOX_SLOTS", "SP_MODEL_PARAMS",
+                 "SP_MODEL_FEATURES",
                  "SP_ORDER_STATIC", "SP_ORDER_LEARNED", "SP_TIMING", "SP_TRACE"):
         m = re.search(r"#define\s+" + name + r"\s+\(?(-?\d+)u?\)?", text)
         assert m, name
