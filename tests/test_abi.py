@@ -83,7 +83,7 @@ def test_options_and_levels_reject_null_handles(lib):
 def _header_struct_fields(text, name):
     """Field names, in order, of `typedef struct { ... } name;` in the header."""
     import re
-    m = re.search(r"typedef struct \{(.*?)\}\s*" + name + r"\s*;", text, re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
     assert m, name
     body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
     fields = []
