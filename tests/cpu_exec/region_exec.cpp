@@ -48,6 +48,85 @@ struct Grid {
 
 int wrap(int p, int n) { return ((p % n) + n) % n; }
 
+// ---- study: transitive reduction of the region DAG's pattern ----
+// A pattern edge runs from (b, S, j) to (b + dband, T, j + d); par is the
+// parity of band b + 1 an inverted pyramid's next-band edge belongs to (-1:
+// every band).  The reduction drops, one edge at a time, every edge whose
+// endpoints stay connected through the edges still kept, on a window of
+// three bands and positions |j_d| <= R (a window path is a path of every
+// periodic grid, so the reduction never drops an edge it cannot replace),
+// and for both band parities.  With g_reduced set the executor releases and
+// counts by the reduced pattern (one mailbox slot only: its next-band edges
+// are implied through the mailbox-reuse edges).
+struct PEdge {
+    int S, dband, T, d[3], par;
+    bool on;
+};
+bool g_reduced = false;
+std::vector<PEdge> g_pattern;
+int g_pattern_B = 0;
+
+constexpr int kWinR = 3, kWinW = 2 * kWinR + 1;
+int win_id(int b, int S, int x, int y, int z) { return (((b * 8 + S) * kWinW + z + kWinR) * kWinW + y + kWinR) * kWinW + x + kWinR; }
+
+bool win_reach(const std::vector<PEdge> &es, int q, const PEdge &target, int skip)
+{
+    std::vector<char> seen(3 * 8 * kWinW * kWinW * kWinW, 0);
+    std::vector<int> stack = {win_id(0, target.S, 0, 0, 0)};
+    seen[stack[0]] = 1;
+    const int goal = win_id(target.dband, target.T, target.d[0], target.d[1], target.d[2]);
+    while (!stack.empty()) {
+        const int u = stack.back();
+        stack.pop_back();
+        if (u == goal) return true;
+        const int x = u % kWinW - kWinR, y = u / kWinW % kWinW - kWinR, z = u / (kWinW * kWinW) % kWinW - kWinR;
+        const int S = u / (kWinW * kWinW * kWinW) % 8, b = u / (kWinW * kWinW * kWinW * 8);
+        for (size_t k = 0; k < es.size(); ++k) {
+            const PEdge &e = es[k];
+            if (!e.on || (int)k == skip || e.S != S || b + e.dband > 2) continue;
+            if (e.par >= 0 && e.par != ((q + b) & 1)) continue;  // band b + 1 has parity q + b
+            const int a = x + e.d[0], bb = y + e.d[1], c = z + e.d[2];
+            if (a < -kWinR || a > kWinR || bb < -kWinR || bb > kWinR || c < -kWinR || c > kWinR) continue;
+            const int v = win_id(b + e.dband, e.T, a, bb, c);
+            if (!seen[v]) {
+                seen[v] = 1;
+                stack.push_back(v);
+            }
+        }
+    }
+    return false;
+}
+
+std::vector<PEdge> reduced_pattern(const sp::TileTables &t)
+{
+    std::vector<PEdge> es;
+    for (int S = 0; S < 8; ++S)
+        for (const sp::Succ &s : t.same_succ[S]) es.push_back({S, 0, s.type, {s.e[0], s.e[1], s.e[2]}, -1, true});
+    for (int q = 0; q < 2; ++q)
+        for (const sp::Succ &s : t.next_succ[q]) es.push_back({7, 1, s.type, {s.e[0], s.e[1], s.e[2]}, q, true});
+    for (int S = 0; S < 8; ++S)
+        for (const sp::Succ &s : t.reuse_succ[S]) es.push_back({S, 1, s.type, {s.e[0], s.e[1], s.e[2]}, -1, true});
+    for (size_t k = 0; k < es.size(); ++k) {
+        bool implied = true;
+        for (int q = 0; q < 2 && implied; ++q)
+            if (es[k].par < 0 || es[k].par == q) implied = win_reach(es, q, es[k], (int)k);
+        if (implied) es[k].on = false;
+    }
+    std::vector<PEdge> kept;
+    for (const PEdge &e : es)
+        if (e.on) kept.push_back(e);
+    return kept;
+}
+
+const std::vector<PEdge> &pattern_for(const sp::TileTables &t)
+{
+    if (g_pattern_B != t.B) {
+        g_pattern = reduced_pattern(t);
+        g_pattern_B = t.B;
+    }
+    return g_pattern;
+}
+
 // successors exactly as the kernel releases them; reuse: with the
 // mailbox-reuse edges of a single mailbox slot
 std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t r, bool reuse)
@@ -55,6 +134,16 @@ std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t 
     int band, S, j[3];
     g.decode(r, &band, &S, j);
     std::vector<int64_t> out;
+    if (g_reduced && reuse) {
+        for (const PEdge &e : pattern_for(t)) {
+            if (e.S != S || band + e.dband >= g.nbands) continue;
+            if (e.par >= 0 && e.par != ((band + 1) & 1)) continue;
+            int jc[3];
+            for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + e.d[d], g.J[d]);
+            out.push_back(g.id(band + e.dband, e.T, jc));
+        }
+        return out;
+    }
     for (const sp::Succ &s : t.same_succ[S]) {
         int jc[3];
         for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + s.e[d], g.J[d]);
@@ -77,6 +166,12 @@ std::vector<int64_t> successors(const sp::TileTables &t, const Grid &g, int64_t 
 
 int initial_count(const sp::TileTables &t, int band, int S, bool reuse)
 {
+    if (g_reduced && reuse) {
+        int n = 0;
+        for (const PEdge &e : pattern_for(t))
+            if (e.T == S && (e.dband == 0 || (band > 0 && (e.par < 0 || e.par == (band & 1))))) ++n;
+        return n;
+    }
     int n = t.same_preds[S];
     if (band > 0) n += t.prev_preds[S] + (reuse ? t.reuse_preds[S] : 0);
     return n;
@@ -425,6 +520,25 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     }
     if (done != R) return fail("not every region ran");
     return 1;
+}
+
+// Study switch: release and count by the transitively reduced pattern (one
+// mailbox slot only).  Returns the number of pattern edges kept for base B
+// and fills kept_by_source[8] (edges leaving each region type) and
+// kept_kind[3] (same-band, next-band, mailbox-reuse).
+int rx_reduced_dag(int B, int on, int *kept_by_source, int *kept_kind)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return -1;
+    g_reduced = on != 0;
+    const std::vector<PEdge> &p = pattern_for(t);
+    for (int S = 0; S < 8; ++S) kept_by_source[S] = 0;
+    for (int k = 0; k < 3; ++k) kept_kind[k] = 0;
+    for (const PEdge &e : p) {
+        kept_by_source[e.S]++;
+        kept_kind[e.dband == 0 ? 0 : (e.par >= 0 ? 1 : 2)]++;
+    }
+    return (int)p.size();
 }
 
 // Mailbox-reuse edges per region type: successors n_succ[S] (and how many of

@@ -120,3 +120,64 @@ def test_predecessor_free_types_lead(rx, B, seeds):
     imports nothing, so seven types are seeds; from base 6 on only the
     pyramid is."""
     assert rx.rx_seed_types(B) == seeds
+
+
+# ------------------------------------------------ reduced region DAG (study)
+def _reduced(rx, B, on):
+    by_src, kind = (ctypes.c_int * 8)(), (ctypes.c_int * 3)()
+    n = rx.rx_reduced_dag(B, 1 if on else 0, by_src, kind)
+    return n, list(by_src), list(kind)
+
+
+@pytest.mark.parametrize("B", [8, 16])
+def test_reduced_dag_keeps_a_third_of_the_edges(rx, B):
+    """Transitive reduction of the release pattern with one mailbox slot: of
+    the 56 same-band, 2 x 27 next-band and 8 mailbox-reuse edges per position,
+    24 same-band and the 8 reuse edges remain; every next-band edge is implied
+    through the reuse edges.  A pyramid would release 6 successors instead of
+    26, an inverted pyramid 8 instead of 35."""
+    n, by_src, kind = _reduced(rx, B, False)
+    assert n == 32 and kind == [24, 0, 8]
+    assert by_src[0] == 6 and by_src[7] == 8
+
+
+@pytest.mark.parametrize("B,n,bands", [(8, (16, 16, 16), 4), (8, (16, 24, 32), 4), (4, (8, 8, 12), 5),
+                                       (6, (12, 18, 12), 4), (16, (32, 32, 32), 3)])
+def test_reduced_dag_is_hazard_free(rx, B, n, bands):
+    """The reduced pattern, released and counted on concrete periodic grids,
+    passes the same cover, counter and hazard checks as the full one."""
+    msg = ctypes.create_string_buffer(256)
+    try:
+        _reduced(rx, B, True)
+        ok = rx.rx_check(B, *n, bands, msg, 256, 1)
+    finally:
+        _reduced(rx, B, False)
+    assert ok == 1, msg.value.decode()
+
+
+@pytest.mark.parametrize("B,n,steps,seed", [(8, (16, 16, 16), 16, 21), (16, (32, 32, 32), 16, 22)])
+def test_reduced_dag_runs_bit_exact(rx, B, n, steps, seed):
+    """Regions executed in random topological orders of the reduced DAG give
+    the whole-grid sweep bit for bit."""
+    phi0, pi0, c0 = inputs.initial_state(n, seed, "gaussian")
+    coef = _coef_table(steps, 2.0, 0.25, 2.0, 10.0, 10.0 + steps * 0.25)
+    fp = ctypes.POINTER(ctypes.c_float)
+
+    def run(mode, order_seed):
+        f, v, c = (np.ascontiguousarray(a, dtype=np.complex64).copy() for a in (phi0, pi0, c0))
+        msg = ctypes.create_string_buffer(256)
+        ok = rx.rx_run(B, *n, steps, mode, order_seed, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
+                       f.view(np.float32).ctypes.data_as(fp), v.view(np.float32).ctypes.data_as(fp),
+                       c.view(np.float32).ctypes.data_as(fp), msg, 256, 1)
+        assert ok == 1, msg.value.decode()
+        return f, v, c
+
+    ref = run(0, 0)
+    try:
+        _reduced(rx, B, True)
+        got = [run(1, s) for s in (31, 32)]
+    finally:
+        _reduced(rx, B, False)
+    for g in got:
+        for a, b in zip(ref, g):
+            assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
