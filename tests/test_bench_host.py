@@ -26,3 +26,36 @@ def test_smem_line_uses_the_sampled_clock():
     assert r["peak"] == pytest.approx(152 * 128 * 1e9 / 1e9)
     assert r["achieved"] == pytest.approx(96 * 1e6 / 1e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu record only while every
+    source that shapes the region kernel's memory traffic is byte-identical to
+    the one the record was taken on, and only for the workload it was taken on."""
+    import hashlib
+    import json
+
+    for i, rel in enumerate(bench.KERNEL_SOURCES):
+        p = tmp_path / rel
+        p.parent.mkdir(parents=True, exist_ok=True)
+        p.write_text(f"source {i}\n")
+    h = hashlib.sha256()
+    for rel in bench.KERNEL_SOURCES:
+        h.update((tmp_path / rel).read_bytes())
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "region_kernel_traffic.json").write_text(json.dumps({
+        "kernel_sources_sha256_16": h.hexdigest()[:16],
+        "dram_bytes_read_per_launch": 7, "dram_bytes_write_per_launch": 5}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic(True) == 12
+    assert bench.ncu_traffic(False) is None
+    (tmp_path / bench.KERNEL_SOURCES[0]).write_text("changed\n")
+    assert bench.ncu_traffic(True) is None
+
+
+def test_committed_traffic_record_names_its_capture():
+    import json
+
+    rec = json.load(open(os.path.join(ROOT, "profiles", "region_kernel_traffic.json")))
+    assert rec["kernel"] == "region_kernel" and "ncu" in rec["command"] and "--clock-control none" in rec["command"]
+    assert rec["dram_bytes_read_per_launch"] > 0 and rec["dram_bytes_write_per_launch"] > 0
