@@ -333,3 +333,63 @@ def test_winding_equals_geodesic_phase_rule(oracle_mod):
             total += (d + np.pi) % (2 * np.pi) - np.pi
         ref = np.rint(total / (2 * np.pi)).astype(np.int64)
         assert np.array_equal(ref, w[k].astype(np.int64))
+
+
+# ------------------------------------------- energy balance in an expanding era
+def _energy_balance_residual(o, dt, nu=2.0, lam=2.0, eta=1.0, tau0=10.0, span=4.0, n=12):
+    """|E_end - E_0 - integral of dE/dtau| along the oracle's trajectory.
+
+    For phi'' + (2 nu/tau) phi' - Lap phi + a^2 lambda (|phi|^2 - eta^2) phi = 0
+    with a = (tau/tau_ref)^nu and E = sum |phi'|^2 + sum_links |d phi|^2 / dx^2 +
+    a^2 (lambda/2) sum (|phi|^2 - eta^2)^2, the equation gives
+    dE/dtau = -(4 nu/tau) sum |phi'|^2 + (2 nu/tau) a^2 (lambda/2) sum (|phi|^2 - eta^2)^2.
+    Energies are taken at whole levels (kinetic term: mean of the two
+    neighbouring half-step |pi|^2), the rate at half levels (pi_{n+1/2}, phi
+    averaged), all computed here from those definitions.  A smooth field starts
+    at rest, with pi_{-1/2} = -(dt/2) phi''(tau0)."""
+    tau_ref = tau0 + span
+    x = np.arange(n) * 2 * np.pi / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi = (0.6 + 0.3 * np.cos(X) + 0.2 * np.sin(Y + Z)) + 1j * (0.4 * np.sin(X) - 0.3 * np.cos(Z))
+
+    def lap(f):
+        return sum(np.roll(f, 1, ax) + np.roll(f, -1, ax) for ax in range(3)) - 6 * f
+
+    def links(f):
+        return sum(np.sum(np.abs(np.roll(f, -1, ax) - f) ** 2) for ax in range(3))
+
+    def pot(f, tau):
+        a = (tau / tau_ref) ** nu
+        return a * a * lam / 2 * np.sum((np.abs(f) ** 2 - eta ** 2) ** 2)
+
+    a0 = (tau0 / tau_ref) ** nu
+    pi = -0.5 * dt * (lap(phi) - a0 * a0 * lam * (np.abs(phi) ** 2 - eta ** 2) * phi)
+    p = o.make_params((n, n, n), lam=lam, eta=eta, nu=nu, dt=dt, tau0=tau0, tau_ref=tau_ref)
+    steps = int(round(span / dt))
+    e_first = e_last = None
+    work = 0.0
+    for s in range(steps):
+        phi1, pi1 = o.step(p, phi, pi, s)
+        tau = tau0 + s * dt
+        e = 0.5 * (np.sum(np.abs(pi) ** 2) + np.sum(np.abs(pi1) ** 2)) + links(phi) + pot(phi, tau)
+        e_first = e if e_first is None else e_first
+        e_last = e
+        if s < steps - 1:
+            th = tau + dt / 2
+            ah = (th / tau_ref) ** nu
+            fb = 0.5 * (phi + phi1)
+            work += dt * (-4 * nu / th * np.sum(np.abs(pi1) ** 2)
+                          + 2 * nu / th * ah * ah * lam / 2 * np.sum((np.abs(fb) ** 2 - eta ** 2) ** 2))
+        phi, pi = phi1, pi1
+    return abs(e_last - e_first - work), abs(e_last - e_first)
+
+
+def test_expanding_era_energy_balance_is_second_order(oracle_mod):
+    """nu = 2, lambda = 2: friction, the growing mass a^2 lambda and the
+    lattice gradient together obey the continuum energy balance, with a
+    residual that falls as dt^2 (a dropped friction factor, a wrong power of
+    a or a missing gradient term would leave an O(1) or O(dt) residual)."""
+    res = [_energy_balance_residual(oracle_mod, dt) for dt in (0.02, 0.01, 0.005)]
+    r1, r2 = res[0][0] / res[1][0], res[1][0] / res[2][0]
+    assert 3.2 < r1 < 4.6 and 3.2 < r2 < 4.6, res
+    assert all(r < 1e-4 * d for r, d in res), res
