@@ -56,6 +56,7 @@ def rx():
     L.rx_bytes_per_update.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int64)] * 3
     L.rx_bytes_per_update.restype = ctypes.c_double
     L.rx_reuse.argtypes = [ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.rx_same_succ.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
     L.rx_reduced_dag.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 2
     L.rx_active_box.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
     return L

@@ -541,6 +541,20 @@ int rx_reduced_dag(int B, int on, int *kept_by_source, int *kept_kind)
     return (int)p.size();
 }
 
+// Same-band successor types of a type-S region (with repeats, one per edge):
+// returns their number and writes up to max of them to types.
+int rx_same_succ(int B, int S, int *types, int max)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty() || S < 0 || S > 7) return -1;
+    int n = 0;
+    for (const sp::Succ &e : t.same_succ[S]) {
+        if (n < max) types[n] = e.type;
+        ++n;
+    }
+    return n;
+}
+
 // Mailbox-reuse edges per region type: successors n_succ[S] (and how many of
 // them go to pyramids, to_pyramid[S]) and predecessors preds[S].
 int rx_reuse(int B, int *n_succ, int *to_pyramid, int *preds)

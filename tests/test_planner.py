@@ -181,3 +181,28 @@ def test_reduced_dag_runs_bit_exact(rx, B, n, steps, seed):
     for g in got:
         for a, b in zip(ref, g):
             assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("B", [6, 8, 16])
+def test_a_band_runs_in_the_papers_four_layers(rx, B):
+    """Same-band edges only go from a region type to a strict superset of its
+    inverted axes, so a band's regions fall into dependency layers by |S|;
+    the longest chain of same-band dependencies has as many regions as the
+XX
+    single level imports nothing, so the chain is pyramid-free: two layers.)"""
+    import os
+
+    golden = os.path.join(os.path.dirname(__file__), "golden", "layers.txt")
+    layers = int(next(ln.split()[1] for ln in open(golden) if ln.startswith("layers_per_band")))
+    buf = (ctypes.c_int * 64)()
+    succ = {}
+    for S in range(8):
+        n = rx.rx_same_succ(B, S, buf, 64)
+        assert 0 <= n <= 26
+        succ[S] = set(buf[:n])
+        for T in succ[S]:
+            assert T & S == S and T != S  # strict superset of inverted axes
+    longest = {}
+    for S in sorted(range(8), key=lambda s: -bin(s).count("1")):
+        longest[S] = 1 + max((longest[T] for T in succ[S]), default=0)
+    assert max(longest.values()) == layers
