@@ -188,8 +188,9 @@ def test_a_band_runs_in_the_papers_four_layers(rx, B):
     """Same-band edges only go from a region type to a strict superset of its
     inverted axes, so a band's regions fall into dependency layers by |S|;
     the longest chain of same-band dependencies has as many regions as the
-XX
-    single level imports nothing, so the chain is pyramid-free: two layers.)"""
+    paper has active layers (tests/golden/layers.txt).  (At base 4 a wedge
+    computes one level and imports nothing, so only the inverted pyramid
+    waits on same-band regions: two layers.)"""
     import os
 
     golden = os.path.join(os.path.dirname(__file__), "golden", "layers.txt")
