@@ -288,9 +288,14 @@ def test_batched_sims_in_one_launch():
 
 
 # ------------------------------------------------------------ diagnostics
-def test_diagnostics_match_oracle(oracle_mod):
+@pytest.mark.parametrize("run_steps", [16, 64])
+def test_diagnostics_match_oracle(oracle_mod, run_steps):
+    """Windings exactly and the three FP64 energy terms to 1e-12 relative,
+    after 16 steps of a matter-era run planned for run_steps: at its end
+    (a = 1) and a quarter of the way in (a = (14/26)^2 = 0.29, where the
+    potential's a^2 and the level it is taken at matter)."""
     n, steps = (32, 24, 16), 16
-    p = params_for(n, 2.0, steps)
+    p = params_for(n, 2.0, run_steps)
     st = inputs.initial_state(n, 4, "gaussian", sigma=0.3)
     g = sp.Grid([p])
     try:
@@ -311,7 +316,9 @@ def test_diagnostics_match_oracle(oracle_mod):
     kin, grad, pot = oracle_mod.energy_parts(op, phi, pi, steps)
     for got, ref in ((d["kinetic"], kin), (d["gradient"], grad), (d["potential"], pot)):
         assert abs(got - ref) <= 1e-12 * abs(ref)
-    assert d["level"] == steps and abs(d["a"] - 1.0) < 1e-15
+    a_ref = oracle_mod.level_coeffs(op, steps)["a"]
+    assert d["level"] == steps and abs(d["a"] - a_ref) <= 1e-15 * a_ref
+    assert (abs(a_ref - 1.0) < 1e-15) == (run_steps == steps)
 
 
 def test_four_string_winding_on_gpu(oracle_mod):

@@ -393,3 +393,70 @@ def test_expanding_era_energy_balance_is_second_order(oracle_mod):
     r1, r2 = res[0][0] / res[1][0], res[1][0] / res[2][0]
     assert 3.2 < r1 < 4.6 and 3.2 < r2 < 4.6, res
     assert all(r < 1e-4 * d for r, d in res), res
+
+
+def _balance_with_energy_parts(o, dt, nu=2.0, lam=2.0, eta=1.0, tau0=10.0, span=4.0, n=12, tau_ref=None):
+    """The expanding-era balance above, with every energy taken from
+    ``energy_parts`` itself: its kinetic term (mean of the two half-step sums
+    of |pi|^2), its gradient term and its potential a_n^2 (lambda/2) sum
+    (|phi|^2 - eta^2)^2 at level n.  The rate of change is written out here
+    from the continuum balance.  Returns (|residual|, |E_end - E_0|, a at the
+    first and last level)."""
+    tau_ref = tau0 + 3 * span if tau_ref is None else tau_ref  # a stays well below 1
+    x = np.arange(n) * 2 * np.pi / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    phi = (0.6 + 0.3 * np.cos(X) + 0.2 * np.sin(Y + Z)) + 1j * (0.4 * np.sin(X) - 0.3 * np.cos(Z))
+    p = o.make_params((n, n, n), lam=lam, eta=eta, nu=nu, dt=dt, tau0=tau0, tau_ref=tau_ref)
+    a0 = o.level_coeffs(p, 0)["a"]
+    lapf = sum(np.roll(phi, 1, ax) + np.roll(phi, -1, ax) for ax in range(3)) - 6 * phi
+    pi = -0.5 * dt * (lapf - a0 * a0 * lam * (np.abs(phi) ** 2 - eta ** 2) * phi)
+    steps = int(round(span / dt))
+    e_first = e_last = None
+    work = 0.0
+    for s in range(steps):
+        phi1, pi1 = o.step(p, phi, pi, s)
+        kin_old, grad, pot = o.energy_parts(p, phi, pi, s)
+        kin_new = o.energy_parts(p, phi, pi1, s)[0]
+        e = 0.5 * (kin_old + kin_new) + grad + pot
+        e_first = e if e_first is None else e_first
+        e_last = e
+        if s < steps - 1:
+            th = tau0 + (s + 0.5) * dt
+            ah = (th / tau_ref) ** nu
+            fb = 0.5 * (phi + phi1)
+            work += dt * (-4 * nu / th * np.sum(np.abs(pi1) ** 2)
+                          + 2 * nu / th * ah * ah * lam / 2 * np.sum((np.abs(fb) ** 2 - eta ** 2) ** 2))
+        phi, pi = phi1, pi1
+    return abs(e_last - e_first - work), abs(e_last - e_first), a0, o.level_coeffs(p, steps - 1)["a"]
+
+
+def test_energy_parts_obey_the_expanding_era_balance(oracle_mod):
+    """``energy_parts`` at a != 1 (nu = 2, a from 0.21 to 0.40 over the run):
+    the energies it returns, level by level, satisfy the continuum balance
+    dE/dtau = -(4 nu/tau) sum |pi|^2 + (2 nu/tau) a^2 (lambda/2) sum (|phi|^2 -
+    eta^2)^2 with a residual that falls as dt^2.  A potential carrying a
+    instead of a^2, a taken one level off, or a kinetic term other than
+    sum |pi|^2 leaves an O(dt) or O(1) residual instead."""
+    res = [_balance_with_energy_parts(oracle_mod, dt) for dt in (0.02, 0.01, 0.005)]
+    assert all(0.2 < r[2] < 0.21 and 0.4 < r[3] < 0.41 for r in res), res
+    r1, r2 = res[0][0] / res[1][0], res[1][0] / res[2][0]
+    assert 3.2 < r1 < 4.6 and 3.2 < r2 < 4.6, res
+    assert all(r[0] < 1e-4 * r[1] for r in res), res
+
+
+def test_energy_parts_of_a_uniform_field_at_a_below_one(oracle_mod):
+    """A uniform field has no gradient energy; its potential scales with a^2
+    at the stored level.  Two levels of one run (a = 0.25 and a = 0.49) give
+    potentials in the ratio (a_1 / a_0)^2 = (tau_1 / tau_0)^4 for nu = 2, a
+    property of the definition that does not retype it: the ratio of two
+    oracle outputs against the ratio of two conformal times."""
+    o = oracle_mod
+    n = (4, 4, 4)
+    p = o.make_params(n, lam=2.0, eta=1.0, nu=2.0, dt=0.25, tau0=10.0, tau_ref=20.0)
+    phi = np.full((4, 4, 4), 0.3 + 0.4j)
+    pi = np.full((4, 4, 4), 0.1 - 0.2j)
+    k0, g0, v0 = o.energy_parts(p, phi, pi, 0)
+    k1, g1, v1 = o.energy_parts(p, phi, pi, 16)  # tau = 14
+    assert g0 == 0.0 and g1 == 0.0
+    assert k0 == k1 == pytest.approx(64 * 0.05, rel=1e-15)
+    assert v1 / v0 == pytest.approx((14.0 / 10.0) ** 4, rel=1e-14)
