@@ -79,6 +79,10 @@ extern "C" {
 /* ---- sp_region_plan: base_B / block_shape chosen by measurement ---- */
 #define SP_AUTOTUNE (-1)
 
+/* ---- sp_params.precision ---- */
+#define SP_FP32_KAHAN 0 /* FP32 state (phi, pi, Kahan carry of phi), FP32 site update with explicit fused
+                           multiply-adds, per-level coefficients computed in FP64 and rounded once */
+
 /* ---- region ordering of sp_region_plan ---- */
 #define SP_ORDER_STATIC 0  /* release order of the dependency DAG */
 #define SP_ORDER_LEARNED 1 /* cost-model priority (results are identical) */
@@ -115,7 +119,7 @@ typedef struct {
     double tau0;         /* conformal time at level 0 (> 0) */
     double tau_ref;      /* time at which a = 1 (> 0); normally tau0 + steps * dt */
     int32_t damp_steps;  /* initial levels with the velocity discarded each step (tau frozen at tau0) */
-    int32_t reserved;    /* must be 0 */
+    int32_t precision;   /* arithmetic of the evolution: SP_FP32_KAHAN (0), the only one built */
 } sp_params;
 
 /* Diagnostics of one simulation at its current level. */
@@ -152,6 +156,9 @@ typedef struct {
 
 /*
  * sp_grid_create -- describe n_sims independent simulations.
+ * Paper Sec. 2.1: a region is evolved from data on its initial surfaces
+ * alone, and the first regions read the initial time slice itself; the
+ * state given here is that slice (level 0) for every simulation.
  *   p         : array of n_sims parameter sets (host memory, copied).
  *   state_dev : NULL, or 2 * n_sims device pointers (phi, pic of sim 0, then
  *               sim 1, ...): phi float2[sites] (8-byte aligned), pic
@@ -174,16 +181,13 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *                SP_AUTOTUNE to time both policies (all 8, 16 where
  *                possible) and keep the faster.  Every n[d] must be a
  *                multiple of B with n[d] / B >= 2.
- *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768, every
- *                worker taking every step of a region; or 193, 321, 385 for
- *                the warp-specialised kernel with 128 + 64, 256 + 64,
- *                256 + 128 compute + data-movement workers, the movement
- *                threads moving level k's surfaces while level k+1 is
- *                computed); one manager warp is added.  0 for the default
- *                of each base (64 for bases 4 and 8, 384 for 16); SP_AUTOTUNE
- *                to time the candidates for the largest base (64, 128, 193
- *                for base 8; 320, 321, 384, 385, 480 for base 16), smaller
- *                bases keeping their default.  A value applies to every base.
+ *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768,
+ *                every worker taking every step of a region); one manager
+ *                warp is added.  0 for the default of each base (64 for
+ *                bases 4 and 8, 384 for 16); SP_AUTOTUNE to time the
+ *                candidates for the largest base (64, 128 for base 8; 320,
+ *                384, 480 for base 16), smaller bases keeping their default.
+ *                A value applies to every base.
  *                The autotuner runs 16-step calls on scratch copies of the
  *                current state (sides above 128 cells are cut to 128 or 120),
  *                on the grid's stream; the state itself is not modified.
@@ -199,6 +203,10 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 
 /*
  * sp_evolve -- advance every simulation by n_steps leapfrog steps.
+ * Paper Sec. 4: a manager holds the pool of regions whose predecessors are
+ * done and hands one to each worker that reports its previous region
+ * finished; here the pool is a device work queue and the workers are the
+ * CTAs of one persistent launch per region base.
  * Whole bands of B/2 steps run as regions in one persistent launch per
  * distinct base (largest base first, each launch sized for its base); a
  * remainder of fewer than B/2 steps runs as whole-grid steps with the same
@@ -218,6 +226,10 @@ int sp_set_option(sp_grid *g, int32_t option, int64_t value);
 
 /*
  * sp_read_surface -- copy out one simulation's state or diagnostics.
+ * Paper Sec. 2.2: the final surfaces that regions write are what later
+ * regions (and the user) read; after a call the inverted pyramids' tops form
+ * the whole field at the current level, which is what SP_SURF_STATE returns.
+ * The string diagnostics follow the paper's Sec. 5 output (string length).
  *   what : SP_SURF_STATE, SP_SURF_DIAG, SP_SURF_TRACE, SP_SURF_WINDING or
  *          SP_SURF_PLAN; dst_bytes must be at least the size of that item.
  *   dst_is_device : nonzero if dst is device memory.
@@ -228,6 +240,8 @@ int sp_read_surface(const sp_grid *g, int32_t sim, int32_t what, void *dst, size
 
 /*
  * sp_write_surface -- load one simulation's state (what = SP_SURF_STATE:
+ * paper Sec. 2.1's initial slice, or a checkpoint: Sec. 7 notes that
+ * surfaces are natural restart points)
  * phi then pic, 24 * sites bytes) from host or device memory, enqueued on the
  * grid's stream; or set its current level (what = SP_SURF_LEVEL, one int64 in
  * host memory), which selects tau, a and the friction of the next steps.
@@ -293,10 +307,14 @@ int sp_model_load(const char *path, void *cuda_stream, sp_model **out);
  * coefficients (128 KiB), in fixed device arrays that every GPU loading the
  * library holds until exit.  The first call on a device looks up those
  * arrays' device addresses (once per device); make it before any stream
- * capture.  All calls share the arrays: calls whose work overlaps on the GPU
+ * capture.  With CUDA's lazy module loading the arrays are created on a
+ * device when this first call loads the library's device code there, so make
+ * that first call early, before the caller's own pools take the device's
+ * memory.  All calls share the arrays: calls whose work overlaps on the GPU
  * (other streams, other threads) race and must be serialised by the caller.
- * Calls no cudaMalloc, cudaFree or allocating library routine.
- * Errors: SP_EINVAL, SP_ESCRATCH (more than SP_NOALLOC_MAX_SITES sites or
+ * Calls no cudaMalloc, cudaFree or allocating library routine, and uses no
+ * host heap: the coefficients travel as kernel arguments.
+ * Errors: SP_EINVAL (also for a side outside [4, 16384]), SP_ESCRATCH (more than SP_NOALLOC_MAX_SITES sites or
  * SP_NOALLOC_MAX_STEPS steps), SP_EUNSTABLE, SP_ECUDA.
  */
 #define SP_NOALLOC_MAX_SITES 262144
@@ -304,7 +322,11 @@ int sp_model_load(const char *path, void *cuda_stream, sp_model **out);
 int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev, int64_t level0, int64_t n_steps,
                      void *cuda_stream);
 
-/* sp_destroy -- free everything the library allocated (not caller state). */
+/* sp_destroy -- free everything the library allocated (not caller state):
+ * plan, mailboxes, work queue, scratch.  Paper Sec. 4: when the pool of
+ * regions is empty the manager retires its workers; this is the host-side end
+ * of that life cycle.  Synchronises the grid's stream first.
+ * Errors: SP_EINVAL (NULL handle). */
 int sp_destroy(sp_grid *g);
 
 /* sp_strerror -- static description of an error code. */

@@ -230,7 +230,7 @@ int check_params(const sp_params &p)
     for (int d = 0; d < 3; ++d)
         if (p.n[d] < 4 || p.n[d] > (1 << 14)) return SP_EINVAL;
     if (!(p.dx > 0) || !(p.dt > 0) || !(p.lambda >= 0) || !(p.eta >= 0) || !(p.nu >= 0)) return SP_EINVAL;
-    if (!(p.tau0 > 0) || !(p.tau_ref > 0) || p.damp_steps < 0 || p.reserved != 0) return SP_EINVAL;
+    if (!(p.tau0 > 0) || !(p.tau_ref > 0) || p.damp_steps < 0 || p.precision != SP_FP32_KAHAN) return SP_EINVAL;
     if (sites_of(p) > (int64_t)1 << 33) return SP_EINVAL;
     return SP_OK;
 }
@@ -605,12 +605,10 @@ int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t 
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
-// Worker counts of the region kernel: 64, 128, 256, 320, 384, 480, 512, 768 (every worker
-// does every step), or an odd value w + 1 for the warp-specialised kernel with
-// w workers (193: 128 compute + 64 movement; 321: 256 + 64; 385: 256 + 128).
+// Worker counts of the region kernel (every worker does every step).
 bool valid_threads(int t)
 {
-    return t == 64 || t == 128 || t == 256 || t == 320 || t == 384 || t == 480 || t == 512 || t == 768 || t == 193 || t == 321 || t == 385;
+    return t == 64 || t == 128 || t == 256 || t == 320 || t == 384 || t == 480 || t == 512 || t == 768;
 }
 
 
@@ -753,9 +751,9 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
         if (block_shape != SP_AUTOTUNE)
             shapes.push_back(block_shape ? block_shape : default_threads(maxB));
         else if (maxB <= 8)
-            shapes = {64, 128, 193};
+            shapes = {64, 128};
         else
-            shapes = {320, 321, 384, 385, 480};
+            shapes = {320, 384, 480};
         for (int nt : shapes) {
             rc = plan_fixed(t, Bs, nt, SP_ORDER_STATIC, nullptr, block_shape == SP_AUTOTUNE);
             if (rc == SP_EINVAL) continue;  // does not fit this device
@@ -1224,7 +1222,7 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
         info.base_B = g->B[sim];
         for (const GroupCfg &c : g->groups)
             if (c.B == g->B[sim]) {
-                info.threads = c.threads;  // an odd value names the warp-specialised kernel
+                info.threads = c.threads;
                 info.ctas_per_sm = c.ctas_per_sm;
                 info.grid = c.grid;
             }

@@ -727,224 +727,6 @@ __global__ void __launch_bounds__(NW + 32, region_min_blocks(NW)) region_kernel(
     }
 }
 
-// ------------------------------------------------------ warp-specialised variant
-// The same persistent scheme with the worker split in two roles that run
-// concurrently (NC compute threads, ND data-movement threads):
-//
-//   compute:  for k = 1..n:  wait "level k-1 ready" -> evolve A(k) -> signal "k done"
-//   movement: load the band base; signal "level 0 ready";
-//             for k = 1..n:  export the final surface of level k-1 and fetch
-//             the sloped initial surface of level k (both while level k is
-//             computed) -> wait "k done" -> signal "level k ready"
-//
-// so the surface traffic of a level overlaps the evolution of the next one.
-// Safety (checked on the host for every region type): the level-k surface
-// lands in the buffer that level k writes, at cells outside A(k); the level-
-// (k-1) exports read cells that level k neither writes nor (for (pi, c))
-// updates; and every movement thread finishes stage k-1 before any starts
-// stage k (they all wait "k-1 done").  Named barriers: 1 all workers, 2
-// "ready" (movement arrives, compute waits), 3 "done" (compute arrives,
-// movement waits), 4 movement threads only.
-constexpr int kBarAll = 1, kBarReady = 2, kBarDone = 3, kBarMove = 4;
-
-template <int NC, int ND>
-__global__ void __launch_bounds__(NC + ND + 32, 1) region_ws_kernel(RegionArgs a, int max_P)
-{
-    constexpr int NW = NC + ND;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_slot[2], s_handoff, s_done;
-    __shared__ SimDev s_sd[2];      // descriptor of the region handed over in each slot
-    __shared__ RegionInfo s_ri[2];  // and the region, decoded
-    __shared__ float2 *s_mb[64];  // consumer code (type | offset bits << 3) -> mailbox base
-    const int tid = threadIdx.x;
-    const int P3 = max_P * max_P * max_P, B3 = (max_P - 2) * (max_P - 2) * (max_P - 2);
-    float2 *phi_buf0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *phi_buf1 = phi_buf0 + P3;
-    float4 *pc_s = reinterpret_cast<float4 *>(phi_buf1 + P3);
-    TablesDev *s_tabs = reinterpret_cast<TablesDev *>(pc_s + B3);
-    LevelCoef *s_coef = reinterpret_cast<LevelCoef *>(s_tabs + a.n_tabs);
-
-    {  // the launch's tables and simulation descriptors, once
-        const int4 *src = reinterpret_cast<const int4 *>(a.tabs);
-        int4 *dst = reinterpret_cast<int4 *>(s_tabs);
-        const int nt = a.n_tabs * (int)(sizeof(TablesDev) / 16);
-        for (int i = tid; i < nt; i += NW + 32) dst[i] = src[i];
-        if (tid == 0) {
-            s_handoff = 0;
-            s_done = 0;
-        }
-    }
-    __syncthreads();
-    unsigned short *s_imp = reinterpret_cast<unsigned short *>(s_coef + kMaxHDev);
-    for (int t = 0; t < a.n_tabs; ++t) {  // every import list of the launch, once
-        const int4 *src = reinterpret_cast<const int4 *>(s_tabs[t].imp);
-        int4 *dst = reinterpret_cast<int4 *>(s_imp + s_tabs[t].imp_smem);
-        for (int i = tid; i < s_tabs[t].imp_n / 8; i += NW + 32) dst[i] = src[i];
-    }
-    __syncthreads();
-    if (tid < 32) {
-        manager_loop(a, s_tabs, s_slot, s_sd, s_ri, &s_handoff, &s_done, false);
-        return;
-    }
-    const int wt = tid - 32;            // worker index
-    const bool mover = wt >= NC;        // data-movement role
-    const int dt = wt - NC;             // movement-thread index
-    __shared__ int s_abort;
-    for (int seq = 1;; ++seq) {
-        if (wt == 0) {
-            // bounded wait for the manager's handoff (a shared-memory poll: the
-            // handoff normally follows within a microsecond)
-            s_abort = 0;
-            const unsigned long long t0 = globaltimer_ns(), limit = 8 * a.ctl->wait_limit_ns;
-            for (unsigned spin = 0; ld_acquire_cta_shared(&s_handoff) < seq; ++spin) {
-                if ((spin & 15u) == 15u && globaltimer_ns() - t0 > limit) {
-                    atomicCAS(&a.ctl->error, 0, kDevTimeout);
-                    s_abort = 1;
-                    break;
-                }
-            }
-        }
-        named_barrier(kBarAll, NW);
-        if (s_abort) break;
-        const int g = s_slot[seq & 1];
-        if (g < 0) break;
-        if (a.trace && wt == 0) a.trace[2 * (size_t)g] = globaltimer_ns();
-
-        const RegionInfo r = s_ri[seq & 1];  // decoded by the manager at the handoff
-        const SimDev &sd = s_sd[seq & 1];
-        const TablesDev &T = s_tabs[sd.tab_index];
-        const TypeMeta &M = T.type[r.S];
-        const int S = r.S, band = r.band;
-        const int B = sd.B, H = sd.H, P = sd.P, PP = P * P;
-        const int nlev = M.levels;
-        int gbase[3];  // global coordinate of local u = 0 along each axis
-        for (int d = 0; d < 3; ++d) gbase[d] = (band & 1) * H + r.j[d] * B - (((S >> d) & 1) ? H + 1 : 1);
-        const int nx = sd.n[0], ny = sd.n[1], nz = sd.n[2];
-        const long long nxy = (long long)nx * ny;
-
-        if (mover) {
-            const long long slot = (long long)(band & 1) * sd.mb_slot;
-            for (int c = dt; c < 64; c += ND) {
-                // mailbox of the consumer with this code, if the code names one
-                const int Sc = c & 7, eb = c >> 3;
-                int jc = 0, mul = 1;
-                for (int d = 0; d < 3; ++d) {
-                    int v = r.j[d] + ((eb >> d) & 1);
-                    v -= (v >= sd.J[d]) ? sd.J[d] : 0;
-                    jc += v * mul;
-                    mul *= sd.J[d];
-                }
-                s_mb[c] = sd.mbox + slot + sd.mb_type_off[Sc] + (long long)jc * T.type[Sc].mb_size;
-            }
-            // ---- band base (tops of the previous band) + coefficients ----
-            if (dt < H) cp_async16(s_coef + dt, sd.coef + band * H + dt);
-            {
-                const Box3 bp = M.base_phi;
-                const Box3 bc = M.base_pc;
-                const int w0 = bp.hi[0] - bp.lo[0];
-                const int cnt = w0 * (bp.hi[1] - bp.lo[1]);
-                for (int i = dt; i < cnt; i += ND) {
-                    const int t1 = fdiv(i, M.rcp_base[0]);
-                    const int ux = bp.lo[0] + i - t1 * w0;
-                    const int uy = bp.lo[1] + t1;
-                    const int oxy = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]);
-                    if (oxy > 1) continue;  // not a 7-point neighbour of A(1)
-                    const long long gxy =
-                        (long long)wrap_axis(gbase[0] + ux, nx) + (long long)nx * wrap_axis(gbase[1] + uy, ny);
-                    for (int uz = bp.lo[2]; uz < bp.hi[2]; ++uz) {
-                        const int out = oxy + (uz < bc.lo[2] || uz >= bc.hi[2]);
-                        if (out > 1) continue;
-                        const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
-                        cp_async8(phi_buf0 + (uz * P + uy) * P + ux, sd.phi + gi);
-                        if (out == 0) cp_async16(pc_s + pc_slot_of(ux, uy, uz, B), sd.pc + gi);
-                    }
-                }
-            }
-            cp_async_commit();
-            cp_async_wait_all();
-            named_barrier(kBarMove, ND);  // s_mb complete for every movement thread
-            named_arrive(kBarReady, NW);  // level 0 ready
-            const float2 *mb_self = sd.mbox + slot + sd.mb_type_off[S] + (long long)r.jl * M.mb_size;
-            const unsigned short *s_imp_t = s_imp + T.imp_smem;
-            int2 pre[kExportPrefetch];
-            for (int k = 1; k <= nlev; ++k) {
-                if (k >= 2) {  // final surface of level k-1
-                    const int ne = M.exp_n[k - 1];
-                    const int2 *el = T.exp + M.exp_off[k - 1];
-                    prefetch_entries<ND>(el, ne, pre, dt);
-                    if (ne > 0) export_entries<ND>(el, ne, pre, s_mb, (k & 1) ? phi_buf0 : phi_buf1, pc_s, dt);
-                }
-                if (k < nlev && k <= H - 1) {  // sloped initial surface of level k
-                    const int nf = M.imp_full_n[k], np = M.imp_phi_n[k];
-                    if (nf + np > 0)
-                        import_level<ND>(mb_self + M.mb_level_off[k], nf, np, s_imp_t + M.imp_full_off[k],
-                                         s_imp_t + M.imp_phi_off[k], (k & 1) ? phi_buf1 : phi_buf0, pc_s, B, P, dt);
-                    cp_async_commit();
-                    cp_async_wait_all();
-                }
-                named_barrier(kBarDone, NW);                // level k computed
-                if (k < nlev) named_arrive(kBarReady, NW);  // level k ready for level k + 1
-            }
-        } else {
-            const PhysConst q = sd.q;
-            for (int k = 1; k <= nlev; ++k) {
-                named_barrier(kBarReady, NW);
-                const float2 *__restrict__ prev_buf = (k & 1) ? phi_buf0 : phi_buf1;
-                float2 *__restrict__ cur = (k & 1) ? phi_buf1 : phi_buf0;
-                const LevelCoef co = s_coef[k - 1];
-                const Box3 A = M.active[k];
-                const float rc = M.rcp_active[k][0], ra = M.rcp_active[k][1];
-                const int w0 = A.hi[0] - A.lo[0], w2 = A.hi[2] - A.lo[2];
-                const int cnt = w0 * (A.hi[1] - A.lo[1]) * w2;
-                const int a = w0 >> 1, cz = w2 >> 1;  // 2x2x2 blocks along x and z
-                int i = wt;
-                for (; i + NC < cnt; i += 2 * NC) {
-                    evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
-                    evolve_cell(i + NC, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
-                }
-                if (i < cnt) evolve_cell(i, A, a, cz, rc, ra, P, PP, B, prev_buf, cur, pc_s, co, q);
-                named_arrive(kBarDone, NW);
-            }
-        }
-        named_barrier(kBarAll, NW);  // every level computed, every earlier surface exported
-        const float2 *last = (nlev & 1) ? phi_buf1 : phi_buf0;
-        if (nlev <= H - 1) {
-            // ---- final surface of the last level, by all workers ----
-            const int ne = M.exp_n[nlev];
-            const int2 *el = T.exp + M.exp_off[nlev];
-            for (int base = wt; base < ne; base += kExportBatch * NW) {
-                int2 e[kExportBatch];
-#pragma unroll
-                for (int u = 0; u < kExportBatch; ++u)
-                    if (base + u * NW < ne) e[u] = __ldg(el + base + u * NW);
-#pragma unroll
-                for (int u = 0; u < kExportBatch; ++u)
-                    if (base + u * NW < ne) export_one(e[u], s_mb, last, pc_s);
-            }
-        } else {
-            // ---- tops of the inverted pyramid: the next band's base ----
-            const float rB = T.type[0].rcp_base[0];  // the pyramid's base box is B wide: 1/B
-            for (int i = wt; i < B * B; i += NW) {
-                const int t1 = fdiv(i, rB);
-                const int ux = 1 + i - t1 * B;
-                const int uy = 1 + t1;
-                const long long gxy =
-                    (long long)wrap_axis(gbase[0] + ux, nx) + (long long)nx * wrap_axis(gbase[1] + uy, ny);
-                for (int uz = 1; uz <= B; ++uz) {
-                    const long long gi = gxy + nxy * wrap_axis(gbase[2] + uz, nz);
-                    __stcg(sd.phi + gi, last[(uz * P + uy) * P + ux]);
-                    __stcg(sd.pc + gi, pc_s[pc_slot_of(ux, uy, uz, B)]);
-                }
-            }
-        }
-        named_barrier(kBarAll, NW);
-        if (wt == 0) {
-            if (a.trace) a.trace[2 * (size_t)g + 1] = globaltimer_ns();
-            st_release_cta_shared(&s_done, seq);
-        }
-    }
-}
-
 // ------------------------------------------------------------ sweep kernel
 // One level of the whole grid: block 32 x 8 over (x, y), each thread marches
 // a chunk of z keeping phi(z-1), phi(z), phi(z+1) in registers; x and y
@@ -1184,16 +966,6 @@ cudaError_t launch_reset(const RegionArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int NC, int ND>
-static cudaError_t region_ws_launch_t(const RegionArgs &a, int max_B, size_t smem, int grid, cudaStream_t st)
-{
-    cudaError_t e =
-        cudaFuncSetAttribute(region_ws_kernel<NC, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    region_ws_kernel<NC, ND><<<grid, NC + ND + 32, smem, st>>>(a, max_B + 2);
-    return cudaGetLastError();
-}
-
 template <int NW, int BB>
 static cudaError_t region_launch_t(const RegionArgs &a, int B, size_t smem, int grid, cudaStream_t st)
 {
@@ -1252,15 +1024,9 @@ size_t region_smem_bytes(int max_B, int n_tabs, int n_sims, int imp_units)
 // threads = worker threads per CTA (the manager warp comes on top)
 cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e;
 #define SP_OCC(NW)                                                                                               \
     case NW:                                                                                                     \
         return region_occupancy_nw<NW>(B, smem, blocks_per_sm);
-#define SP_OCC_WS(NC, ND)                                                                                        \
-    case NC + ND + 1:                                                                                            \
-        e = cudaFuncSetAttribute(region_ws_kernel<NC, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                                          \
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, region_ws_kernel<NC, ND>, NC + ND + 32, smem);
     switch (threads) {
         SP_OCC(64)
         SP_OCC(128)
@@ -1270,14 +1036,10 @@ cudaError_t region_occupancy(int threads, int B, size_t smem, int *blocks_per_sm
         SP_OCC(480)
         SP_OCC(512)
         SP_OCC(768)
-        SP_OCC_WS(128, 64)
-        SP_OCC_WS(256, 64)
-        SP_OCC_WS(256, 128)
     default:
         return cudaErrorInvalidValue;
     }
 #undef SP_OCC
-#undef SP_OCC_WS
 }
 
 cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t smem, int grid, cudaStream_t st)
@@ -1299,12 +1061,6 @@ cudaError_t launch_region(const RegionArgs &a, int threads, int max_B, size_t sm
         return region_launch_nw<512>(a, max_B, smem, grid, st);
     case 768:
         return region_launch_nw<768>(a, max_B, smem, grid, st);
-    case 128 + 64 + 1:
-        return region_ws_launch_t<128, 64>(a, max_B, smem, grid, st);
-    case 256 + 64 + 1:
-        return region_ws_launch_t<256, 64>(a, max_B, smem, grid, st);
-    case 256 + 128 + 1:
-        return region_ws_launch_t<256, 128>(a, max_B, smem, grid, st);
     default:
         return cudaErrorInvalidValue;
     }

@@ -11,12 +11,15 @@
 // only scratch it needs lives in this file: a phi ping-pong buffer and the
 // per-level coefficients, both in file-scope device arrays of fixed size.
 // Every GPU that loads the library holds these arrays until the process exits.
+// The host side uses no heap either: the coefficients are computed in
+// fixed-size chunks on the stack and reach the device as kernel arguments of
+// a small fill kernel, so no host buffer has to outlive the call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
-#include <vector>
 
 #include "sp.h"
 #include "sp_device.cuh"
@@ -32,6 +35,19 @@ constexpr int kMaxDevices = 64;
 // addresses: the device addresses come from cudaGetSymbolAddress below.
 static __device__ __align__(256) float2 g_phi_scratch[kMaxSites];
 static __device__ __align__(256) sp::LevelCoef g_coef_scratch[kMaxSteps];
+
+// Coefficients handed to the device by value, kCoefChunk levels per launch
+// (3.8 KB of kernel arguments, under the 4 KB that every launch accepts).
+constexpr int kCoefChunk = 240;
+struct CoefChunk {
+    sp::LevelCoef c[kCoefChunk];
+};
+
+__global__ void fill_coef_kernel(CoefChunk chunk, int first, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) g_coef_scratch[first + i] = chunk.c[i];
+}
 
 struct ScratchAddr {
     float2 *phi = nullptr;
@@ -90,19 +106,20 @@ extern "C" int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev
 {
     if (!p || !phi_dev || !pic_dev || level0 < 0 || n_steps < 0) return SP_EINVAL;
     if (((uintptr_t)phi_dev & 7u) || ((uintptr_t)pic_dev & 15u)) return SP_EINVAL;
+    // each side bounded before the product is formed (no overflow), as in
+    // sp_grid_create
     for (int d = 0; d < 3; ++d)
-        if (p->n[d] < 4) return SP_EINVAL;
+        if (p->n[d] < 4 || p->n[d] > (1 << 14)) return SP_EINVAL;
     if (!(p->dx > 0) || !(p->dt > 0) || !(p->lambda >= 0) || !(p->eta >= 0) || !(p->nu >= 0) || !(p->tau0 > 0) ||
-        !(p->tau_ref > 0) || p->damp_steps < 0 || p->reserved != 0)
+        !(p->tau_ref > 0) || p->damp_steps < 0 || p->precision != SP_FP32_KAHAN)
         return SP_EINVAL;
     const int64_t sites = (int64_t)p->n[0] * p->n[1] * p->n[2];
     if (sites > kMaxSites || n_steps > kMaxSteps) return SP_ESCRATCH;
     if (n_steps == 0) return SP_OK;
 
-    std::vector<sp::LevelCoef> coef((size_t)n_steps);
-    for (int64_t k = 0; k < n_steps; ++k) {
+    for (int64_t k = 0; k < n_steps; ++k) {  // every level stable before any work is enqueued
         double stiff = 0.0;
-        coef[(size_t)k] = level_coef(*p, level0 + k, &stiff);
+        level_coef(*p, level0 + k, &stiff);
         if (!(stiff < 4.0)) return SP_EUNSTABLE;
     }
     ScratchAddr s;
@@ -110,8 +127,16 @@ extern "C" int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev
     if (rc != SP_OK) return rc;
 
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    cudaError_t e =
-        cudaMemcpyAsync(s.coef, coef.data(), coef.size() * sizeof(sp::LevelCoef), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
+    for (int64_t first = 0; first < n_steps && e == cudaSuccess; first += kCoefChunk) {
+        const int count = (int)std::min<int64_t>(kCoefChunk, n_steps - first);
+        CoefChunk chunk;
+        double stiff = 0.0;
+        for (int i = 0; i < kCoefChunk; ++i)
+            chunk.c[i] = i < count ? level_coef(*p, level0 + first + i, &stiff) : sp::LevelCoef{0.0f, 0.0f, 0.0f, 0.0f};
+        fill_coef_kernel<<<(count + 127) / 128, 128, 0, st>>>(chunk, (int)first, count);
+        e = cudaGetLastError();
+    }
     sp::PhysConst q;
     q.dt = (float)p->dt;
     q.inv_dx2 = (float)(1.0 / (p->dx * p->dx));

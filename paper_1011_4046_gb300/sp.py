@@ -58,6 +58,7 @@ SP_MODEL_PARAMS = 5313
 SP_AUTOTUNE = -1
 SP_ORDER_STATIC = 0
 SP_ORDER_LEARNED = 1
+SP_FP32_KAHAN = 0
 
 
 class sp_params(ctypes.Structure):
@@ -71,7 +72,7 @@ class sp_params(ctypes.Structure):
         ("tau0", ctypes.c_double),
         ("tau_ref", ctypes.c_double),
         ("damp_steps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
     ]
 
 
@@ -232,7 +233,7 @@ def make_params(n, dx=1.0, dt=0.25, lam=2.0, eta=1.0, nu=0.0, tau0=1.0, tau_ref=
     p = sp_params()
     p.n[0], p.n[1], p.n[2] = (int(v) for v in n)
     p.dx, p.dt, p.lam, p.eta, p.nu = float(dx), float(dt), float(lam), float(eta), float(nu)
-    p.tau0, p.tau_ref, p.damp_steps, p.reserved = float(tau0), float(tau_ref), int(damp_steps), 0
+    p.tau0, p.tau_ref, p.damp_steps, p.precision = float(tau0), float(tau_ref), int(damp_steps), SP_FP32_KAHAN
     return p
 
 

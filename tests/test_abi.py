@@ -39,7 +39,7 @@ def test_create_validates_before_any_cuda_call(lib):
     rc, h = sp.sp_grid_create([], None, 0)
     assert rc == sp.SP_EINVAL
     p = sp.make_params(16)
-    p.reserved = 1
+    p.precision = 1  # only SP_FP32_KAHAN is built
     rc, h = sp.sp_grid_create([p], None, 0)
     assert rc == sp.SP_EINVAL
 
@@ -113,7 +113,28 @@ def test_header_constants_match_the_binding():
     for name in ("SP_AUTOTUNE", "SP_FEATURES", "SP_SURF_FEATURES", "SP_SURF_LEVEL", "SP_OPT_WAIT_LIMIT_NS",
                  "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_OPT_MAILBOX_SLOTS", "SP_MODEL_PARAMS",
                  "SP_MODEL_FEATURES",
-                 "SP_ORDER_STATIC", "SP_ORDER_LEARNED", "SP_TIMING", "SP_TRACE"):
+                 "SP_ORDER_STATIC", "SP_ORDER_LEARNED", "SP_TIMING", "SP_TRACE", "SP_FP32_KAHAN",
+                 "SP_NOALLOC_MAX_SITES", "SP_NOALLOC_MAX_STEPS"):
         m = re.search(r"#define\s+" + name + r"\s+\(?(-?\d+)u?\)?", text)
         assert m, name
         assert int(m.group(1)) == getattr(sp, name), name
+
+
+def test_noalloc_rejects_bad_sizes_before_any_cuda_call(lib):
+    """sp_sweep_noalloc bounds every side before it forms the site count: a
+    grid whose product would wrap a 64-bit integer (2^30 x 2^18 x 2^16) is
+    rejected, as are sides below 4 and a non-zero precision; sizes beyond its
+    fixed scratch give SP_ESCRATCH.  All return before any CUDA call (no GPU
+    here); the pointers are never dereferenced."""
+    fake = 1 << 20  # 16-byte aligned stand-ins
+    for n in ((1 << 30, 1 << 18, 1 << 16), (1 << 15, 8, 8), (2, 16, 16)):
+        p = sp.make_params(n, nu=0.0)
+        assert sp.sp_sweep_noalloc(p, fake, fake, 0, 4, 0) == sp.SP_EINVAL, n
+    p = sp.make_params(16, nu=0.0)
+    p.precision = 1
+    assert sp.sp_sweep_noalloc(p, fake, fake, 0, 4, 0) == sp.SP_EINVAL
+    p = sp.make_params((16384, 16384, 4), nu=0.0)  # sides in range, too many sites
+    assert sp.sp_sweep_noalloc(p, fake, fake, 0, 4, 0) == sp.SP_ESCRATCH
+    p = sp.make_params(16, nu=0.0)
+    assert sp.sp_sweep_noalloc(p, fake, fake, 0, sp.SP_NOALLOC_MAX_STEPS + 1, 0) == sp.SP_ESCRATCH
+    assert sp.sp_sweep_noalloc(p, fake + 4, fake, 0, 4, 0) == sp.SP_EINVAL  # misaligned phi

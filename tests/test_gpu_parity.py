@@ -139,9 +139,9 @@ def test_gpu_matches_fp64_oracle_matter_era_64(oracle_mod):
     ((48, 32, 32), 16, 27, 2.0, 256),   # ragged: 3 bands + 3 remainder steps, 256 threads
     ((24, 24, 24), 8, 3, 0.0, 128),     # fewer steps than a band: all remainder
     ((32, 48, 64), 8, 20, 2.0, 128),    # 128 workers at base 8 (the default is 64)
-    ((32, 48, 64), 8, 20, 2.0, 193),    # warp-specialised kernel, 128 compute + 64 movement threads
-    ((48, 32, 32), 16, 27, 2.0, 321),   # warp-specialised, 256 + 64, ragged
-    ((32, 32, 32), 16, 16, 1.0, 385),   # warp-specialised, 256 + 128
+    ((64, 32, 32), 8, 20, 1.0, 256),    # 256 workers at base 8
+    ((48, 32, 32), 16, 27, 2.0, 320),   # ragged
+    ((32, 32, 32), 16, 16, 1.0, 480),
     ((32, 32, 48), 16, 24, 2.0, 480),   # 480 workers
     ((32, 32, 32), 16, 16, 0.0, 128),   # 128 workers at base 16
 ])
@@ -186,8 +186,8 @@ def test_random_configurations_bit_exact(n, B, steps, nu, threads):
     ((16, 16, 16), 4, 11, 0.0, 0),      # base 4: seven seed types, remainder step
     ((32, 48, 64), 8, 20, 2.0, 0),      # base 8, anisotropic, 5 bands
     ((48, 32, 32), 16, 27, 2.0, 0),     # base 16, ragged
-    ((32, 48, 64), 8, 20, 2.0, 193),    # warp-specialised kernel
-    ((32, 32, 48), 16, 40, 1.0, 321),   # warp-specialised, 5 bands
+    ((32, 48, 64), 8, 20, 2.0, 128),
+    ((32, 32, 48), 16, 40, 1.0, 256),   # 5 bands
 ])
 def test_one_mailbox_slot_bit_exact(n, B, steps, nu, threads):
     """One mailbox slot for every band instead of a ring of two: half the
