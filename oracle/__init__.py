@@ -15,6 +15,9 @@ Functions and the passage each follows:
   exactly that.
 * :func:`run` -- whole-grid FP64 leapfrog, the plain definition that the
   region decomposition (Sec. 1, Sec. 2) must reproduce.
+* :func:`run_fp32_storage` -- the same steps with the state rounded to FP32
+  after each one: how far storage in FP32 alone moves a run (the yardstick
+  for the accuracy bar on chaotic runs).
 * :func:`energy_parts`, :func:`lap_dot` -- energy of a stored state and the
   lattice-Laplacian bilinear form.
 * :func:`winding` -- exact per-plaquette winding numbers (string detection).
@@ -88,6 +91,7 @@ def _load():
             lib.or_level_coeffs.argtypes = [P, ctypes.c_int64, dp]
             lib.or_step.argtypes = [P, ctypes.c_int64, dp, dp, ctypes.c_int]
             lib.or_run.argtypes = [P, ctypes.c_int64, ctypes.c_int64, dp, dp, ctypes.c_int]
+            lib.or_run_fp32_storage.argtypes = [P, ctypes.c_int64, ctypes.c_int64, dp, dp, ctypes.c_int]
             lib.or_energy_parts.argtypes = [P, ctypes.c_int64, dp, dp, dp, ctypes.c_int]
             lib.or_lap_dot.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_double, dp, dp, ctypes.c_int]
             lib.or_lap_dot.restype = ctypes.c_double
@@ -127,6 +131,16 @@ def run(p: Params, phi, pi, level0: int, nsteps: int, nthreads: int = 0):
     v = _as_c128(pi)
     _load().or_run(ctypes.byref(p), int(level0), int(nsteps), _dptr(f.view(np.float64)),
                    _dptr(v.view(np.float64)), int(nthreads))
+    return f, v
+
+
+def run_fp32_storage(p: Params, phi, pi, level0: int, nsteps: int, nthreads: int = 0):
+    """As :func:`run`, with phi and pi rounded to FP32 after every step: the
+    error floor of any scheme that stores the field in FP32."""
+    f = _as_c128(phi)
+    v = _as_c128(pi)
+    _load().or_run_fp32_storage(ctypes.byref(p), int(level0), int(nsteps), _dptr(f.view(np.float64)),
+                                _dptr(v.view(np.float64)), int(nthreads))
     return f, v
 
 

@@ -129,6 +129,25 @@ void or_run(const or_params *p, int64_t level0, int64_t nsteps, double *phi, dou
 }
 
 /*
+ * The FP32-storage twin of or_run: the same FP64 steps, with phi and pi
+ * rounded to FP32 (round to nearest) after every step.  Its distance from
+ * or_run is the error that storing the field in FP32 costs by itself, the
+ * floor of any scheme that keeps its state in FP32.
+ */
+void or_run_fp32_storage(const or_params *p, int64_t level0, int64_t nsteps, double *phi, double *pi, int nthreads)
+{
+    const int64_t n2 = 2 * (int64_t)p->n[0] * p->n[1] * p->n[2];
+    for (int64_t k = 0; k < nsteps; ++k) {
+        or_step(p, level0 + k, phi, pi, nthreads);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n2; ++i) {
+            phi[i] = (double)(float)phi[i];
+            pi[i] = (double)(float)pi[i];
+        }
+    }
+}
+
+/*
  * Energy of a stored state (phi_n, pi) at level n, split in its three terms:
  *   out[0] = sum |pi|^2
  *   out[1] = sum_i sum_x |phi(x + e_i) - phi(x)|^2 / dx^2

@@ -5,7 +5,8 @@ the worker count picked by the library's autotuner.
 Bars: every simulation of the batch is bit-exact against its own monolithic
 GPU sweep (the decomposition, the batching, the graph replay and the tuned
 launch shape change nothing), and the smallest simulations of the full
-64-simulation workload meet the FP64-oracle bar of the single-grid tests.
+64-simulation workload meet the FP64-oracle bars of the single-grid tests
+(accuracy_bars.py).
 """
 import numpy as np
 import pytest
@@ -13,6 +14,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_1011_4046_gb300 import inputs, sp  # noqa: E402
+
+from accuracy_bars import check_run, format_report  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -109,14 +112,13 @@ def test_full_batched_workload(oracle_mod):
     """The batched workload at full size: 64 simulations, N drawn from the
     multiples of 8 in [48, 160], nu in {0, 1, 2}, seeds 0-63, 192 steps each,
     in one autotuned persistent launch replayed from a graph.  All 64 are
-    bit-exact against their monolithic sweeps; the two smallest (48^3 at
-    nu = 1 and nu = 2) are checked against the FP64 oracle.  The radiation-era
-    one is chaotic: there even the FP64 oracle with its state rounded to FP32
-    after every step ends 3.8e-4 from the plain oracle, so the bar is relative
-    to that FP32-storage floor: max error within 8x max(floor, 1e-5 eta), RMS
-    error within 8x max(floor RMS, 1e-6 eta).  (The FP32 Kahan arithmetic
-    ends 7.1x the floor in max and 6.6x in RMS there, deterministically; the
-    matter-era one ends at 5.2e-6, inside 1e-5 eta.)"""
+    bit-exact against their monolithic sweeps.  The two smallest (48^3 at
+    nu = 1 and nu = 2) meet the FP64-oracle bars: 1e-5 eta on every 32-step
+    segment restarted from the GPU's own state, and globally while the
+    FP32-storage floor stays within a tenth of that (the radiation-era one is
+    chaotic: even FP64 with FP32 storage ends 3.8e-4 from FP64 there).  Their
+    region runs are repeated here in 32-step calls, which the bit-exactness
+    tests show changes nothing."""
     specs = batch_specs(64, STEPS)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
@@ -126,20 +128,22 @@ def test_full_batched_workload(oracle_mod):
     for i in range(len(specs)):
         assert_bit_equal(got[i], mono[i], f"sim {i}: ")
         assert np.all(np.isfinite(got[i][0]))
-    order = sorted(range(len(specs)), key=lambda i: specs[i][0].n[0])
+    order = sorted(range(len(specs)), key=lambda i: (specs[i][0].n[0], specs[i][0].nu))
     for i in order[:2]:
         p, st = specs[i]
+        g = sp.Grid([p])
+        cps = {}
+        try:
+            g.write_state(0, *st)
+            g.plan(base_B=infos[i]["base_B"])
+            for lvl in range(32, STEPS + 1, 32):
+                g.evolve(32)
+                cps[lvl] = g.read_state(0)
+        finally:
+            g.close()
+        assert_bit_equal(cps[STEPS], got[i], f"sim {i} in 32-step calls: ")
         op = oracle_mod.make_params(p.n[0], dt=p.dt, lam=p.lam, eta=p.eta, nu=p.nu, tau0=p.tau0,
                                     tau_ref=p.tau_ref)
-        f, v = st[0].astype(np.complex128), st[1].astype(np.complex128)
-        g, w = f.copy(), v.copy()
-        for n in range(STEPS):  # plain FP64, and FP64 with the state rounded to FP32 each step
-            f, v = oracle_mod.run(op, f, v, n, 1)
-            g, w = oracle_mod.run(op, g, w, n, 1)
-            g, w = (x.astype(np.complex64).astype(np.complex128) for x in (g, w))
-        fl = np.abs(g - f)
-        floor, floor_rms = float(fl.max()), float(np.sqrt(np.mean(fl ** 2)))
-        d = np.abs(got[i][0].astype(np.complex128) - f)
-        err, rms = float(d.max()), float(np.sqrt(np.mean(d ** 2)))
-        assert rms <= 8.0 * max(floor_rms, 1e-6 * p.eta), f"sim {i}: rms {rms:.3e} (floor rms {floor_rms:.3e})"
-        assert err <= 8.0 * max(floor, 1e-5 * p.eta), f"sim {i}: max {err:.3e} (floor {floor:.3e})"
+        rep = check_run(oracle_mod, op, st, cps, p.eta)
+        assert rep["asserted_global"], f"sim {i}: the global bar was asserted nowhere"
+        print("\n" + format_report(f"batched sim {i} ({p.n[0]}^3, nu = {p.nu:g})", rep))

@@ -460,3 +460,23 @@ def test_energy_parts_of_a_uniform_field_at_a_below_one(oracle_mod):
     assert g0 == 0.0 and g1 == 0.0
     assert k0 == k1 == pytest.approx(64 * 0.05, rel=1e-15)
     assert v1 / v0 == pytest.approx((14.0 / 10.0) ** 4, rel=1e-14)
+
+
+def test_fp32_storage_twin_rounds_after_every_step(oracle_mod):
+    """run_fp32_storage is the plain FP64 step followed by rounding phi and pi
+    to FP32, repeated: it equals that composition written out with numpy's
+    own float32 rounding, bit for bit, and every value it returns is an FP32
+    number."""
+    o = oracle_mod
+    n = (8, 6, 10)
+    phi, _, _ = inputs.initial_state(n, seed=21, kind="phase")
+    pi = inputs.gaussian_field(n, seed=22, sigma=0.2)
+    p = o.make_params(n, lam=2.0, nu=2.0, dt=0.25, tau0=10.0, tau_ref=14.0)
+    f, v = o.run_fp32_storage(p, phi, pi, 3, 7)
+    g, w = phi.astype(np.complex128), pi.astype(np.complex128)
+    for k in range(7):
+        g, w = o.run(p, g, w, 3 + k, 1)
+        g, w = g.astype(np.complex64).astype(np.complex128), w.astype(np.complex64).astype(np.complex128)
+    assert np.array_equal(f, g) and np.array_equal(v, w)
+    assert np.array_equal(f.astype(np.complex64).astype(np.complex128), f)
+    assert not np.array_equal(f, o.run(p, phi, pi, 3, 7)[0])  # the rounding does move the run
