@@ -1,23 +1,30 @@
 """Benchmark: lattice site-updates/s of the region-scheduled evolution on one GB300.
 
-Workload (one "step" = one pass of the whole hot path over one batch): the
-128^3 matter-era string field (nu = 2, tau0 = 10, tau_ref = tau0 + 256 dt,
-lambda = 2, eta = 1, dx = 1, dt = 0.25), random-phase initial field from
-seed 0, evolved 256 leapfrog steps in FP32 with the Kahan-compensated drift,
-region base B = 16 (8 steps per band, 32 bands, 131072 regions).  Every step
-starts from the same initial state (restored on the device before the step,
-outside the timed region) and L2 is flushed between steps.
+Workload (the largest single-GPU configuration): the 1280^3 matter-era string
+field (nu = 2, tau0 = 10, tau_ref = tau0 + 2048 dt, lambda = 2, eta = 1,
+dx = 1, dt = 0.25), random-phase initial field from seed 0, 2048 leapfrog
+steps in FP32 with the Kahan-compensated drift, one mailbox slot.  One bench
+"step" is one pass of the whole hot path over a slice of that run: one
+sp_evolve call of 64 leapfrog steps (whole bands of regions: queue reset,
+persistent region kernel), continuing from where the previous step stopped;
+when a pass reaches level 2048 the initial field is restored (outside the
+timed region) and the run starts over.  Every band of the run has the same
+regions, so the rate over any slice is the rate of the whole run.  The
+state (50 GB) and mailboxes are far larger than L2, so no flush is needed.
 
 Printed (rank 0, one JSON line): value = site-updates/s from CUDA events on
 the library's stream around each sp_evolve call; the monolithic GPU sweep on
-the same inputs; roofline of the region kernel (algorithmic bytes per
-site-update x updates / kernel time from events around that kernel, against
-the measured HBM copy bandwidth); e2e through the C ABI with host buffers;
-the FP64 CPU oracle timed on the host cores (bounded sample); SM clocks
-sampled with nvidia-smi during the timed region.
+the same field (its own grid, after the region grid is freed); the roofline
+of the region kernel (algorithmic bytes per site-update x updates / kernel
+time from events around that kernel, against the measured HBM copy
+bandwidth); e2e through the C ABI with the state in host memory (copied in
+and out inside the timed region); the FP64 CPU oracle timed on the host cores
+on a bounded sample; SM clocks sampled with nvidia-smi during the timed
+region; and, as an extra key, the 128^3 x 256 L2-resident workload.
 
---impl reference times the FP64 CPU oracle on the same workload instead
-(bounded sample per step), as the reference arm.
+--impl reference times the FP64 CPU oracle on the same workload's bounded
+sample instead, as the reference arm.  --workload batched runs the
+64-simulation batch.
 
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the method needs no collective), value = all ranks' updates / max time.
@@ -25,6 +32,7 @@ Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import os
 import statistics
@@ -37,13 +45,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N, STEPS, B = 128, 256, 16  # the benchmark workload (options below resize it for profiling only)
 NU, TAU0, LAM, ETA, DX, DT = 2.0, 10.0, 2.0, 1.0, 1.0, 0.25
 SEED = 0
-# Algorithmic HBM bytes per site-update of the region path at B = 16: band-top
-# state plus sloped faces, counted by brute force over one steady-state band
-# (13.8 read + 11.4 written, each face cell written once, read by every
-# consumer).
+# The workloads: grid side, leapfrog steps of the whole run, steps per bench
+# step (one sp_evolve call), region base.
+BIG = dict(N=1280, STEPS=2048, PER_STEP=64, B=16)
+SMALL = dict(N=128, STEPS=256, PER_STEP=256, B=16)
+# Sample of the big workload that the FP64 oracle times on the host cores: the
+# first SAMPLE_Z planes of its initial field as a periodic slab.
+SAMPLE_Z = 32
+# Algorithmic HBM bytes per site-update of the region path, by region base:
+# band-top state plus sloped faces, counted by brute force over one
+# steady-state band (each face cell written once, read by every consumer).
 ALG_BYTES_PER_UPDATE = {8: 42.8, 16: 25.3, 32: 13.8}
 MONO_BYTES_PER_UPDATE = 48.0
 # On-chip (shared-memory) bytes per site-update of the region kernel: seven
@@ -51,9 +64,13 @@ MONO_BYTES_PER_UPDATE = 48.0
 SMEM_BYTES_PER_UPDATE = 7 * 8 + 8 + 2 * 16
 # Shared-memory bandwidth of one GB300, nominal: 128 B per clock per SM.
 SMS, SMEM_BYTES_PER_CLOCK = 152, 128
-WORKLOAD = (f"{N}^3 matter era (nu=2, tau0=10, tau_ref=74), lambda=2, eta=1, dx=1, dt=0.25, random-phase "
-            f"init seed 0, {STEPS} leapfrog steps, region base B={B}")
 METRIC = "lattice site-updates/s"
+
+
+def workload_name(w):
+    n, steps = w["N"], w["STEPS"]
+    return (f"{n}^3 matter era (nu=2, tau0=10, tau_ref={TAU0 + steps * DT:g}), lambda=2, eta=1, dx=1, dt=0.25, "
+            f"random-phase init seed 0, {steps} leapfrog steps, region base B={w['B']}")
 
 
 def peaks():
@@ -72,10 +89,12 @@ KERNEL_SOURCES = ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_g
                   "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h"]
 
 
-def ncu_traffic(workload_is_default):
-    """DRAM bytes per region-kernel launch from the committed ncu record, or
-    None when the kernel sources changed since it was taken (or the workload
-    differs from the one it was taken on)."""
+def ncu_traffic(base, updates_per_launch):
+    """DRAM bytes (read + written) per region-kernel launch, from the committed
+    ncu record: its bytes per site-update, measured on a smaller grid of the
+    same kernel and base whose state and mailboxes are far larger than L2,
+    times the site-updates of this launch.  None when the kernel sources
+    changed since the record was taken or the base differs."""
     import hashlib
 
     try:
@@ -85,9 +104,10 @@ def ncu_traffic(workload_is_default):
         for s in KERNEL_SOURCES:
             with open(os.path.join(ROOT, s), "rb") as f:
                 h.update(f.read())
-        if not workload_is_default or h.hexdigest()[:16] != rec["kernel_sources_sha256_16"]:
+        if h.hexdigest()[:16] != rec["kernel_sources_sha256_16"] or int(rec["region_base"]) != int(base):
             return None
-        return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+        per_update = (rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]) / rec["site_updates"]
+        return per_update * updates_per_launch
     except Exception:
         return None
 
@@ -118,7 +138,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -132,24 +152,29 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return parse_clocks(open(self.path).read().splitlines())
+
+
+def parse_clocks(lines):
+    """Median SM clock, maximum clock and the throttle reasons seen, from
+    nvidia-smi csv lines (the FIELDS order, no header, no units)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
 def smem_roofline(updates, kernel_ms, clk):
@@ -194,20 +219,45 @@ def whole_job_rate(local_ms, units_per_rank, ws, device=None):
     return ws * units_per_rank / (t / 1e3), t
 
 
-def flush_l2(buf):
-    buf.zero_()
+def pass_schedule(n_calls, per_step, run_steps):
+    """Start level of each of n_calls consecutive bench steps of per_step
+    leapfrog steps over a run of run_steps: the run continues from call to
+    call and starts over at level 0 when a pass is complete (a restore)."""
+    out, lvl = [], 0
+    for _ in range(n_calls):
+        if lvl + per_step > run_steps:
+            lvl = 0
+        out.append(lvl)
+        lvl += per_step
+    return out
 
 
-def run_ours(args):
+def host_available_bytes():
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        return 0
+
+
+def fill_random_phase(phi, n, seed, slab=16):
+    """The random-phase field into the device tensor phi (nz, ny, nx), made on
+    the host slab by slab (the same values as the whole-field generator)."""
     import torch
 
-    global N, STEPS, WORKLOAD
-    if args.grid != N or args.leapfrog_steps != STEPS:
-        WORKLOAD = WORKLOAD.replace(f"{N}^3", f"{args.grid}^3").replace(f"{STEPS} leapfrog", f"{args.leapfrog_steps} leapfrog")
-        WORKLOAD = WORKLOAD.replace("tau_ref=74", f"tau_ref={TAU0 + args.leapfrog_steps * DT:g}")
-        N, STEPS = args.grid, args.leapfrog_steps
+    from paper_1011_4046_gb300 import inputs
 
-    from paper_1011_4046_gb300 import inputs, sp
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as pool:
+        jobs = {pool.submit(inputs.random_phase_slab, n, seed, z, min(z + slab, n[2])): z
+                for z in range(0, n[2], slab)}
+        for fut in cf.as_completed(jobs):
+            z = jobs[fut]
+            s = torch.from_numpy(fut.result())
+            phi[z:z + s.shape[0]].copy_(s, non_blocking=False)
+
+
+def setup_dist():
+    import torch
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -217,8 +267,18 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def run_grid(args, w, extra=None):
+    """The region path, the sweep and e2e on one grid workload ``w``."""
+    import torch
+
+    from paper_1011_4046_gb300 import sp
+
+    ws, rank, local = dist_env()
     dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.Stream(device=dev)  # a capturable stream (the sweep is replayed as a CUDA graph)
+    stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
 
     def barrier():
@@ -226,97 +286,139 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    N, STEPS, PER, B = w["N"], w["STEPS"], w["PER_STEP"], w["B"]
+    n = (N, N, N)
+    sites = N ** 3
     p = sp.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
-    phi0, pi0, c0 = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
-    host_init = sp.pack_state(phi0, pi0, c0)                    # library state layout, 24 B/site
-    init_dev = torch.from_numpy(host_init).to(dev)              # resident copy to restore from
-    g = sp.Grid([p], stream=stream)
-    g.plan(base_B=args.base, threads=args.threads)
+    shape = (N, N, N)
+    phi = torch.empty(shape, dtype=torch.complex64, device=dev)
+    pic = torch.zeros(shape + (2,), dtype=torch.complex64, device=dev)
+    t0 = time.perf_counter()
+    fill_random_phase(phi, n, SEED)
+    phi0 = phi.clone()  # pi = c = 0 at the start: phi alone restores the initial state
+    init_s = time.perf_counter() - t0
+    updates = sites * PER
+
+    def restore(g):
+        phi.copy_(phi0)
+        pic.zero_()
+        g.set_level(0, 0)
+
+    g = sp.Grid([p], states=[(phi, pic)], stream=stream)
+    g.plan(base_B=B if args.base == 0 else args.base, threads=args.threads)
     info = g.plan_info(0)
-    updates = N ** 3 * STEPS
-    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    init_bytes = init_dev.numel() * 8
+    base = info["base_B"]
+    calls = args.warmup + args.steps
+    sched = pass_schedule(calls, PER, STEPS)
 
-    def restore():
-        rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, init_dev.data_ptr(), init_bytes, 1)
-        assert rc == 0, sp.sp_strerror(rc)
-
-    def one_step(flags):
-        restore()
-        flush_l2(l2_flush)
+    def one_step(start_level):
+        if start_level == 0 and g.level(0) != 0:
+            restore(g)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rc = sp.sp_evolve(g.h, STEPS, sp.SP_ASYNC | sp.SP_RESTART | sp.SP_TIMING | flags)
+        rc = sp.sp_evolve(g.h, PER, sp.SP_ASYNC | sp.SP_TIMING)
         e1.record(stream)
         if rc != 0:
             raise sp.SpError(rc, "sp_evolve")
         e1.synchronize()
-        kernel = g.timing()
-        return e0.elapsed_time(e1), kernel
+        return e0.elapsed_time(e1), g.timing()[1]
 
-    # ---- region path ----
-    for _ in range(args.warmup):
-        one_step(0)
+    for lvl in sched[:args.warmup]:
+        one_step(lvl)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     t_wall0 = time.perf_counter()
     step_ms, kern_ms = [], []
-    for _ in range(args.steps):
-        ms, kt = one_step(0)
+    for lvl in sched[args.warmup:]:
+        ms, kt = one_step(lvl)
         step_ms.append(ms)
-        kern_ms.append(kt[1])
+        kern_ms.append(kt)
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     value, total_ms = whole_job_rate(sum(step_ms), updates * args.steps, ws, dev)
-    ms_per_step = total_ms / args.steps
-
-    # correctness guard on the benchmarked result: finite field
-    phi_end = g.read_state(0)[0]
-    finite = bool(np.all(np.isfinite(phi_end)))
+    finite = bool(torch.isfinite(torch.view_as_real(phi)).all().item())
+    end_level = g.level(0)
 
     # the paper's utilisation figures (Sec. 6), from one traced call outside the timed region
-    restore()
-    rc = sp.sp_evolve(g.h, STEPS, sp.SP_RESTART | sp.SP_TRACE)
-    if rc != 0:
-        raise sp.SpError(rc, "sp_evolve (trace)")
-    utilisation = trace_utilisation(g.trace(0, int(info["regions_per_band"] * (STEPS // (info["base_B"] // 2)))),
-                                    info["grid"])
-
-    # ---- monolithic sweep on the same inputs (the comparator) ----
-    for _ in range(max(1, args.warmup // 2)):
-        one_step(sp.SP_MONOLITHIC)
-    mono_ms = [one_step(sp.SP_MONOLITHIC)[0] for _ in range(args.steps)]
-    mono_value = updates * args.steps / (sum(mono_ms) / 1e3)
-
-    # ---- e2e through the C ABI with host buffers ----
-    pinned_in = torch.from_numpy(host_init.view(np.float32).copy()).pin_memory()  # phi | (pi, c)
-    pinned_out = torch.empty_like(pinned_in).pin_memory()
-    nbytes = pinned_in.numel() * 4
-    e2e_ms = []
-    for it in range(args.warmup + args.steps):
-        barrier()
-        t0 = time.perf_counter()
-        rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, pinned_in.data_ptr(), nbytes, 0)
-        rc = rc or sp.sp_evolve(g.h, STEPS, sp.SP_ASYNC | sp.SP_RESTART)
-        rc = rc or sp.sp_read_surface(g.h, 0, sp.SP_SURF_STATE, pinned_out.data_ptr(), nbytes, 0)
-        t1 = time.perf_counter()
+    utilisation = None
+    if not args.no_trace:
+        if end_level + PER > STEPS:
+            restore(g)
+        rc = sp.sp_evolve(g.h, PER, sp.SP_TRACE)
         if rc != 0:
-            raise sp.SpError(rc, "e2e")
-        if it >= args.warmup:
-            e2e_ms.append((t1 - t0) * 1e3)
-    e2e_value = ws * updates * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+            raise sp.SpError(rc, "sp_evolve (trace)")
+        regions = int(info["regions_per_band"] * (PER // (base // 2)))
+        utilisation = trace_utilisation(g.trace(0, regions), info["grid"])
+
+    # ---- e2e through the C ABI: state in host memory, copied in and out every step ----
+    e2e = None
+    if not args.no_e2e:
+        nbytes = 24 * sites
+        if g.level(0) + PER * (args.e2e_steps + 1) > STEPS:
+            restore(g)
+        pinned = host_available_bytes() > 3 * nbytes
+        host = torch.empty(nbytes // 4, dtype=torch.float32, pin_memory=pinned)
+        rc = sp.sp_read_surface(g.h, 0, sp.SP_SURF_STATE, host.data_ptr(), nbytes, 0)
+        if rc != 0:
+            raise sp.SpError(rc, "sp_read_surface")
+        e2e_ms = []
+        for it in range(1 + args.e2e_steps):
+            barrier()
+            t0 = time.perf_counter()
+            rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, host.data_ptr(), nbytes, 0)
+            rc = rc or sp.sp_evolve(g.h, PER, sp.SP_ASYNC)
+            rc = rc or sp.sp_read_surface(g.h, 0, sp.SP_SURF_STATE, host.data_ptr(), nbytes, 0)
+            t1 = time.perf_counter()
+            if rc != 0:
+                raise sp.SpError(rc, "e2e")
+            if it:
+                e2e_ms.append((t1 - t0) * 1e3)
+        del host
+        e2e = {"value": ws * updates * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": "site-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": sum(e2e_ms) / len(e2e_ms), "steps": len(e2e_ms),
+               "host_buffer": "pinned" if pinned else "pageable",
+               "how": "per step: sp_write_surface (host -> device), sp_evolve, sp_read_surface (device -> host), "
+                      "host wall clock"}
     g.close()
 
-    if rank != 0:
-        return None
+    # ---- monolithic sweep on the same field (its own grid, after the mailboxes are freed) ----
+    mono = None
+    if args.mono_steps > 0:
+        restore_level = 0
+        phi.copy_(phi0)
+        pic.zero_()
+        gm = sp.Grid([p], states=[(phi, pic)], stream=stream)
+        try:
+            gm.set_level(0, restore_level)
+            ms = []
+            for it in range(1 + args.mono_steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc = sp.sp_evolve(gm.h, PER, sp.SP_ASYNC | sp.SP_MONOLITHIC)
+                e1.record(stream)
+                if rc != 0:
+                    raise sp.SpError(rc, "sp_evolve (sweep)")
+                e1.synchronize()
+                if it:
+                    ms.append(e0.elapsed_time(e1))
+        finally:
+            gm.close()
+        mv = updates * len(ms) / (sum(ms) / 1e3)
+        mono = {"value": mv, "unit": "site-updates/s", "ms_per_step": sum(ms) / len(ms), "steps": len(ms),
+                "speedup_of_regions": value / ws / mv,
+                "roofline_frac": MONO_BYTES_PER_UPDATE * mv / 1e9 / peaks()[0]}
+    del phi, pic, phi0
+    torch.cuda.empty_cache()
+
     hbm, peak_kind = peaks()
     kern_mean = sum(kern_ms) / len(kern_ms)
-    base = info["base_B"]
-    alg_bytes = ALG_BYTES_PER_UPDATE[base] * updates
-    achieved = alg_bytes / (kern_mean / 1e3) / 1e9
+    achieved = ALG_BYTES_PER_UPDATE[base] * updates / (kern_mean / 1e3) / 1e9
+    wl = dict(w, B=base)
     out = {
         "metric": METRIC,
         "value": value,
@@ -324,39 +426,94 @@ def run_ours(args):
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms_per_step,
+        "ms_per_step": total_ms / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded random-phase field)",
-        "config": {"workload": WORKLOAD if base == B else WORKLOAD.replace(f"B={B}", f"B={base}"), "grid": N,
-                   "leapfrog_steps": STEPS, "region_base": base,
-                   "regions": int(info["regions_per_band"] * (STEPS // (base // 2))),
+        "config": {"workload": workload_name(wl), "grid": N, "leapfrog_steps": STEPS,
+                   "leapfrog_steps_per_bench_step": PER, "region_base": base,
+                   "bench_step": f"one sp_evolve call of {PER} leapfrog steps continuing the run "
+                                 f"(start levels {sched[args.warmup]}..{sched[-1]} timed); the initial field is "
+                                 f"restored when a pass reaches level {STEPS}",
+                   "regions_per_bench_step": int(info["regions_per_band"] * (PER // (base // 2))),
                    "threads_per_cta": info["threads"], "ctas": info["grid"],
                    "mailbox_slots": info["mailbox_slots"], "mailbox_bytes": info["mailbox_bytes"],
-                   "l2": "flushed (512 MiB write) before every step; state restored on device outside timing",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-        "monolithic": {"value": mono_value, "unit": "site-updates/s", "ms_per_step": sum(mono_ms) / len(mono_ms),
-                       "speedup_of_regions": value / ws / mono_value},
+                   "l2": ("inputs larger than L2 (state 24 B/site = "
+                          f"{24 * sites / 1e9:.1f} GB plus mailboxes), no flush" if N >= 512 else
+                          "state and mailboxes partly L2-resident (see extra key)"),
+                   "init_s": init_s, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "monolithic": mono,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(N == 128 and STEPS == 256 and base == B and args.threads == 0),
+                     "traffic": ncu_traffic(base, updates),
                      "kernel": "region_kernel", "kernel_ms": kern_mean,
                      "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
-                     "design_bytes_per_update": info["bytes_per_update"]},
+                     "design_bytes_per_update": info["bytes_per_update"],
+                     "traffic_from": "profiles/region_kernel_traffic.json scaled by site-updates per launch"},
         "roofline_smem": smem_roofline(updates, kern_mean, clk),
-        "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes, "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
-        "gpu_launches": 2 * args.steps,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,  # per bench step: queue reset + persistent region kernel
         "utilisation": utilisation,
         "clocks": clk,
         "wall_s_timed_region": wall,
         "field_finite": finite,
     }
-    if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if extra:
+        out.update(extra)
     return out
+
+
+def run_small(args):
+    """The 128^3 x 256 workload, whose state and mailboxes are largely
+    L2-resident (the sweep runs at L2 speed there): region path and sweep,
+    L2 flushed (512 MiB write) before every step, state restored on the device
+    outside the timed region."""
+    import torch
+
+    from paper_1011_4046_gb300 import inputs, sp
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    w = SMALL
+    N, STEPS = w["N"], w["STEPS"]
+    p = sp.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
+    st = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
+    init_dev = torch.from_numpy(sp.pack_state(*st)).to(dev)
+    g = sp.Grid([p], stream=stream)
+    g.plan(base_B=w["B"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    updates = N ** 3 * STEPS
+    res = {}
+    for name, flags in (("regions", 0), ("monolithic", sp.SP_MONOLITHIC)):
+        ms, kms = [], []
+        for it in range(args.small_warmup + args.small_steps):
+            rc = sp.sp_write_surface(g.h, 0, sp.SP_SURF_STATE, init_dev.data_ptr(), init_dev.numel() * 8, 1)
+            assert rc == 0, sp.sp_strerror(rc)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = sp.sp_evolve(g.h, STEPS, sp.SP_ASYNC | sp.SP_RESTART | sp.SP_TIMING | flags)
+            e1.record(stream)
+            if rc != 0:
+                raise sp.SpError(rc, "sp_evolve")
+            e1.synchronize()
+            if it >= args.small_warmup:
+                ms.append(e0.elapsed_time(e1))
+                kms.append(g.timing()[1])
+        res[name] = (updates * len(ms) / (sum(ms) / 1e3), sum(ms) / len(ms), sum(kms) / len(kms))
+    g.close()
+    hbm, _ = peaks()
+    kern = res["regions"][2]
+    return {"workload": workload_name(w), "value": res["regions"][0], "unit": "site-updates/s",
+            "ms_per_step": res["regions"][1], "steps": args.small_steps,
+            "monolithic": {"value": res["monolithic"][0], "ms_per_step": res["monolithic"][1],
+                           "speedup_of_regions": res["regions"][0] / res["monolithic"][0]},
+            "roofline_frac": ALG_BYTES_PER_UPDATE[w["B"]] * updates / (kern / 1e3) / 1e9 / hbm,
+            "l2": "flushed (512 MiB write) before every step; state restored on device outside timing"}
 
 
 def run_batched(args):
@@ -392,7 +549,7 @@ def run_batched(args):
         for i, buf in enumerate(inits):
             rc = sp.sp_write_surface(g.h, i, sp.SP_SURF_STATE, buf.data_ptr(), buf.numel() * 8, 1)
             assert rc == 0, sp.sp_strerror(rc)
-        flush_l2(l2_flush)
+        l2_flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -433,28 +590,40 @@ def run_batched(args):
             "gpu_launches": 2 * len(bases) * args.steps}  # per base: queue reset + region kernel
 
 
-def cpu_baseline(budget_s, n_steps_cap=STEPS):
-    """The FP64 oracle, as it stands, on the host cores: the same workload,
-    bounded to about budget_s seconds of steps."""
+def oracle_sample(w, z_planes=SAMPLE_Z):
+    """The bounded sample of workload ``w`` the FP64 oracle is timed on: the
+    first z_planes planes of its initial field, as a periodic slab, with the
+    workload's physics.  Returns (oracle params, phi, pi)."""
     import oracle
     from paper_1011_4046_gb300 import inputs
 
+    N = w["N"]
+    nz = min(N, z_planes)
+    phi = inputs.random_phase_slab((N, N, N), SEED, 0, nz, eta=ETA).astype(np.complex128)
+    p = oracle.make_params((N, N, nz), dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0,
+                           tau_ref=TAU0 + w["STEPS"] * DT)
+    return p, phi, np.zeros_like(phi)
+
+
+def cpu_baseline(budget_s, w=BIG):
+    """The FP64 oracle, as it stands, on the host cores: the bounded sample
+    of the workload, stepped in calls of 4 steps for about budget_s seconds."""
+    import oracle
+
     oracle.build()
-    p = oracle.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
-    phi0, pi0, _ = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
-    phi = phi0.astype(np.complex128)
-    pi = pi0.astype(np.complex128)
-    done, chunk = 0, 8  # steps per oracle call
+    p, phi, pi = oracle_sample(w)
+    sites = p.n[0] * p.n[1] * p.n[2]
+    done, chunk = 0, 4
     t0 = time.perf_counter()
-    while done < n_steps_cap and (time.perf_counter() - t0) < budget_s:
-        k = min(chunk, n_steps_cap - done)
-        phi, pi = oracle.run(p, phi, pi, done, k)
-        done += k
+    while done < w["STEPS"] and (time.perf_counter() - t0) < budget_s:
+        phi, pi = oracle.run(p, phi, pi, done, chunk)
+        done += chunk
     el = time.perf_counter() - t0
-    return {"value": N ** 3 * done / el, "unit": "site-updates/s", "cores": oracle.max_threads(),
+    return {"value": sites * done / el, "unit": "site-updates/s", "cores": oracle.max_threads(),
             "kind": "oracle",
-            "sample": f"first {done} of {STEPS} steps of the {N}^3 workload in calls of 8 steps "
-                      f"({N ** 3 * done:.3g} site-updates, {el:.1f} s, FP64, OpenMP over z-planes)"}
+            "sample": f"the first {p.n[2]} z-planes of the {w['N']}^3 workload's initial field as a periodic "
+                      f"{p.n[0]}x{p.n[1]}x{p.n[2]} slab with the workload's physics, {done} leapfrog steps in "
+                      f"calls of 4 ({sites * done:.3g} site-updates, {el:.1f} s, FP64, OpenMP over z-planes)"}
 
 
 def run_reference(args):
@@ -462,29 +631,28 @@ def run_reference(args):
     if rank != 0:
         return None
     import oracle
-    from paper_1011_4046_gb300 import inputs
 
     oracle.build()
-    p = oracle.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
-    phi0, pi0, _ = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
+    w = BIG
+    p, phi0, pi0 = oracle_sample(w)
+    sites = p.n[0] * p.n[1] * p.n[2]
     per_step = max(1, args.ref_levels)
     times = []
-    phi = phi0.astype(np.complex128)
-    pi = pi0.astype(np.complex128)
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        phi, pi = oracle.run(p, phi0, pi0, 0, per_step)
+        oracle.run(p, phi0, pi0, 0, per_step)
         el = time.perf_counter() - t0
         if it >= args.warmup:
             times.append(el)
-    value = N ** 3 * per_step * len(times) / sum(times)
-    sample = (f"each step: the first {per_step} of {STEPS} leapfrog steps of the {N}^3 workload "
-              f"(FP64 oracle, OpenMP over z-planes)")
+    value = sites * per_step * len(times) / sum(times)
+    sample = (f"each step: {per_step} leapfrog steps of the first {p.n[2]} z-planes of the {w['N']}^3 workload "
+              f"as a periodic {p.n[0]}x{p.n[1]}x{p.n[2]} slab (FP64 oracle, OpenMP over z-planes)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random-phase field)",
-            "config": {"workload": WORKLOAD, "grid": N, "leapfrog_steps": STEPS, "region_base": B},
+            "config": {"workload": workload_name(w), "grid": w["N"], "leapfrog_steps": w["STEPS"],
+                       "region_base": w["B"]},
             "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": oracle.max_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -496,22 +664,47 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1280", choices=["1280", "batched"],
+                    help="1280: the 1280^3 x 2048 workload (default, with the 128^3 x 256 workload as an "
+                         "extra key); batched: the 64-simulation batch")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-levels", type=int, default=4, help="leapfrog steps per reference-arm step")
-    ap.add_argument("--base", type=int, default=B, help="region base (the workload's is 16)")
+    ap.add_argument("--base", type=int, default=0, help="region base (0: the workload's)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
-    ap.add_argument("--grid", type=int, default=N, help="grid side (profiling of smaller cases only)")
-    ap.add_argument("--leapfrog-steps", type=int, default=STEPS, help="steps per run (profiling only)")
-    ap.add_argument("--workload", default="grid", choices=["grid", "batched"],
-                    help="grid: the 128^3 workload (default); batched: the 64-simulation batch")
+    ap.add_argument("--grid", type=int, default=0, help="grid side (profiling of smaller cases only)")
+    ap.add_argument("--per-step", type=int, default=0, help="leapfrog steps per bench step (profiling only)")
+    ap.add_argument("--mono-steps", type=int, default=3, help="timed sweep steps (after one warm-up)")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="timed e2e steps (after one warm-up)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-trace", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 128^3 extra key")
+    ap.add_argument("--small-steps", type=int, default=5)
+    ap.add_argument("--small-warmup", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == "batched":
         out = run_batched(args)
     else:
-        out = run_ours(args)
+        setup_dist()
+        ws, rank, _ = dist_env()
+        w = dict(BIG)
+        if args.grid:
+            w["N"] = args.grid
+        if args.per_step:
+            w["PER_STEP"] = args.per_step
+        extra = {}
+        if not args.no_extra and not args.grid:
+            import torch
+
+            extra["extra_128cubed_l2_resident"] = run_small(args)
+            torch.cuda.empty_cache()
+        out = run_grid(args, w, extra)
+        if rank != 0:
+            out = None
+        elif not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, w)
     if out is not None:
         print(json.dumps(out), flush=True)
 

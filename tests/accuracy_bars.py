@@ -28,6 +28,15 @@ import numpy as np
 ETA_TOL = 1e-5
 
 
+def energy_tol(sites):
+    """Relative tolerance between two FP64 energy sums over ``sites`` sites
+    taken in different orders (the GPU's block tree against the oracle's
+    OpenMP reduction): summing n non-negative terms in any order errs by at
+    most about n 2^-53 relative, and each site contributes up to three
+    gradient links and a product or two, so 4 n 2^-53 bounds the difference."""
+    return 4.0 * sites * 2.0 ** -53
+
+
 def _c128(a):
     return np.asarray(a).astype(np.complex128)
 

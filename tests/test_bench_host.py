@@ -31,7 +31,8 @@ def test_smem_line_uses_the_sampled_clock():
 def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
     """roofline.traffic comes from the committed ncu record only while every
     source that shapes the region kernel's memory traffic is byte-identical to
-    the one the record was taken on, and only for the workload it was taken on."""
+    the one the record was taken on and the region base is the record's; it
+    is the record's bytes per site-update times the launch's site-updates."""
     import hashlib
     import json
 
@@ -44,13 +45,32 @@ def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, m
         h.update((tmp_path / rel).read_bytes())
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "region_kernel_traffic.json").write_text(json.dumps({
-        "kernel_sources_sha256_16": h.hexdigest()[:16],
+        "kernel_sources_sha256_16": h.hexdigest()[:16], "region_base": 16, "site_updates": 4,
         "dram_bytes_read_per_launch": 7, "dram_bytes_write_per_launch": 5}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic(True) == 12
-    assert bench.ncu_traffic(False) is None
+    assert bench.ncu_traffic(16, 4) == 12
+    assert bench.ncu_traffic(16, 40) == 120
+    assert bench.ncu_traffic(32, 4) is None
     (tmp_path / bench.KERNEL_SOURCES[0]).write_text("changed\n")
-    assert bench.ncu_traffic(True) is None
+    assert bench.ncu_traffic(16, 4) is None
+
+
+def test_pass_schedule_continues_and_restarts():
+    """Bench steps continue the run and start over (a restore) only when the
+    next step would pass the run's last level."""
+    assert bench.pass_schedule(5, 64, 2048) == [0, 64, 128, 192, 256]
+    s = bench.pass_schedule(40, 64, 2048)
+    assert s[31] == 1984 and s[32] == 0 and s[33] == 64
+    assert bench.pass_schedule(3, 256, 256) == [0, 0, 0]
+
+
+def test_clock_parsing_reports_median_and_reasons():
+    lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "0, 1900, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+             "0, 2000, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+             "garbage"]
+    c = bench.parse_clocks(lines)
+    assert c == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
 
 
 def test_committed_traffic_record_names_its_capture():
@@ -58,6 +78,7 @@ def test_committed_traffic_record_names_its_capture():
 
     rec = json.load(open(os.path.join(ROOT, "profiles", "region_kernel_traffic.json")))
     assert rec["kernel"] == "region_kernel" and "ncu" in rec["command"] and "--clock-control none" in rec["command"]
+    assert rec["region_base"] in (8, 16, 32) and rec["site_updates"] > 0
     assert rec["dram_bytes_read_per_launch"] > 0 and rec["dram_bytes_write_per_launch"] > 0
 
 
@@ -76,7 +97,7 @@ def test_reference_arm_prints_one_contract_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "site-updates/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
-    assert d["config"]["workload"] == bench.WORKLOAD
+    assert d["config"]["workload"] == bench.workload_name(bench.BIG)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

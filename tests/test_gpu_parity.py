@@ -10,7 +10,8 @@ Bars (stated per result):
   FP32-storage floor;
 * region-scheduled run vs the monolithic GPU sweep: bit-exact (phi, pi, c);
 * diagnostics: plaquette windings equal the oracle's exactly on the same
-  FP32 field; FP64 energy terms agree to 1e-12 relative.
+  FP32 field; FP64 energy terms agree within the rounding bound of two FP64
+  sums taken in different orders (accuracy_bars.energy_tol).
 Every call goes through the C ABI (paper_1011_4046_gb300.sp).
 """
 import numpy as np
@@ -20,7 +21,7 @@ torch = pytest.importorskip("torch")
 
 from paper_1011_4046_gb300 import inputs, sp  # noqa: E402
 
-from accuracy_bars import ETA_TOL, check_run, format_report  # noqa: E402
+from accuracy_bars import ETA_TOL, check_run, energy_tol, format_report  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -279,7 +280,8 @@ def test_batched_sims_in_one_launch():
 # ------------------------------------------------------------ diagnostics
 @pytest.mark.parametrize("run_steps", [16, 64])
 def test_diagnostics_match_oracle(oracle_mod, run_steps):
-    """Windings exactly and the three FP64 energy terms to 1e-12 relative,
+    """Windings exactly and the three FP64 energy terms within the summation
+    rounding bound (accuracy_bars.energy_tol, 5.5e-12 relative here),
     after 16 steps of a matter-era run planned for run_steps: at its end
     (a = 1) and a quarter of the way in (a = (14/26)^2 = 0.29, where the
     potential's a^2 and the level it is taken at matter)."""
@@ -304,7 +306,7 @@ def test_diagnostics_match_oracle(oracle_mod, run_steps):
     op = oracle_mod.make_params(n, dt=p.dt, lam=p.lam, eta=p.eta, nu=p.nu, tau0=p.tau0, tau_ref=p.tau_ref)
     kin, grad, pot = oracle_mod.energy_parts(op, phi, pi, steps)
     for got, ref in ((d["kinetic"], kin), (d["gradient"], grad), (d["potential"], pot)):
-        assert abs(got - ref) <= 1e-12 * abs(ref)
+        assert abs(got - ref) <= energy_tol(n[0] * n[1] * n[2]) * abs(ref)
     a_ref = oracle_mod.level_coeffs(op, steps)["a"]
     assert d["level"] == steps and abs(d["a"] - a_ref) <= 1e-15 * a_ref
     assert (abs(a_ref - 1.0) < 1e-15) == (run_steps == steps)
