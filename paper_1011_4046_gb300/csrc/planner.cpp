@@ -435,6 +435,241 @@ std::string build_tables(int B, TileTables *tp)
     return std::string();
 }
 
+// ---------------------------------------------------------------- octants
+namespace {
+
+// offset from c_j of the cell at octant distance dist (upper octant) of a
+// region of type S along axis d
+inline int xrel_of(int S, int d, int dist, int H) { return dist + (inverted(S, d) ? 0 : H); }
+
+// the octant's cells at level k: dist < w along every axis
+inline int oct_width(int S, int d, int k, int H, int levels)
+{
+    if (k < 1 || k > levels) return 0;
+    return inverted(S, d) ? k : H - k;
+}
+
+}  // namespace
+
+std::string build_octant_tables(const TileTables &t, OctTables *op)
+{
+    OctTables &o = *op;
+    o = OctTables();
+    const int B = t.B, H = t.H, P = H + 2;
+    if (B < 8 || B > kMaxB || B % 4 != 0) return "octant tables need B a multiple of 4 in [8, 32]";
+    o.B = B;
+    o.H = H;
+    o.P = P;
+    auto phi_index = [&](const int u[3]) { return (u[2] * P + u[1]) * P + u[0]; };
+    auto pc_index = [&](const int dist[3]) { return (dist[2] * H + dist[1]) * H + dist[0]; };
+    for (int S = 0; S < kTypes; ++S) {
+        o.levels[S] = t.levels[S];
+        for (int k = 0; k <= kMaxH + 1; ++k)
+            for (int d = 0; d < 3; ++d) {
+                const int w = oct_width(S, d, k, H, o.levels[S]);
+                o.w[S][k][d] = w;
+                o.active[S][k].lo[d] = 1;
+                o.active[S][k].hi[d] = 1 + w;
+            }
+        for (int d = 0; d < 3; ++d) {
+            const int w1 = o.w[S][1][d];
+            o.base_phi[S].lo[d] = 0;        // the inner halo comes from the band base too
+            o.base_phi[S].hi[d] = w1 + 2;
+            o.base_pc[S].lo[d] = 1;
+            o.base_pc[S].hi[d] = w1 + 1;
+        }
+        // the octant boxes are the region's active sets cut at the centre
+        for (int k = 1; k <= o.levels[S]; ++k) {
+            int64_t v = 1;
+            for (int d = 0; d < 3; ++d) v *= o.w[S][k][d];
+            if (8 * v != t.active[S][k].volume()) return "octant boxes do not split the region's level";
+        }
+    }
+
+    struct Exp {
+        int producer, L;
+        ExportEntry e;
+    };
+    std::vector<Exp> exports;
+    int64_t imp_bytes[kTypes] = {0};
+    for (int S = 0; S < kTypes; ++S) {
+        int32_t off = 0;
+        for (int L = 0; L < kMaxH; ++L) {
+            o.imp_full_off[S][L] = (int32_t)o.imp_full.size();
+            o.imp_phi_off[S][L] = (int32_t)o.imp_phi.size();
+            o.face_imp_off[S][L] = (int32_t)o.face_imp.size();
+            o.imp_full_n[S][L] = o.imp_phi_n[S][L] = o.face_imp_n[S][L] = 0;
+            o.mb_level_off[S][L] = off;
+            if (L < 1 || L > H - 1) continue;
+            std::vector<std::array<int, 3>> full, ring;
+            for (int z = 0; z <= H; ++z)
+                for (int y = 0; y <= H; ++y)
+                    for (int x = 0; x <= H; ++x) {
+                        const int dist[3] = {x, y, z};
+                        int r[3];
+                        for (int d = 0; d < 3; ++d) r[d] = xrel_of(S, d, dist[d], H);
+                        if (in_active(S, r, L, B)) continue;
+                        if (in_active(S, r, L + 1, B))
+                            full.push_back({x, y, z});
+                        else if (in_ring(S, r, L + 1, B))
+                            ring.push_back({x, y, z});
+                    }
+            const int nf = (int)full.size(), np = (int)ring.size();
+            o.imp_full_n[S][L] = nf;
+            o.imp_phi_n[S][L] = np;
+            imp_bytes[S] += 8 * (24LL * nf + 8LL * np);
+            for (int kind = 0; kind < 2; ++kind) {
+                const auto &cells = kind == 0 ? full : ring;
+                for (int i = 0; i < (int)cells.size(); ++i) {
+                    const int dist[3] = {cells[i][0], cells[i][1], cells[i][2]};
+                    int u[3], r[3];
+                    for (int d = 0; d < 3; ++d) {
+                        u[d] = dist[d] + 1;
+                        r[d] = xrel_of(S, d, dist[d], H);
+                        if (u[d] >= P) return "octant import outside the octant's buffer";
+                    }
+                    if (kind == 0) {
+                        for (int d = 0; d < 3; ++d)
+                            if (dist[d] >= H) return "octant full import is not an octant cell";
+                        o.imp_full.push_back(phi_index(u) | (pc_index(dist) << 16));
+                        int mask = 0;
+                        for (int d = 0; d < 3; ++d)
+                            if (dist[d] == 0) mask |= 1 << d;
+                        if (mask) o.face_imp.push_back(phi_index(u) | (mask << 16));
+                    } else {
+                        o.imp_phi.push_back(phi_index(u));
+                    }
+                    // the producer: owner at level L in the same band
+                    int Sp = 0, delta[3], dp[3], gmask = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        const bool inv = owner_1d(r[d], L, B, &delta[d]);
+                        if (inv) Sp |= 1 << d;
+                        const int rp = r[d] - delta[d] * B - (inv ? 0 : H);  // from the producer's centre
+                        const int op_d = rp >= 0;
+                        dp[d] = op_d ? rp : -1 - rp;
+                        const bool flip = inverted(S, d) != inv;
+                        // the consumer is the upper octant at position 0: every producer sits at
+                        // position 0 too; along an axis of the same type it is the same octant,
+                        // along a flipped one either (the outer halo of the last level comes
+                        // from the upright neighbour's upper half, the rest from its lower one)
+                        if (delta[d] != 0 || (!flip && op_d != 1))
+                            return "octant import from an unexpected producer octant";
+                        gmask |= (op_d ? 0 : 1) << d;
+                        if (dp[d] < 0 || dp[d] >= H) return "octant producer cell outside its octant";
+                    }
+                    if ((Sp & ~S) != 0 || Sp == S) return "octant import owner type is not a proper subset";
+                    int rpx[3];
+                    for (int d = 0; d < 3; ++d) rpx[d] = r[d] - delta[d] * B;
+                    if (!in_active(Sp, rpx, L, B)) return "octant import owner does not compute the cell";
+                    if (kind == 0 && in_active(Sp, rpx, L + 1, B))
+                        return "octant full-state export cell is recomputed by the next level";
+                    int up[3];
+                    for (int d = 0; d < 3; ++d) up[d] = dp[d] + 1;
+                    ExportEntry e;
+                    e.src = phi_index(up) | ((kind == 0 ? pc_index(dp) : 0xFFFF) << 16);
+                    e.code = S | (gmask << 3);
+                    e.dst_phi = kind == 0 ? off + 2 * nf + i : off + 3 * nf + i;
+                    e.dst_pc = kind == 0 ? off + 2 * i : -1;
+                    exports.push_back({Sp, L, e});
+                }
+            }
+            o.face_imp_n[S][L] = (int32_t)o.face_imp.size() - o.face_imp_off[S][L];
+            off += 3 * nf + np;
+            off += off & 1;  // every chunk 16-byte aligned
+        }
+        o.mb_size[S] = off;
+    }
+    std::stable_sort(exports.begin(), exports.end(), [](const Exp &a, const Exp &b) {
+        if (a.producer != b.producer) return a.producer < b.producer;
+        if (a.L != b.L) return a.L < b.L;
+        if (a.e.code != b.e.code) return a.e.code < b.e.code;
+        return a.e.dst_phi < b.e.dst_phi;
+    });
+    int64_t exp_bytes[kTypes] = {0};
+    {
+        size_t i = 0;
+        for (int S = 0; S < kTypes; ++S)
+            for (int L = 0; L < kMaxH; ++L) {
+                o.exp_off[S][L] = (int32_t)o.exp.size();
+                while (i < exports.size() && exports[i].producer == S && exports[i].L == L) {
+                    o.exp.push_back(exports[i].e);
+                    exp_bytes[S] += 8 * (exports[i].e.dst_pc >= 0 ? 24 : 8);
+                    ++i;
+                }
+                o.exp_n[S][L] = (int32_t)o.exp.size() - o.exp_off[S][L];
+            }
+        if (i != exports.size()) return "octant export bookkeeping mismatch";
+    }
+
+    // ---- inner-face exchange: before level L+1 every octant needs phi(L) on
+    // the neighbour's dist = 0 face inside the level-(L+1) box along the other
+    // axes; the neighbour holds it as a level-L cell or a level-L import ----
+    for (int S = 0; S < kTypes; ++S)
+        for (int L = 1; L < o.levels[S]; ++L)
+            for (int d = 0; d < 3; ++d) {
+                const int *w1 = o.w[S][L + 1], *w0 = o.w[S][L];
+                if (w1[d] == 0) continue;
+                const int a = (d + 1) % 3, b = (d + 2) % 3;
+                int64_t want = (int64_t)w1[a] * w1[b], computed = 0, imported = 0;
+                for (int ib = 0; ib < w1[b]; ++ib)
+                    for (int ia = 0; ia < w1[a]; ++ia)
+                        if (ia < w0[a] && ib < w0[b] && w0[d] > 0) ++computed;
+                for (int i = 0; i < o.face_imp_n[S][L]; ++i)
+                    if ((o.face_imp[o.face_imp_off[S][L] + i] >> 16) & (1 << d)) ++imported;
+                if (computed + imported != want) return "inner-face exchange does not cover the neighbour's needs";
+            }
+
+    // ---- the kernel's copy schedule, as for whole regions: level L's sloped
+    // surface lands one level ahead; it must touch nothing levels L-2 and L-1
+    // read or write ----
+    auto in_box = [](const Box3 &bx, int x, int y, int z) {
+        return x >= bx.lo[0] && x < bx.hi[0] && y >= bx.lo[1] && y < bx.hi[1] && z >= bx.lo[2] && z < bx.hi[2];
+    };
+    for (int S = 0; S < kTypes; ++S)
+        for (int L = 1; L <= H - 1; ++L) {
+            const Box3 *A = o.active[S];
+            auto phi_ok = [&](int q) {
+                const int x = q % P, y = (q / P) % P, z = q / (P * P);
+                if (x == 0 || y == 0 || z == 0) return false;  // the inner halo is the exchange's
+                if (L - 2 >= 1 && in_box(A[L - 2], x, y, z)) return false;
+                if (L - 1 >= 1) {
+                    const int nb[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+                    for (const auto &v : nb)
+                        if (in_box(A[L - 1], x + v[0], y + v[1], z + v[2])) return false;
+                }
+                return true;
+            };
+            for (int i = 0; i < o.imp_phi_n[S][L]; ++i)
+                if (!phi_ok(o.imp_phi[o.imp_phi_off[S][L] + i])) return "an octant copy overtakes a level in flight";
+            for (int i = 0; i < o.imp_full_n[S][L]; ++i) {
+                const int e = o.imp_full[o.imp_full_off[S][L] + i];
+                if (!phi_ok(e & 0xFFFF)) return "an octant copy overtakes a level in flight";
+                const int c = e >> 16, x = c % H + 1, y = (c / H) % H + 1, z = c / (H * H) + 1;
+                for (int k = std::max(1, L - 2); k <= L; ++k)
+                    if (in_box(A[k], x, y, z)) return "an octant (pi, c) copy overtakes a level in flight";
+            }
+        }
+
+    // ---- traffic and site-updates per region (eight octants) ----
+    for (int S = 0; S < kTypes; ++S) {
+        int64_t base_cells = 0, upd = 0;
+        const Box3 &bp = o.base_phi[S], &bc = o.base_pc[S];
+        for (int z = bp.lo[2]; z < bp.hi[2]; ++z)
+            for (int y = bp.lo[1]; y < bp.hi[1]; ++y)
+                for (int x = bp.lo[0]; x < bp.hi[0]; ++x) {
+                    const int out = (x < bc.lo[0] || x >= bc.hi[0]) + (y < bc.lo[1] || y >= bc.hi[1]) +
+                                    (z < bc.lo[2] || z >= bc.hi[2]);
+                    base_cells += out <= 1;
+                }
+        for (int k = 1; k <= o.levels[S]; ++k) upd += 8 * o.active[S][k].volume();
+        if (upd != t.updates[S]) return "octant site-updates differ from the region's";
+        o.updates[S] = upd;
+        o.bytes_read[S] = 8 * (8 * base_cells + 16 * o.active[S][1].volume()) + imp_bytes[S];
+        o.bytes_written[S] = exp_bytes[S] + (S == kTypes - 1 ? 24LL * B * B * B : 0);
+    }
+    return std::string();
+}
+
 PlanStats plan_stats(const TileTables &t, const int n[3])
 {
     PlanStats s{};

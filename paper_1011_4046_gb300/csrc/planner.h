@@ -103,6 +103,56 @@ struct TileTables {
 // the same band: returns true for an inverted piece, and its index offset.
 bool owner_1d(int r, int L, int B, int *delta);
 
+// One region split over a 2 x 2 x 2 cluster of CTAs, one octant each (the
+// region's cells on one side of its centre along every axis; the centre is
+// c_j for an inverted axis and c_j + H for an upright one).  Every octant is
+// described in its own mirrored coordinates: dist = r for the upper half
+// (r >= 0) and -1 - r for the lower one, so dist grows away from the centre
+// and the octant's active cells at level k form the corner box
+// dist < w(k) along each axis, w = k (inverted axis) or H - k (upright): the
+// same box in all eight octants.  Buffer coordinate u = dist + 1 in
+// [0, H + 2): u = 0 is the inner halo (the neighbouring octant's dist = 0
+// layer, received from that CTA every level), u = H + 1 the outer halo.
+//
+// The tables below are those of the octant whose every dist equals r (the
+// upper one along every axis); by the mirror symmetry they serve all eight.
+// Imports are the region's imports that fall in the octant (the mailbox of a
+// region is eight equal octant mailboxes, each laid out like the B <= 16
+// ones).  An export entry names the consumer by its type and the set G of
+// axes along which the consumer's octant differs from the producer's
+// (consumer octant = producer octant ^ G).  Its position differs from the
+// producer's only along the axes of F = (consumer type) ^ (producer type):
+// there it is one further exactly when the producer's octant bit equals G's
+// bit (producer upper and consumer lower octant, or, for the outer halo of
+// the last level, producer lower and consumer lower).
+struct OctTables {
+    int B = 0, H = 0, P = 0;                   // P = H + 2 (buffer side)
+    int32_t levels[kTypes];
+    int32_t w[kTypes][kMaxH + 2][3];           // active widths at level k (0 = none)
+    Box3 active[kTypes][kMaxH + 2];            // u-box [1, w + 1) of level k
+    Box3 base_phi[kTypes], base_pc[kTypes];    // u-boxes read from the band base
+    std::vector<int32_t> imp_full, imp_phi;    // (pc index << 16 | phi index), phi index
+    int32_t imp_full_off[kTypes][kMaxH], imp_full_n[kTypes][kMaxH];
+    int32_t imp_phi_off[kTypes][kMaxH], imp_phi_n[kTypes][kMaxH];
+    int32_t mb_level_off[kTypes][kMaxH];       // float2 offset of level L's chunk in an octant mailbox
+    int32_t mb_size[kTypes];                   // float2 elements per octant mailbox (16-byte multiple)
+    // exports: code = consumer type | G << 3; dst offsets in the consumer octant's mailbox
+    std::vector<ExportEntry> exp;
+    int32_t exp_off[kTypes][kMaxH], exp_n[kTypes][kMaxH];
+    // imported cells of level L on the inner faces (dist_d = 0 along some
+    // axis d, inside the next level's box along the others): phi index | axis
+    // mask << 16; the CTA sends them to its neighbours with its own face cells
+    std::vector<int32_t> face_imp;
+    int32_t face_imp_off[kTypes][kMaxH], face_imp_n[kTypes][kMaxH];
+    // per region (all eight octants): traffic and site-updates
+    int64_t bytes_read[kTypes], bytes_written[kTypes], updates[kTypes];
+};
+
+// Builds and self-checks the octant tables of base B (B a multiple of 4,
+// 8 <= B <= 32) from the region tables t of the same base (its dependency
+// pattern is the region's).  Returns an empty string on success.
+std::string build_octant_tables(const TileTables &t, OctTables *o);
+
 // Builds and self-checks the tables for base size B (even, 4 <= B <= 32).
 // Returns an empty string on success or a description of the failed check.
 std::string build_tables(int B, TileTables *t);

@@ -11,6 +11,7 @@
 //   * executes the regions one at a time in a seeded random topological
 //     order with the same FP32 site update, so the result can be compared bit
 //     for bit with a whole-grid CPU sweep.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -203,6 +204,176 @@ bool setup(int B, const int n[3], int nbands, Grid *g, sp::TileTables *t, std::s
         g->Jtot *= g->J[d];
     }
     return true;
+}
+
+// ---- octant executor: a region as eight octants (the cluster kernel's data
+// flow), level by level, with the inner faces exchanged between octants
+// before every level and everything else taken from the octant tables.
+// Buffers start as NaN, so any read the tables do not provide shows up as a
+// mismatch with the sweep. ----
+int run_octants(const Grid &g, const sp::TileTables &t, int nsteps, uint64_t order_seed, const sp::LevelCoef *coef,
+                const sp::PhysConst &q, f2 *F, f2 *V, f2 *K, char *msg, int msglen, int slots)
+{
+    auto fail = [&](const std::string &m) {
+        std::snprintf(msg, msglen, "%s", m.c_str());
+        return 0;
+    };
+    sp::OctTables o;
+    std::string err = sp::build_octant_tables(t, &o);
+    if (!err.empty()) return fail(err);
+    const int B = g.B, H = g.H, P = o.P, PP = P * P;
+    const int64_t R = g.regions();
+    std::vector<std::vector<f2>> mbox(2);
+    std::vector<int64_t> type_off(8);
+    int64_t slot = 0;
+    for (int S = 0; S < 8; ++S) {
+        type_off[S] = slot;
+        slot += (int64_t)g.Jtot * 8 * o.mb_size[S];
+    }
+    for (auto &m : mbox) m.assign(slot, f2{NAN, NAN});
+    std::vector<int> count(R);
+    std::vector<int64_t> ready;
+    for (int64_t r = 0; r < R; ++r) {
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        count[r] = initial_count(t, band, S, slots == 1);
+        if (count[r] == 0) ready.push_back(r);
+    }
+    std::mt19937_64 rng(order_seed);
+    struct Oct {
+        std::vector<f2> buf[2], pis, cs;
+    };
+    std::vector<Oct> oc(8);
+    for (auto &x : oc) {
+        x.buf[0].resize(P * P * P);
+        x.buf[1].resize(P * P * P);
+        x.pis.resize(H * H * H);
+        x.cs.resize(H * H * H);
+    }
+    int64_t done = 0;
+    while (!ready.empty()) {
+        size_t pick = (size_t)(rng() % ready.size());
+        int64_t r = ready[pick];
+        ready[pick] = ready.back();
+        ready.pop_back();
+        int band, S, j[3];
+        g.decode(r, &band, &S, j);
+        int C[3];
+        for (int d = 0; d < 3; ++d) C[d] = (band & 1) * H + j[d] * B + (sp::inverted(S, d) ? 0 : H);
+        auto gsite = [&](int oi, const int u[3]) {
+            int p[3];
+            for (int d = 0; d < 3; ++d) {
+                const int dist = u[d] - 1;
+                p[d] = wrap(C[d] + (((oi >> d) & 1) ? dist : -1 - dist), g.n[d]);
+            }
+            return g.site(p);
+        };
+        std::vector<f2> &mb = mbox[slots == 2 ? band & 1 : 0];
+        const int jl = j[0] + g.J[0] * (j[1] + g.J[1] * j[2]);
+        for (int oi = 0; oi < 8; ++oi) {
+            Oct &x = oc[oi];
+            for (auto *v : {&x.buf[0], &x.buf[1], &x.pis, &x.cs}) std::fill(v->begin(), v->end(), f2{NAN, NAN});
+            const sp::Box3 &bp = o.base_phi[S], &bc = o.base_pc[S];
+            for (int uz = bp.lo[2]; uz < bp.hi[2]; ++uz)
+                for (int uy = bp.lo[1]; uy < bp.hi[1]; ++uy)
+                    for (int ux = bp.lo[0]; ux < bp.hi[0]; ++ux) {
+                        const int out = (ux < bc.lo[0] || ux >= bc.hi[0]) + (uy < bc.lo[1] || uy >= bc.hi[1]) +
+                                        (uz < bc.lo[2] || uz >= bc.hi[2]);
+                        if (out > 1) continue;
+                        const int u[3] = {ux, uy, uz};
+                        const int64_t s = gsite(oi, u);
+                        x.buf[0][(uz * P + uy) * P + ux] = F[s];
+                        if (out == 0) {
+                            const int ci = ((uz - 1) * H + (uy - 1)) * H + (ux - 1);
+                            x.pis[ci] = V[s];
+                            x.cs[ci] = K[s];
+                        }
+                    }
+            // every sloped-surface import lands at region start (the kernel: one level ahead)
+            const int64_t self = type_off[S] + ((int64_t)jl * 8 + oi) * o.mb_size[S];
+            for (int L = 1; L <= H - 1; ++L) {
+                std::vector<f2> &dst = x.buf[L & 1];
+                const int64_t base = self + o.mb_level_off[S][L];
+                const int nf = o.imp_full_n[S][L], np = o.imp_phi_n[S][L];
+                for (int i = 0; i < nf; ++i) {
+                    const int e = o.imp_full[o.imp_full_off[S][L] + i];
+                    x.pis[e >> 16] = mb[base + 2 * i];
+                    x.cs[e >> 16] = mb[base + 2 * i + 1];
+                    dst[e & 0xFFFF] = mb[base + 2 * nf + i];
+                }
+                for (int i = 0; i < np; ++i) dst[o.imp_phi[o.imp_phi_off[S][L] + i]] = mb[base + 3 * nf + i];
+            }
+        }
+        for (int k = 1; k <= o.levels[S]; ++k) {
+            const int *w = o.w[S][k];
+            // inner faces of phi(k-1) (level 1: the band base brought them)
+            if (k >= 2)
+                for (int oi = 0; oi < 8; ++oi)
+                    for (int d = 0; d < 3; ++d) {
+                        if (w[d] == 0) continue;
+                        const int a = (d + 1) % 3, b = (d + 2) % 3;
+                        const std::vector<f2> &src = oc[oi].buf[(k - 1) & 1];
+                        std::vector<f2> &dst = oc[oi ^ (1 << d)].buf[(k - 1) & 1];
+                        for (int ib = 1; ib <= w[b]; ++ib)
+                            for (int ia = 1; ia <= w[a]; ++ia) {
+                                int us[3], ud[3];
+                                us[d] = 1;
+                                ud[d] = 0;
+                                us[a] = ud[a] = ia;
+                                us[b] = ud[b] = ib;
+                                dst[(ud[2] * P + ud[1]) * P + ud[0]] = src[(us[2] * P + us[1]) * P + us[0]];
+                            }
+                    }
+            for (int oi = 0; oi < 8; ++oi) {
+                Oct &x = oc[oi];
+                const std::vector<f2> &prev = x.buf[(k - 1) & 1];
+                std::vector<f2> &cur = x.buf[k & 1];
+                for (int uz = 1; uz <= w[2]; ++uz)
+                    for (int uy = 1; uy <= w[1]; ++uy)
+                        for (int ux = 1; ux <= w[0]; ++ux) {
+                            const int pi_ = (uz * P + uy) * P + ux;
+                            const int ci = ((uz - 1) * H + (uy - 1)) * H + (ux - 1);
+                            cur[pi_] = sp::site_update(prev[pi_], prev[pi_ - 1], prev[pi_ + 1], prev[pi_ - P],
+                                                       prev[pi_ + P], prev[pi_ - PP], prev[pi_ + PP], x.pis[ci],
+                                                       x.cs[ci], coef[band * H + k - 1], q);
+                        }
+                if (k <= H - 1)
+                    for (int i = 0; i < o.exp_n[S][k]; ++i) {
+                        const sp::ExportEntry &e = o.exp[o.exp_off[S][k] + i];
+                        const int Sc = e.code & 7, Gm = (e.code >> 3) & 7, Fm = Sc ^ S;
+                        // one further along a flipped axis where the producer's octant bit equals G's
+                        const int step = Fm & ~(oi ^ Gm) & 7;
+                        int jc[3];
+                        for (int d = 0; d < 3; ++d) jc[d] = wrap(j[d] + ((step >> d) & 1), g.J[d]);
+                        const int oc_ = oi ^ Gm;
+                        const int64_t dst = type_off[Sc] +
+                                            ((int64_t)(jc[0] + g.J[0] * (jc[1] + g.J[1] * jc[2])) * 8 + oc_) *
+                                                o.mb_size[Sc];
+                        mb[dst + e.dst_phi] = cur[e.src & 0xFFFF];
+                        if (e.dst_pc >= 0) {
+                            mb[dst + e.dst_pc] = x.pis[(e.src >> 16) & 0xFFFF];
+                            mb[dst + e.dst_pc + 1] = x.cs[(e.src >> 16) & 0xFFFF];
+                        }
+                    }
+                if (k == H)
+                    for (int uz = 1; uz <= H; ++uz)
+                        for (int uy = 1; uy <= H; ++uy)
+                            for (int ux = 1; ux <= H; ++ux) {
+                                const int u[3] = {ux, uy, uz};
+                                const int64_t s = gsite(oi, u);
+                                const int ci = ((uz - 1) * H + (uy - 1)) * H + (ux - 1);
+                                F[s] = cur[(uz * P + uy) * P + ux];
+                                V[s] = x.pis[ci];
+                                K[s] = x.cs[ci];
+                            }
+            }
+        }
+        for (int64_t s : successors(t, g, r, slots == 1))
+            if (--count[s] == 0) ready.push_back(s);
+        ++done;
+    }
+    if (done != R) return fail("not every region ran");
+    return 1;
 }
 
 }  // namespace
@@ -403,6 +574,8 @@ int rx_run(int B, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         }
         return 1;
     }
+
+    if (mode == 2) return run_octants(g, t, nsteps, order_seed, coef, q, F, V, K, msg, msglen, slots);
 
     // ---- region executor: the kernel's data flow, one region at a time ----
     const int P = g.P, H = g.H;
@@ -614,3 +787,25 @@ int rx_active_box(int B, int S, int k, int32_t *lohi)
 }
 
 }  // extern "C"
+
+// Sizes of the octant tables of base B: out = {full imports, phi-only
+// imports, export entries, face imports, largest octant mailbox (float2),
+// site-updates, bytes read, bytes written (per steady-state band cell)}.
+extern "C" int rx_octant_stats(int B, int64_t *out)
+{
+    sp::TileTables t;
+    if (!sp::build_tables(B, &t).empty()) return 0;
+    sp::OctTables o;
+    if (!sp::build_octant_tables(t, &o).empty()) return 0;
+    int64_t mb = 0, upd = 0, rd = 0, wr = 0;
+    for (int S = 0; S < 8; ++S) {
+        mb = std::max<int64_t>(mb, o.mb_size[S]);
+        upd += o.updates[S];
+        rd += o.bytes_read[S];
+        wr += o.bytes_written[S];
+    }
+    const int64_t v[8] = {(int64_t)o.imp_full.size(), (int64_t)o.imp_phi.size(), (int64_t)o.exp.size(),
+                          (int64_t)o.face_imp.size(), mb, upd, rd, wr};
+    for (int i = 0; i < 8; ++i) out[i] = v[i];
+    return 1;
+}
