@@ -29,6 +29,16 @@ namespace {
 struct TablesOnDevice {
     sp::TileTables host;
     sp::TablesDev dev;             // host copy of the device descriptor
+    // base 32: the octant tables of the cluster kernel (TablesDev then holds
+    // the dependency pattern only)
+    bool octant = false;
+    sp::OctTables oct;
+    sp::TablesOct oct_dev;
+    sp::TablesOct *d_oct = nullptr;
+    unsigned short *d_oimp = nullptr;
+    int2 *d_oexp = nullptr;
+    int *d_oface = nullptr;
+    int64_t region_mb_size[sp::kTypes] = {0};  // float2 elements of one region's mailbox
     // band-0 regions of types 0 .. seed_types-1 have no predecessor and are
     // queued at reset (1 for bases of 8 and more: the pyramids; at base 4 every
     // type but the inverted pyramid computes one level and imports nothing)
@@ -269,6 +279,178 @@ bool block_decode_exact(const sp::Box3 *boxes, int last, const float (*rcp)[2])
     return true;
 }
 
+// The dependency pattern of a base (same-band, next-band and mailbox-reuse
+// successors, predecessor counts) into the device descriptor; geometry
+// fields are left to the caller.
+void fill_dag(const sp::TileTables &t, sp::TablesDev *h)
+{
+    for (int S = 0; S < sp::kTypes; ++S) {
+        sp::TypeMeta &m = h->type[S];
+        m.levels = t.levels[S];
+        m.n_same_succ = (int)t.same_succ[S].size();
+        m.same_preds = t.same_preds[S];
+        m.prev_preds = t.prev_preds[S];
+        m.n_reuse = (int)t.reuse_succ[S].size();
+        m.reuse_preds = t.reuse_preds[S];
+        for (size_t i = 0; i < t.same_succ[S].size(); ++i) m.same_succ[i] = t.same_succ[S][i];
+    }
+    for (int q = 0; q < 2; ++q)
+        for (size_t i = 0; i < t.next_succ[q].size(); ++i) h->next_succ[q][i] = t.next_succ[q][i];
+}
+
+int upload_reuse(const sp::TileTables &t, sp::Succ **d_reuse)
+{
+    std::vector<sp::Succ> reuse((size_t)sp::kTypes * sp::kMaxSameSucc, sp::Succ{0, {0, 0, 0}});
+    for (int S = 0; S < sp::kTypes; ++S) {
+        if ((int)t.reuse_succ[S].size() > sp::kMaxSameSucc) return SP_EINVAL;
+        for (size_t i = 0; i < t.reuse_succ[S].size(); ++i) reuse[(size_t)S * sp::kMaxSameSucc + i] = t.reuse_succ[S][i];
+    }
+    if (cudaMalloc((void **)d_reuse, reuse.size() * sizeof(sp::Succ)) != cudaSuccess) return SP_ENOMEM;
+    if (cudaMemcpy(*d_reuse, reuse.data(), reuse.size() * sizeof(sp::Succ), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SP_ECUDA;
+    return SP_OK;
+}
+
+// Base 32: the region's dependency pattern plus the octant tables of the
+// cluster kernel, packed for the device (see sp_device.cuh, TablesOct).
+int build_octant_device_tables(sp_grid *g, TablesOnDevice *tdp)
+{
+    TablesOnDevice &td = *tdp;
+    const sp::TileTables &t = td.host;
+    if (!sp::build_octant_tables(t, &td.oct).empty()) return SP_EINVAL;
+    const sp::OctTables &o = td.oct;
+    if (o.H != 16 || o.P != 18) return SP_EINVAL;  // the kernel's index packing and shifts
+    td.octant = true;
+    td.seed_types = 0;
+    while (td.seed_types < sp::kTypes && t.same_preds[td.seed_types] == 0) ++td.seed_types;
+    for (int S = td.seed_types; S < sp::kTypes; ++S)
+        if (t.same_preds[S] == 0) return SP_EINVAL;
+    if (td.seed_types == 0) return SP_EINVAL;
+    std::memset(&td.dev, 0, sizeof td.dev);
+    td.dev.B = t.B;
+    td.dev.H = t.H;
+    td.dev.P = t.P;
+    fill_dag(t, &td.dev);
+    sp::TablesOct &h = td.oct_dev;
+    std::memset(&h, 0, sizeof h);
+    h.B = o.B;
+    h.H = o.H;
+    h.P = o.P;
+    std::vector<unsigned short> imp;
+    for (int S = 0; S < sp::kTypes; ++S) {
+        sp::OctTypeMeta &m = h.type[S];
+        m.levels = o.levels[S];
+        m.mb_size = o.mb_size[S];
+        td.region_mb_size[S] = 8LL * o.mb_size[S];
+        td.dev.type[S].mb_size = 8 * o.mb_size[S];
+        m.base_phi = o.base_phi[S];
+        m.base_pc = o.base_pc[S];
+        const sp::Box3 &bp = o.base_phi[S];
+        const int bw0 = bp.hi[0] - bp.lo[0], bw1 = bp.hi[1] - bp.lo[1], bw2 = bp.hi[2] - bp.lo[2];
+        m.base_cols = bw0 * bw1;
+        m.base_runs = (bw2 + 3) / 4;
+        m.rcp_cols = 1.0f / (float)m.base_cols;
+        m.rcp_base0 = 1.0f / (float)bw0;
+        for (int u = 0; u < m.base_cols * m.base_runs; ++u) {  // the kernel's (run, column, row) split
+            const int run = sp::fdiv(u, m.rcp_cols), i = u - run * m.base_cols;
+            if (run != u / m.base_cols || sp::fdiv(i, m.rcp_base0) != i / bw0) return SP_EINVAL;
+        }
+        for (int k = 0; k < sp::kMaxHOct + 2; ++k) {
+            int w[3];
+            for (int d = 0; d < 3; ++d) {
+                w[d] = k <= sp::kMaxH + 1 ? o.w[S][k][d] : 0;
+                m.w[k][d] = (unsigned char)w[d];
+            }
+            m.rcp_w[k][0] = w[0] ? 1.0f / (float)w[0] : 0.0f;
+            m.rcp_w[k][1] = w[1] ? 1.0f / (float)w[1] : 0.0f;
+            const int fd[3] = {w[1], w[0] - 1, w[1] - 1};
+            for (int q = 0; q < 3; ++q) m.rcp_f[k][q] = fd[q] > 0 ? 1.0f / (float)fd[q] : 0.0f;
+            // the kernel's face-first decode: slabs x (w1 x w2), y ((w0-1) x w2), z ((w0-1) x (w1-1)),
+            // then the interior ((w0-1) x (w1-1) x (w2-1))
+            if (w[0] > 0 && w[1] > 0 && w[2] > 0) {
+                for (int i = 0; i < w[1] * w[2]; ++i)
+                    if (sp::fdiv(i, m.rcp_f[k][0]) != i / w[1]) return SP_EINVAL;
+                if (w[0] > 1)
+                    for (int i = 0; i < (w[0] - 1) * std::max(w[2], w[1]); ++i)
+                        if (sp::fdiv(i, m.rcp_f[k][1]) != i / (w[0] - 1)) return SP_EINVAL;
+                if (w[0] > 1 && w[1] > 1)
+                    for (int i = 0; i < (w[0] - 1) * (w[1] - 1) * (w[2] - 1); ++i) {
+                        const int t = sp::fdiv(i, m.rcp_f[k][1]);
+                        if (t != i / (w[0] - 1) || sp::fdiv(t, m.rcp_f[k][2]) != t / (w[1] - 1)) return SP_EINVAL;
+                    }
+            }
+            for (int i = 0; i < w[0] * w[1] * w[2]; ++i) {  // the kernel's decode of level k's cells
+                const int t1 = sp::fdiv(i, m.rcp_w[k][0]);
+                if (t1 != i / w[0] || sp::fdiv(t1, m.rcp_w[k][1]) != t1 / w[1]) return SP_EINVAL;
+            }
+            int64_t xb = 0;  // inner-face bytes received before level k (the faces of phi(k-1))
+            if (k >= 2)
+                for (int d = 0; d < 3; ++d)
+                    if (w[d] > 0) xb += 8LL * w[(d + 1) % 3] * w[(d + 2) % 3];
+            m.xbytes[k] = (int)xb;
+        }
+        for (int L = 0; L < sp::kMaxHOct; ++L) {
+            m.mb_level_off[L] = o.mb_level_off[S][L];
+            m.exp_off[L] = o.exp_off[S][L];
+            m.exp_n[L] = o.exp_n[S][L];
+            m.face_off[L] = o.face_imp_off[S][L];
+            m.face_n[L] = o.face_imp_n[S][L];
+            m.imp_full_n[L] = o.imp_full_n[S][L];
+            m.imp_phi_n[L] = o.imp_phi_n[S][L];
+            m.imp_full_off[L] = (int)imp.size();
+            for (int i = 0; i < o.imp_full_n[S][L]; ++i) {
+                const int e = o.imp_full[o.imp_full_off[S][L] + i], c = e >> 16;
+                const int pidx = (((c >> 8) + 1) * 18 + ((c >> 4) & 15) + 1) * 18 + (c & 15) + 1;
+                if (pidx != (e & 0xFFFF)) return SP_EINVAL;  // the kernel derives phi from (pi, c) by shifts
+                imp.push_back((unsigned short)c);
+            }
+            m.imp_phi_off[L] = (int)imp.size();
+            for (int i = 0; i < o.imp_phi_n[S][L]; ++i) imp.push_back((unsigned short)o.imp_phi[o.imp_phi_off[S][L] + i]);
+        }
+        if (o.mb_size[S] > 0xFFFF) return SP_EINVAL;
+    }
+    while (imp.size() % 8) imp.push_back(0);
+    h.imp_n = (int)imp.size();
+    std::vector<int2> ex(o.exp.size());
+    for (size_t i = 0; i < o.exp.size(); ++i) {
+        const sp::ExportEntry &e = o.exp[i];
+        const int phi = e.src & 0xFFFF, pc = (e.src >> 16) & 0xFFFF, has_pc = e.dst_pc >= 0;
+        if (phi >= 8192 || (has_pc && pc >= 4096) || e.dst_phi < 0 || e.dst_phi > 0xFFFF || e.dst_pc > 0xFFFF)
+            return SP_EINVAL;
+        ex[i].x = (int)((unsigned)phi | ((unsigned)(has_pc ? pc : 0) << 13) | ((unsigned)e.code << 25) |
+                        ((unsigned)has_pc << 31));
+        ex[i].y = (int)((unsigned)e.dst_phi | ((unsigned)(has_pc ? e.dst_pc : 0) << 16));
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void **dst, const void *src, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up((void **)&td.d_oimp, imp.data(), imp.size() * sizeof(unsigned short));
+    up((void **)&td.d_oexp, ex.data(), ex.size() * sizeof(int2));
+    std::vector<int> face(o.face_imp);
+    while (face.size() % 4) face.push_back(0);
+    h.face_total = (int)face.size();
+    up((void **)&td.d_oface, face.data(), face.size() * sizeof(int));
+    h.imp = td.d_oimp;
+    h.exp = td.d_oexp;
+    h.face = td.d_oface;
+    up((void **)&td.d_oct, &h, sizeof h);
+    int rc = e == cudaSuccess ? upload_reuse(t, &td.d_reuse) : SP_OK;
+    if (e != cudaSuccess || rc != SP_OK) {
+        cudaFree(td.d_oimp);
+        cudaFree(td.d_oexp);
+        cudaFree(td.d_oface);
+        cudaFree(td.d_oct);
+        cudaFree(td.d_reuse);
+        return e == cudaErrorMemoryAllocation || rc == SP_ENOMEM ? SP_ENOMEM : (rc != SP_OK ? rc : SP_ECUDA);
+    }
+    td.dev.reuse = td.d_reuse;
+    g->tables[32] = td;
+    return SP_OK;
+}
+
 int build_device_tables(sp_grid *g, int B)
 {
     if (g->tables.count(B)) return SP_OK;
@@ -276,8 +458,10 @@ int build_device_tables(sp_grid *g, int B)
     std::string err = sp::build_tables(B, &td.host);
     if (!err.empty()) return SP_EINVAL;
     const sp::TileTables &t = td.host;
+    if (B == 32) return build_octant_device_tables(g, &td);
     // the device tables and index packing serve bases up to 16
     if (t.P * t.P * t.P > 8192 || t.B * t.B * t.B > 4096 || t.H > sp::kMaxHDev) return SP_EINVAL;
+    for (int S = 0; S < sp::kTypes; ++S) td.region_mb_size[S] = t.mb_size[S];
     // the seeds (band-0 regions without predecessors) must be the leading
     // region types: the queue reset takes the first Jtot * seed_types ids
     td.seed_types = 0;
@@ -412,6 +596,10 @@ void free_plan(sp_grid *g)
         cudaFree(kv.second.d_exp);
         cudaFree(kv.second.d_reuse);
         cudaFree(kv.second.d_dev);
+        cudaFree(kv.second.d_oimp);
+        cudaFree(kv.second.d_oexp);
+        cudaFree(kv.second.d_oface);
+        cudaFree(kv.second.d_oct);
     }
     g->tables.clear();
     g->groups.clear();
@@ -436,7 +624,7 @@ int choose_B(const sp_params &p, int requested)
     return -1;
 }
 
-int default_threads(int B) { return B <= 8 ? 64 : 384; }
+int default_threads(int B) { return B <= 8 ? 64 : B == 32 ? sp::region_oct_workers() : 384; }
 
 // Pending device error of the last region launch -> SP code.
 int collect_device_error(sp_grid *g)
@@ -537,7 +725,9 @@ int enqueue_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int6
         }
         if (e == cudaSuccess) e = sp::launch_reset(a, g->stream);
         if (timing && gi == 0) mark(g->ev[1]);
-        if (e == cudaSuccess) e = sp::launch_region(a, gl.cfg.threads, gl.cfg.B, gl.cfg.smem, gl.cfg.grid, g->stream);
+        if (e == cudaSuccess)
+            e = gl.cfg.B == 32 ? sp::launch_region_oct(a, gl.cfg.smem, gl.cfg.grid / 8, g->stream)
+                               : sp::launch_region(a, gl.cfg.threads, gl.cfg.B, gl.cfg.smem, gl.cfg.grid, g->stream);
     }
     if (groups.empty() && timing) mark(g->ev[1]);
     if (timing) mark(g->ev[2]);
@@ -641,6 +831,19 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
     for (auto it = g->tables.rbegin(); it != g->tables.rend(); ++it) {
         GroupCfg c;
         c.B = it->first;
+        if (it->second.octant) {
+            // base 32: one region per 8-CTA cluster, as many clusters as fit
+            c.threads = sp::region_oct_workers();
+            c.smem = sp::region_oct_smem_bytes(it->second.oct_dev.imp_n, it->second.oct_dev.face_total);
+            if (c.smem > 227 * 1024) return SP_EINVAL;
+            int clusters = 0;
+            e = sp::region_oct_clusters(c.smem, &clusters);
+            if (e != cudaSuccess || clusters < 1) return SP_EINVAL;
+            c.ctas_per_sm = 1;
+            c.grid = 8 * clusters;
+            g->groups.push_back(c);
+            continue;
+        }
         const bool mine = threads && (!largest_only || c.B == g->max_B);
         c.threads = mine ? threads : default_threads(c.B);
         int n_in = 0;
@@ -662,13 +865,13 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
     g->mb_elems.assign(g->n_sims, 0);
     g->mb_type_off.assign(g->n_sims, {});
     for (int s = 0; s < g->n_sims; ++s) {
-        const sp::TileTables &t = g->tables[g->B[s]].host;
+        const TablesOnDevice &td = g->tables[g->B[s]];
         long long J = 1;
         for (int d = 0; d < 3; ++d) J *= g->p[s].n[d] / g->B[s];
         long long off = 0;
         for (int S = 0; S < sp::kTypes; ++S) {
             g->mb_type_off[s][S] = off;
-            off += J * t.mb_size[S];
+            off += J * td.region_mb_size[S];
         }
         const int slots = g->mb_slots;
         g->mb_elems[s] = off;
@@ -701,11 +904,12 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
 {
     std::vector<std::vector<int>> policies;
     if (base_B == SP_AUTOTUNE) {
-        for (int pref : {8, 16}) {
+        for (int pref : {8, 16, 32}) {
             std::vector<int> Bs(g->n_sims);
             bool ok = true;
             for (int s = 0; s < g->n_sims && ok; ++s) {
                 Bs[s] = choose_B(g->p[s], pref);
+                if (Bs[s] < 0 && pref > 16) Bs[s] = choose_B(g->p[s], 16);
                 if (Bs[s] < 0) Bs[s] = choose_B(g->p[s], 8);
                 ok = Bs[s] > 0;
             }
@@ -880,7 +1084,8 @@ int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t orde
 {
     if (!g) return SP_EINVAL;
     // bases are powers of two: the kernels decode cell indices with shifts
-    if (base_B != 0 && base_B != SP_AUTOTUNE && base_B != 4 && base_B != 8 && base_B != 16) return SP_EINVAL;
+    if (base_B != 0 && base_B != SP_AUTOTUNE && base_B != 4 && base_B != 8 && base_B != 16 && base_B != 32)
+        return SP_EINVAL;
     if (block_shape != 0 && block_shape != SP_AUTOTUNE && !valid_threads(block_shape)) return SP_EINVAL;
     if (order != SP_ORDER_STATIC && order != SP_ORDER_LEARNED) return SP_EINVAL;
     g->tune = TuneReport();
@@ -991,6 +1196,7 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
                 for (int S = 0; S < sp::kTypes; ++S) d.mb_type_off[S] = g->mb_type_off[s][S];
                 d.tab = g->tables[B].d_dev;
                 d.tab_index = 0;
+                d.oct = g->tables[B].octant ? g->tables[B].d_oct : nullptr;
                 g->last_tile_base[s] = all_total + total;
                 g->last_tiles[s] = d.tiles;
                 total += d.tiles;
@@ -1215,8 +1421,20 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
     }
     case SP_SURF_PLAN: {
         if (dst_bytes < sizeof(sp_plan_info) || !g->planned) return SP_EINVAL;
-        const sp::TileTables &t = g->tables[g->B[sim]].host;
-        sp::PlanStats ps = sp::plan_stats(t, p.n);
+        const TablesOnDevice &td = g->tables[g->B[sim]];
+        sp::PlanStats ps = sp::plan_stats(td.host, p.n);
+        if (td.octant) {  // the cluster kernel moves the octant tables' traffic
+            int64_t J = 1, upd = 0, rd = 0, wr = 0;
+            for (int d = 0; d < 3; ++d) J *= p.n[d] / td.oct.B;
+            for (int S = 0; S < sp::kTypes; ++S) {
+                upd += td.oct.updates[S];
+                rd += td.oct.bytes_read[S];
+                wr += td.oct.bytes_written[S];
+            }
+            ps.bytes_read_per_band = J * rd;
+            ps.bytes_written_per_band = J * wr;
+            ps.bytes_per_update = (double)(rd + wr) / (double)upd;
+        }
         sp_plan_info info;
         std::memset(&info, 0, sizeof info);
         info.base_B = g->B[sim];

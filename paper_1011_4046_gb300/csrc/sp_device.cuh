@@ -64,6 +64,49 @@ struct alignas(16) TablesDev {
     const int2 *exp;            // all export entries, global memory
 };
 
+// Levels per band of the octant (cluster) kernel: bases up to 32.
+constexpr int kMaxHOct = 16;
+
+// Geometry and routing of one region type for the cluster kernel, in the
+// mirrored coordinates of one octant (planner.h, OctTables): buffer side
+// P = H + 2, u = dist + 1.
+struct alignas(16) OctTypeMeta {
+    int levels, mb_size;        // levels; float2 elements of one octant mailbox
+    int base_cols, base_runs;   // band-base copy in (column, run of up to 4 cells along z) units
+    float rcp_cols, rcp_base0;  // 1 / columns, 1 / width of the base box along x
+    int pad0, pad1;
+    Box3 base_phi, base_pc;
+    // widths of the active corner box at level k (0 = none) and the FP32
+    // reciprocals of its extents along x and y (exact decode, fdiv)
+    unsigned char w[kMaxHOct + 2][4];
+    float rcp_w[kMaxHOct + 2][2];
+    // face-first order of level k: 1 / w1, 1 / (w0 - 1), 1 / (w1 - 1) (0 where the width is 0)
+    float rcp_f[kMaxHOct + 2][3];
+    int pad2;
+    int imp_full_off[kMaxHOct], imp_full_n[kMaxHOct];
+    int imp_phi_off[kMaxHOct], imp_phi_n[kMaxHOct];
+    int mb_level_off[kMaxHOct];
+    int exp_off[kMaxHOct], exp_n[kMaxHOct];
+    int face_off[kMaxHOct], face_n[kMaxHOct];
+    int xbytes[kMaxHOct + 2];   // bytes of inner faces an octant receives before level k
+};
+
+// Everything the cluster kernel reads for one base (B = 32): per-type
+// geometry (copied into shared memory once per launch), the 16-bit import
+// lists (shared memory), the export entries and imported face cells
+// (global memory, read through L1).  Export entry: x = phi index (13 bits) |
+// (pi, c) index (12 bits) << 13 | consumer code (type | G << 3) << 25 |
+// has (pi, c) << 31; y = phi offset | (pi, c) offset << 16 in the consumer
+// octant's mailbox (float2 units).  Face entry: phi index | axis mask << 16.
+struct alignas(16) TablesOct {
+    int B, H, P, imp_n;
+    OctTypeMeta type[kTypes];
+    const unsigned short *imp;
+    const int2 *exp;
+    const int *face;  // all face entries (face_total, a multiple of 4), copied into shared memory
+    int face_total, pad3;
+};
+
 // One simulation of a batch, as the persistent region kernel sees it.
 struct alignas(16) SimDev {
     int n[3];
@@ -86,6 +129,10 @@ struct alignas(16) SimDev {
     // 1: one mailbox slot for every band; a region also waits for the
     // previous band's readers of the mailboxes it writes (reuse edges)
     int mb_reuse;
+    // base 32: the octant tables of the cluster kernel (the dependency
+    // pattern stays in tab); nullptr otherwise
+    const TablesOct *oct;
+    long long pad_oct;
 };
 
 // Priority buckets of the learned ordering (bucket 0 is queued first).
@@ -129,6 +176,7 @@ struct RegionArgs {
 };
 
 static_assert(sizeof(TablesDev) % 16 == 0, "tables are copied in 16-byte units");
+static_assert(sizeof(TablesOct) % 16 == 0, "octant tables are copied in 16-byte units");
 static_assert(sizeof(SimDev) % 16 == 0, "descriptors are copied in 16-byte units");
 static_assert(sizeof(LevelCoef) == 16, "coefficients are copied in 16-byte units");
 
@@ -248,6 +296,104 @@ __device__ __forceinline__ void cp_async_wait_pending(int n)
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
 }
+
+// ---- thread-block clusters: distributed shared memory and mbarriers ----
+__device__ __forceinline__ unsigned cluster_ctarank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned map_shared(const void *p, unsigned rank)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init_cluster()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// This thread's arrival on a local mbarrier, announcing `bytes` of
+// asynchronous stores the current phase also waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(a), "r"(bytes)
+                 : "memory");
+    asm volatile("" ::"l"(state));
+}
+
+// One poll of the phase with parity `parity` (true once it completed);
+// acquire at cluster scope, so the stores other CTAs made into this CTA's
+// shared memory for that phase are visible to the caller.
+__device__ __forceinline__ bool mbar_test_parity_cluster(unsigned long long *bar, unsigned parity)
+{
+    unsigned a = (unsigned)__cvta_generic_to_shared(bar), ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 8-byte store into another CTA's shared memory (cluster address `raddr`)
+// that completes as 8 bytes of transaction count on that CTA's mbarrier
+// `rbar` (cluster address).
+__device__ __forceinline__ void st_async_f2(unsigned raddr, float2 v, unsigned rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(v.x), "f"(v.y), "r"(rbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_release_cluster_shared(unsigned raddr, int v)
+{
+    asm volatile("st.release.cluster.shared::cluster.s32 [%0], %1;" ::"r"(raddr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_shared_int4(unsigned raddr, int4 v)
+{
+    asm volatile("st.shared::cluster.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(raddr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_cluster_shared(const int *p)
+{
+    int v;
+    unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.acquire.cluster.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_cluster_add(unsigned raddr, int v)
+{
+    asm volatile("red.release.cluster.shared::cluster.add.s32 [%0], %1;" ::"r"(raddr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 #endif
 

@@ -22,3 +22,12 @@ cudaError_t launch_winding(const float2 *phi, const int n[3], signed char *w, un
                            cudaStream_t st);
 
 }  // namespace sp
+
+namespace sp {
+// The base-32 cluster kernel (sp_octant.cu): shared memory per CTA, the
+// number of 8-CTA clusters that fit the device, its launch and worker count.
+size_t region_oct_smem_bytes(int imp_units, int face_units);
+cudaError_t region_oct_clusters(size_t smem, int *clusters);
+cudaError_t launch_region_oct(const RegionArgs &a, size_t smem, int clusters, cudaStream_t st);
+int region_oct_workers();
+}  // namespace sp
