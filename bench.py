@@ -86,7 +86,8 @@ def peaks():
 # the region kernel and everything that shapes what it moves (tables, launch)
 KERNEL_SOURCES = ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
                   "paper_1011_4046_gb300/csrc/sp_update.h", "paper_1011_4046_gb300/csrc/sp_api.cu",
-                  "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h"]
+                  "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h",
+                  "paper_1011_4046_gb300/csrc/sp_region_common.cuh"]
 
 
 def ncu_traffic(base, updates_per_launch):
