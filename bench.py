@@ -62,8 +62,12 @@ MONO_BYTES_PER_UPDATE = 48.0
 # On-chip (shared-memory) bytes per site-update of the region kernel: seven
 # phi reads (8 B) and one phi write, one (pi, c) read and write (16 B each).
 SMEM_BYTES_PER_UPDATE = 7 * 8 + 8 + 2 * 16
-# Shared-memory bandwidth of one GB300, nominal: 128 B per clock per SM.
+# Shared-memory bandwidth of one GB300, nominal: 128 B per clock per SM (the
+# fallback when the measured peak is not available).
 SMS, SMEM_BYTES_PER_CLOCK = 152, 128
+# FP32 flops of one site update (the Laplacian sums, force, kick and
+# Kahan-compensated drift of both components; a fused multiply-add counts 2).
+FLOP_PER_UPDATE = 41
 METRIC = "lattice site-updates/s"
 
 
@@ -178,16 +182,30 @@ def parse_clocks(lines):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def smem_roofline(updates, kernel_ms, clk):
+def smem_roofline(updates, kernel_ms, clk, measured_gbs=None):
     """On-chip line of the region kernel: its shared-memory bytes per launch
-    over the launch time, against the nominal bandwidth at the SM clock
-    sampled during the timed region (or the maximum clock)."""
-    mhz = (clk or {}).get("sm_mhz") or 2070.0
-    peak = SMS * SMEM_BYTES_PER_CLOCK * mhz * 1e6 / 1e9
+    over the launch time, against the device's measured shared-memory read
+    bandwidth (sp_measure_peaks) when given, else the nominal bandwidth at the
+    SM clock sampled during the timed region (or the maximum clock)."""
     achieved = SMEM_BYTES_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e9
+    if measured_gbs:
+        peak, kind = measured_gbs, "measured (sp_measure_peaks: conflict-free 16-byte shared-memory reads, all SMs)"
+    else:
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak = SMS * SMEM_BYTES_PER_CLOCK * mhz * 1e6 / 1e9
+        kind = f"nominal (152 SMs x 128 B/clock at {mhz:.0f} MHz)"
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": f"nominal (152 SMs x 128 B/clock at {mhz:.0f} MHz)",
-            "bytes_per_update": SMEM_BYTES_PER_UPDATE}
+            "peak_kind": kind, "bytes_per_update": SMEM_BYTES_PER_UPDATE}
+
+
+def alu_roofline(updates, kernel_ms, measured_tflops):
+    """FP32 line of the region kernel: FLOP_PER_UPDATE flops per site-update
+    (fused multiply-adds counted as two) over the launch time, against the
+    measured FP32 FMA throughput."""
+    achieved = FLOP_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": measured_tflops, "unit": "TFLOP/s",
+            "frac": achieved / measured_tflops, "peak_kind": "measured (sp_measure_peaks: FP32 FMA chains)",
+            "flop_per_update": FLOP_PER_UPDATE}
 
 
 def trace_utilisation(trace, ctas):
@@ -288,6 +306,7 @@ def run_grid(args, w, extra=None):
         torch.cuda.synchronize()
 
     N, STEPS, PER, B = w["N"], w["STEPS"], w["PER_STEP"], w["B"]
+    peaks_onchip = sp.sp_measure_peaks(stream.cuda_stream)
     n = (N, N, N)
     sites = N ** 3
     p = sp.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
@@ -453,7 +472,9 @@ def run_grid(args, w, extra=None):
                      "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
                      "design_bytes_per_update": info["bytes_per_update"],
                      "traffic_from": "profiles/region_kernel_traffic.json scaled by site-updates per launch"},
-        "roofline_smem": smem_roofline(updates, kern_mean, clk),
+        "roofline_smem": smem_roofline(updates, kern_mean, clk, peaks_onchip[0]),
+        "roofline_alu": alu_roofline(updates, kern_mean, peaks_onchip[1]),
+        "measured_onchip_peaks": {"smem_gbs": peaks_onchip[0], "fp32_tflops": peaks_onchip[1]},
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,  # per bench step: queue reset + persistent region kernel
         "utilisation": utilisation,

@@ -322,6 +322,19 @@ int sp_model_load(const char *path, void *cuda_stream, sp_model **out);
 int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev, int64_t level0, int64_t n_steps,
                      void *cuda_stream);
 
+/*
+ * sp_measure_peaks -- measured on-chip peaks of the current device, for the
+ * roofline lines of the region kernel (its shared-memory traffic and its
+ * FP32 arithmetic; the HBM line uses a measured copy bandwidth): the
+ * shared-memory read bandwidth of the whole device (GB/s: every SM reading
+ * 16-byte words without bank conflicts) and the FP32 fused multiply-add
+ * throughput (TFLOP/s, 2 flops per FMA).  Each is one timed launch after a
+ * warm-up on cuda_stream; the call synchronises.  The paper has no
+ * counterpart (its cost figures are CPU times, Sec. 6).
+ * Errors: SP_EINVAL (NULL output), SP_ENOMEM, SP_ECUDA.
+ */
+int sp_measure_peaks(void *cuda_stream, double *smem_gbs, double *fp32_tflops);
+
 /* sp_destroy -- free everything the library allocated (not caller state):
  * plan, mailboxes, work queue, scratch.  Paper Sec. 4: when the pool of
  * regions is empty the manager retires its workers; this is the host-side end

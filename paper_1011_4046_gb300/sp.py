@@ -157,6 +157,7 @@ def load(build_if_missing: bool = False):
         lib.sp_destroy.argtypes = [vp]
         lib.sp_sweep_noalloc.argtypes = [ctypes.POINTER(sp_params), vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
         lib.sp_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+        lib.sp_measure_peaks.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.sp_strerror.argtypes = [ctypes.c_int]
         lib.sp_strerror.restype = ctypes.c_char_p
         fp = ctypes.POINTER(ctypes.c_float)
@@ -174,7 +175,7 @@ def load(build_if_missing: bool = False):
         for f in ("sp_grid_create", "sp_region_plan", "sp_evolve", "sp_read_surface", "sp_write_surface",
                   "sp_destroy", "sp_sweep_noalloc", "sp_model_create", "sp_model_destroy", "sp_model_get_params",
                   "sp_model_set_params", "sp_model_predict", "sp_model_grad", "sp_model_adam_step", "sp_model_train",
-                  "sp_model_save", "sp_model_load", "sp_set_option"):
+                  "sp_model_save", "sp_model_load", "sp_set_option", "sp_measure_peaks"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -224,6 +225,14 @@ def sp_sweep_noalloc(params, phi_ptr, pic_ptr, level0, n_steps, stream=0):
     """Whole-grid steps with no memory allocation (see include/sp.h)."""
     return load().sp_sweep_noalloc(ctypes.byref(params), ctypes.c_void_p(int(phi_ptr)), ctypes.c_void_p(int(pic_ptr)),
                                    int(level0), int(n_steps), ctypes.c_void_p(int(stream)))
+
+
+def sp_measure_peaks(stream=0):
+    """(shared-memory GB/s, FP32 TFLOP/s) measured on the current device."""
+    smem, fp32 = ctypes.c_double(), ctypes.c_double()
+    rc = load().sp_measure_peaks(ctypes.c_void_p(int(stream)), ctypes.byref(smem), ctypes.byref(fp32))
+    _check(rc, "sp_measure_peaks")
+    return smem.value, fp32.value
 
 
 # ------------------------------------------------------------ helpers

@@ -26,6 +26,14 @@ def test_smem_line_uses_the_sampled_clock():
     assert r["peak"] == pytest.approx(152 * 128 * 1e9 / 1e9)
     assert r["achieved"] == pytest.approx(96 * 1e6 / 1e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    m = bench.smem_roofline(1_000_000, 1.0, {"sm_mhz": 1000.0}, measured_gbs=30000.0)
+    assert m["peak"] == 30000.0 and m["peak_kind"].startswith("measured")
+
+
+def test_alu_line_counts_the_site_update_flops():
+    r = bench.alu_roofline(2_000_000, 2.0, 50.0)
+    assert r["achieved"] == pytest.approx(41 * 2e6 / 2e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 50.0) and r["bound"] == "alu"
 
 
 def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):

@@ -162,68 +162,100 @@ def _region_samples(g, info, steps):
     return f, np.log(us).astype(np.float32)
 
 
+def _train_cost_model(tmp_path, s):
+    """The cost network trained on measured region times of the plain-method
+    and 128^3 matter-era workloads (features from SP_FEATURES, times from
+    SP_TRACE); returns (model file, samples, final loss)."""
+    Xs, ys = [], []
+    for n, nu, B, steps, kind in ((32, 0.0, 8, 64, "gaussian"), (128, 2.0, 16, 256, "phase")):
+        tau0 = 10.0 if nu > 0 else 1.0
+        p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=nu, tau0=tau0, tau_ref=tau0 + steps * 0.25)
+        st = inputs.initial_state((n, n, n), 0, kind, sigma=0.3)
+        g = sp.Grid([p], stream=s)
+        try:
+            g.plan(base_B=B)
+            info = g.plan_info(0)
+            for rep in range(2):
+                g.write_state(0, *st)
+                g.evolve(steps, sp.SP_RESTART | sp.SP_TRACE | sp.SP_FEATURES)
+                f, t = _region_samples(g, info, steps)
+                assert np.all(np.isfinite(f)) and f.shape[1] == 16
+                Xs.append(f)
+                ys.append(t)
+        finally:
+            g.close()
+    X = np.concatenate(Xs)
+    y = np.concatenate(ys)
+    xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    m = sp.Model(seed=1, stream=s)
+    try:
+        losses = m.train(xd.data_ptr(), yd.data_ptr(), len(y), epochs=8, batch=256, lr=1e-3, order_seed=1)
+        path = str(tmp_path / "cost_model.bin")
+        m.save(path)
+    finally:
+        m.close()
+    assert float(np.mean(losses[-50:])) < float(np.mean(losses[:50]))
+    return path, len(y), float(np.mean(losses[-50:]))
+
+
+def _order_ab(p, st, steps, B, path, s, reps=4):
+    """The same run in static and in learned order: final states and the
+    median time (CUDA events around the call's launches) after one warm-up."""
+    res, times = {}, {}
+    for order in (sp.SP_ORDER_STATIC, sp.SP_ORDER_LEARNED):
+        g = sp.Grid([p], stream=s)
+        try:
+            g.plan(base_B=B, order=order, model_path=path if order == sp.SP_ORDER_LEARNED else None)
+            ms = []
+            for rep in range(reps):
+                g.write_state(0, *st)
+                g.evolve(steps, sp.SP_RESTART | sp.SP_TIMING)
+                ms.append(sum(g.timing()))
+            res[order] = g.read_state(0)
+            times[order] = float(np.median(ms[1:]))
+        finally:
+            g.close()
+    for a, b in zip(res[sp.SP_ORDER_STATIC], res[sp.SP_ORDER_LEARNED]):
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    return times[sp.SP_ORDER_STATIC], times[sp.SP_ORDER_LEARNED]
+
+
 def test_learned_order_is_bit_identical_and_timed(tmp_path):
     """Train the network on measured region times of the plain-method and
-    128^3 matter-era workloads (features from SP_FEATURES, times from
-    SP_TRACE), then evolve the 128^3 workload in static and in learned order:
-    the fields are bit-identical; both times are printed."""
+    128^3 matter-era workloads, then evolve the 128^3 workload in static and
+    in learned order: the fields are bit-identical; both times are printed."""
     s = torch.cuda.Stream()
-    Xs, ys = [], []
     with torch.cuda.stream(s):
-        for n, nu, B, steps, kind in ((32, 0.0, 8, 64, "gaussian"), (128, 2.0, 16, 256, "phase")):
-            tau0 = 10.0 if nu > 0 else 1.0
-            p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=nu, tau0=tau0, tau_ref=tau0 + steps * 0.25)
-            st = inputs.initial_state((n, n, n), 0, kind, sigma=0.3)
-            g = sp.Grid([p], stream=s)
-            try:
-                g.plan(base_B=B)
-                info = g.plan_info(0)
-                for rep in range(2):
-                    g.write_state(0, *st)
-                    g.evolve(steps, sp.SP_RESTART | sp.SP_TRACE | sp.SP_FEATURES)
-                    f, t = _region_samples(g, info, steps)
-                    assert np.all(np.isfinite(f)) and f.shape[1] == 16
-                    Xs.append(f)
-                    ys.append(t)
-            finally:
-                g.close()
-        X = np.concatenate(Xs)
-        y = np.concatenate(ys)
-        xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
-        m = sp.Model(seed=1, stream=s)
-        try:
-            losses = m.train(xd.data_ptr(), yd.data_ptr(), len(y), epochs=8, batch=256, lr=1e-3, order_seed=1)
-            path = str(tmp_path / "cost_model.bin")
-            m.save(path)
-        finally:
-            m.close()
-        assert float(np.mean(losses[-50:])) < float(np.mean(losses[:50]))
-
+        path, samples, loss = _train_cost_model(tmp_path, s)
         n, steps = 128, 256
         p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=2.0, tau0=10.0, tau_ref=10.0 + steps * 0.25)
         st = inputs.initial_state((n, n, n), 0, "phase")
-        res, times = {}, {}
-        for order in (sp.SP_ORDER_STATIC, sp.SP_ORDER_LEARNED):
-            g = sp.Grid([p], stream=s)
-            try:
-                g.plan(base_B=16, order=order, model_path=path if order == sp.SP_ORDER_LEARNED else None)
-                ms = []
-                for rep in range(4):
-                    g.write_state(0, *st)
-                    g.evolve(steps, sp.SP_RESTART | sp.SP_TIMING)
-                    ms.append(sum(g.timing()))
-                res[order] = g.read_state(0)
-                times[order] = float(np.median(ms[1:]))
-            finally:
-                g.close()
-    for a, b in zip(res[sp.SP_ORDER_STATIC], res[sp.SP_ORDER_LEARNED]):
-        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
-    gain = times[sp.SP_ORDER_STATIC] / times[sp.SP_ORDER_LEARNED]
-    print(f"\n128^3 x 256: static order {times[sp.SP_ORDER_STATIC]:.3f} ms, learned order "
-          f"{times[sp.SP_ORDER_LEARNED]:.3f} ms, gain x{gain:.3f}")
+        t_static, t_learned = _order_ab(p, st, steps, 16, path, s)
+    gain = t_static / t_learned
+    print(f"\n128^3 x 256: static order {t_static:.3f} ms, learned order {t_learned:.3f} ms, gain x{gain:.3f}")
     out = os.environ.get("SP_LEARNED_ORDER_REPORT")
     if out:
         with open(out, "w") as fh:
-            fh.write(f"static_ms {times[sp.SP_ORDER_STATIC]:.4f}\nlearned_ms {times[sp.SP_ORDER_LEARNED]:.4f}\n"
-                     f"gain {gain:.4f}\nsamples {len(y)}\nfinal_loss {float(np.mean(losses[-50:])):.5f}\n")
+            fh.write(f"static_ms {t_static:.4f}\nlearned_ms {t_learned:.4f}\n"
+                     f"gain {gain:.4f}\nsamples {samples}\nfinal_loss {loss:.5f}\n")
     assert gain > 0.5  # the learned schedule may not be pathological
+
+
+def test_learned_order_on_the_512_damped_workload(tmp_path):
+    """The 512^3 workload with cost-model scheduling: random phases, 64 damped
+    levels then 1024 matter-era steps, base 16, the network trained on the
+    region times of the plain-method and 128^3 workloads, against static DAG
+    order: bit-identical fields, both times printed (the comparison the
+    workload asks for)."""
+    n, damp, steps = 512, 64, 1024
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        path, _, _ = _train_cost_model(tmp_path, s)
+        p = sp.make_params(n, dt=0.25, lam=2.0, eta=1.0, nu=2.0, tau0=10.0, tau_ref=10.0 + steps * 0.25,
+                           damp_steps=damp)
+        st = inputs.initial_state((n, n, n), 0, "phase")
+        t_static, t_learned = _order_ab(p, st, damp + steps, 16, path, s, reps=2)
+    gain = t_static / t_learned
+    print(f"\n512^3 x (64 damped + 1024): static order {t_static:.1f} ms, learned order {t_learned:.1f} ms, "
+          f"gain x{gain:.3f}")
+    assert gain > 0.5
