@@ -2,12 +2,14 @@
 // uses, for its roofline lines: shared-memory read bandwidth and FP32 FMA
 // throughput of the whole device (HBM bandwidth is measured elsewhere).
 //
-// Shared memory: every thread of a full-occupancy grid reads 16-byte words
-// of a 32 KB shared array, a warp's 32 reads covering 512 consecutive bytes
-// (four wavefronts, no bank conflict), folding them into an XOR so that no
-// read can be dropped.  FP32: eight independent fused multiply-add chains
-// per thread.  Both are timed with CUDA events around one launch after a
-// warm-up launch; the result is written so the compiler must keep the work.
+// Shared memory: every thread of a full-occupancy grid reads eight distinct
+// 16-byte words of a 32 KB shared array per step, a warp's 32 reads covering
+// 512 consecutive bytes (four wavefronts, no bank conflict), folding them
+// into an XOR so that no read can be dropped (the offsets differ, so no two
+// reads of a step can be merged, and they move every step).  FP32: eight
+// independent fused multiply-add chains per thread.  Both are timed with CUDA
+// events around one launch after a warm-up launch; the result is written so
+// the compiler must keep the work.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,7 +32,7 @@ __global__ void __launch_bounds__(kPeakThreads) smem_read_kernel(int iters, unsi
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const float4 v = buf[(idx + u * kPeakThreads) & (kSmemWords - 1)];
+            const float4 v = buf[(idx + u * (kSmemWords / 8)) & (kSmemWords - 1)];  // eight distinct words
             acc ^= __float_as_uint(v.x) ^ __float_as_uint(v.y) ^ __float_as_uint(v.z) ^ __float_as_uint(v.w);
         }
         idx = (idx + 32) & (kSmemWords - 1);
