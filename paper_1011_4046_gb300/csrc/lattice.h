@@ -1,0 +1,173 @@
+// lattice.h -- the paper's own region geometry: a lattice of 4-cubes with
+// time along the main diagonal (Sec. 2, Figs. 2-5), planned for in-place
+// evolution of the state arrays.
+//
+// Geometry.  With the 7-point stencil, the value at (t, x) depends on
+// (t-1, x) and (t-1, x +- e_d).  The four forms
+//
+//   f_i(t, x) = t + sigma_i . x,   sigma = (1,1,1), (1,-1,-1), (-1,1,-1), (-1,-1,1)
+//
+// change along such a dependency by 1 - sigma_i . d, which is 0, 1 or 2:
+// none of them ever decreases.  So the cells with floor(f_i / 4s) = n_i
+// (n in Z^4) form regions that read only from regions n' <= n (componentwise)
+// and feed only regions n' >= n: each region has four initial faces
+// (f_i = 4s n_i) and four final ones.  These are the paper's 4-cubes with the
+// generators (+-1/2, +-1/2, +-1/2, 1/2) scaled by 4s; under the 7-point
+// stencil's cone (one cell per step along every axis) their faces are
+// characteristic as they are, with no rescaling of time.  A region holds
+// 16 s^4 site-updates over 4s levels; all regions are translates of one
+// another (one congruent type).  In local coordinates -- level k from the
+// region's bottom vertex and cell offset r from its centre -- the region's
+// cells at level k are
+//
+//   { r : -k <= sigma_i . r <= 4s - 1 - k  for i = 1..4 },
+//
+// a tetrahedron growing from one cell (k < s), an octahedron-like middle and
+// a shrinking inverted tetrahedron (k >= 3s).
+//
+// Layers (Sec. 2, Fig. 2).  Region n starts at level s (n_1 + n_2 + n_3 + n_4)
+// (its layer L times s) and has its centre at
+//   s (n1 + n2 - n3 - n4, n1 - n2 + n3 - n4, n1 - n2 - n3 + n4).
+// Regions of one layer start together; four layers are active at any level;
+// region n's predecessors are n - e_i (layer L - 1, centres shifted by
+// -s(1,1,1), s(-1,1,1), s(1,-1,1), s(1,1,-1)), its successors n + e_i.
+// Dependencies that cross two or more faces at once (a corner or an edge)
+// come from regions n - e_i - e_j ..., which precede n through the four face
+// predecessors.
+//
+// Periodicity (Sec. 2.2).  On a periodic grid of sides N_d = 4 s M_d a
+// centre is taken mod N_d; a layer then holds 4 M_x M_y M_z regions (the
+// centres form a face-centred cubic lattice of cube side 4s).
+//
+// In-place state.  Regions read and write the state arrays themselves: phi at
+// level t lives in buffer t mod 2 (two phi arrays), (pi, c) in one array.
+// A region imports phi(t-1, y) and (pi, c)(t-1, y) it does not compute and
+// exports every value some other region (or the end of the call) needs.
+// This is race-free by the monotonicity above: a write that could clobber
+// a read, phi(t+1, y) over phi(t-1, y) or (pi, c) at a later level over
+// (pi, c)(t-1, y), is made by the reading region itself (later) or by one of
+// its successors, and a value read is written by the reader's predecessor.
+// Two regions of one layer may write phi(t, y) and read phi(t-1, y) at the
+// same time: these sit in different buffers.  No mailbox is needed.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#if defined(__CUDACC__)
+#define LAT_HD __host__ __device__ __forceinline__
+#else
+#define LAT_HD inline
+#endif
+
+namespace sp {
+
+constexpr int kLatMinS = 1;
+constexpr int kLatMaxS = 6;  // slot indices are 12 bits, coordinates 5 bits per axis
+
+// Cell entry of one computed cell (64 bits), the kernel's per-level work list:
+//   bits  0..11 shared-memory slot of the cell (its phi in both parity buffers)
+//   bits 12..23 index of its (pi, c) pair (footprint cells only)
+//   bits 24..31 slot(y - 1) - slot (signed 8 bits); bits 32..39 slot(y + 1) - slot
+//   bits 40..49 slot(z - 1) - slot (signed 10 bits); bits 50..59 slot(z + 1) - slot
+//   bit 60 export phi at this level; bit 61 export (pi, c) at this level
+// x neighbours are slot - 1 and slot + 1 (rows are contiguous in x).
+constexpr int kLatCellSlotBits = 12;
+constexpr uint64_t kLatExpPhi = 1ull << 60;
+constexpr uint64_t kLatExpPc = 1ull << 61;
+
+// Import entry (16 bits): slot | full << 15.  A full import loads phi(k-1)
+// and (pi, c)(k-1) of a cell entering the region at level k; otherwise only
+// phi(k-1) of a neighbour outside the region.
+constexpr uint16_t kLatImpFull = 1u << 15;
+
+// Slot record (32 bits): (rx + 2s) | (ry + 2s) << 5 | (rz + 2s) << 10 |
+// (pi, c) index << 15 | footprint << 27.  Offsets r are relative to the
+// region's centre, |r_d| <= 2s.
+struct LatticeTables {
+    int s = 0, K = 0;           // K = 4s levels per region
+    int n_slots = 0, n_foot = 0;  // phi slots (footprint + halo, row layout), (pi, c) slots
+    std::vector<uint64_t> cell;   // level k: cell[cell_off[k] .. cell_off[k+1])
+    std::vector<int32_t> cell_off;  // K + 1
+    std::vector<uint16_t> imp;    // before level k: imp[imp_off[k] .. imp_off[k+1]), ascending slots
+    std::vector<int32_t> imp_off;   // K + 1
+    std::vector<uint32_t> slot_rec;  // n_slots
+    // one whole region: site-updates, bytes read and written (this design)
+    int64_t updates = 0, bytes_read = 0, bytes_written = 0;
+    int64_t imports_full = 0, imports_phi = 0, exports_phi = 0, exports_pc = 0;
+    int max_level_cells = 0;
+};
+
+// Builds the tables of lattice size s (kLatMinS..kLatMaxS) and checks them:
+// the cell count 16 s^4; that every value a level reads is in shared memory
+// from the previous level or imported before it; that every import is
+// exported by the region that computes it (located through the lattice);
+// the packing ranges.  Returns an empty string on success.
+std::string build_lattice_tables(int s, LatticeTables *t);
+
+// ---- the regions of one call (host and device) ----
+//
+// A call advances levels t0 + 1 .. t0 + T.  The lattice is aligned to the
+// call: layer L's regions start at relative level tau_b = 1 + s L (tau =
+// t - t0), so layers L = -3 .. floor((T - 1) / s) intersect the call; the
+// first three are cut by the call's first level and the last few by its
+// last level.  A cut region computes its levels k_lo .. k_hi only: it loads
+// its level-(k_lo - 1) cells whole from the state at t0, and at k_hi < 4s - 1
+// exports the whole state of its level-k_hi cells (the state at t0 + T).
+struct LatGeom {
+    int s, M[3];  // N_d = 4 s M_d
+};
+
+LAT_HD int lat_layer_count(int s, int64_t T) { return (int)((T - 1) / s) + 4; }
+LAT_HD int lat_min_layer() { return -3; }
+LAT_HD int64_t lat_per_layer(const LatGeom &g) { return 4ll * g.M[0] * g.M[1] * g.M[2]; }
+
+// Centre of region idx of layer L in units of s: a_d in [0, 4 M_d), all
+// congruent to L mod 2, a_0 + a_1 + a_2 congruent to -L mod 4.
+LAT_HD void lat_centre(const LatGeom &g, int L, int64_t idx, int a[3])
+{
+    const int p = L & 1;
+    const int q = ((-L - 3 * p) & 3) >> 1;  // parity of a'_0 + a'_1 + a'_2, a_d = 2 a'_d + p
+    const int64_t h = idx % g.M[0];
+    const int64_t rest = idx / g.M[0];
+    const int b1 = (int)(rest % (2 * g.M[1]));
+    const int b2 = (int)(rest / (2 * g.M[1]));
+    const int b0 = 2 * (int)h + ((q + b1 + b2) & 1);
+    a[0] = 2 * b0 + p;
+    a[1] = 2 * b1 + p;
+    a[2] = 2 * b2 + p;
+}
+
+// Inverse of lat_centre (a_d reduced mod 4 M_d by the caller).
+LAT_HD int64_t lat_index(const LatGeom &g, const int a[3])
+{
+    const int b0 = a[0] >> 1, b1 = a[1] >> 1, b2 = a[2] >> 1;
+    return ((int64_t)b2 * (2 * g.M[1]) + b1) * g.M[0] + (b0 >> 1);
+}
+
+// Centre shift (units of s) from a region to its predecessor n - e_i; the
+// successor n + e_i is the opposite shift.
+LAT_HD void lat_pred_shift(int i, int d[3])
+{
+    d[0] = (i == 0 || i == 1) ? -1 : 1;
+    d[1] = (i == 0 || i == 2) ? -1 : 1;
+    d[2] = (i == 0 || i == 3) ? -1 : 1;
+}
+
+LAT_HD int lat_wrap(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Index of the predecessor n - e_i of region (L, idx) in layer L - 1.
+LAT_HD int64_t lat_pred(const LatGeom &g, int L, int64_t idx, int i)
+{
+    int a[3], d[3];
+    lat_centre(g, L, idx, a);
+    lat_pred_shift(i, d);
+    for (int k = 0; k < 3; ++k) a[k] = lat_wrap(a[k] + d[k], 4 * g.M[k]);
+    return lat_index(g, a);
+}
+
+}  // namespace sp
