@@ -95,11 +95,28 @@ extern "C" {
                                        with SP_ETIMEOUT after the wait limit; -1 clears */
 #define SP_OPT_GRAPHS 3             /* 1 (default): capture region calls into CUDA graphs on
                                        non-legacy streams; 0: launch directly */
+#define SP_OPT_REGION_SHAPE 5       /* region geometry, applied by the next sp_region_plan:
+                                       SP_SHAPE_SPLIT (default) or SP_SHAPE_LATTICE */
 #define SP_OPT_MAILBOX_SLOTS 4      /* sloped-surface mailboxes, applied by the next sp_region_plan:
                                        1 (default): one slot for every band, with each region also
                                        waiting for the previous band's readers of the mailboxes it
                                        writes; 2: a ring of two band slots, twice the memory
                                        (sp_plan_info.mailbox_bytes).  Results are identical. */
+
+/* ---- region geometry (SP_OPT_REGION_SHAPE) ----
+ * SP_SHAPE_SPLIT: products of 1-D diamonds (pyramids, inverted pyramids and
+ *   wedges of B^3 cells, B/2 steps per band), surfaces routed through
+ *   mailboxes.
+ * SP_SHAPE_LATTICE: the paper's own lattice of 4-cubes with time along the
+ *   main diagonal (Sec. 2, Figs. 2-5): one congruent region type of
+ *   16 s^4 site-updates over 4s levels with four initial and four final
+ *   faces, B = 4s the cube's edge; four predecessors and four successors per
+ *   region (Fig. 2's layers).  Regions read and write the state arrays in
+ *   place (phi at odd levels of a call in a second array of 8 bytes per
+ *   site), so no mailbox is allocated; any step count runs as regions.
+ *   Results are bit-identical to the split tiling and the sweep. */
+#define SP_SHAPE_SPLIT 0
+#define SP_SHAPE_LATTICE 1
 
 /* ---- region cost model ---- */
 #define SP_MODEL_FEATURES 16
@@ -150,8 +167,10 @@ typedef struct {
     int32_t tune_candidates; /* candidates the autotuner timed */
     double tune_best_ms;     /* its trial time of the chosen candidate (16 steps) */
     double tune_default_ms;  /* its trial time of the default choice, 0 if not timed */
-    int32_t mailbox_slots;   /* 2: ring of two band slots; 1: one slot for every band */
-    int32_t reserved;
+    int32_t mailbox_slots;   /* 2: ring of two band slots; 1: one slot for every band (0: lattice) */
+    int32_t region_shape;    /* SP_SHAPE_SPLIT or SP_SHAPE_LATTICE; for a lattice plan "band" reads
+                                "layer" (s levels: 4 M_x M_y M_z regions, N_d = B M_d) and
+                                mailbox_bytes holds the odd-level phi array */
 } sp_plan_info;
 
 /*
@@ -176,12 +195,18 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  * sp_region_plan -- build the region tiling, the dependency DAG and the
  * surface routing tables (paper Sec. 2 geometry and Sec. 3 sizing), and size
  * the persistent launch.
- *   base_B     : region base in cells (4, 8 or 16; B/2 steps per band); 0 to
- *                take 16 where it divides every side of a simulation, else 8;
- *                SP_AUTOTUNE to time both policies (all 8, 16 where
- *                possible) and keep the faster.  Every n[d] must be a
- *                multiple of B with n[d] / B >= 2.
- *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768,
+ *   base_B     : region base in cells (4, 8, 16 or 32; B/2 steps per band);
+ *                0 to take 16 where it divides every side of a simulation,
+ *                else 8; SP_AUTOTUNE to time the policies (all 8, 16 where
+ *                possible, 32 where possible) and keep the fastest.  Every
+ *                n[d] must be a multiple of B with n[d] / B >= 2.
+ *                With SP_SHAPE_LATTICE: the 4-cube edge B = 4s, s = 1..6
+ *                (4, 8, 12, 16, 20 or 24; 4s levels per region); every n[d]
+ *                a multiple of B; 0 takes 16 where it divides, else 8, else
+ *                4; SP_AUTOTUNE times the sizes that divide every side.
+ *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768;
+ *                lattice plans: 64, 128 (the default) or 256, one region per
+ *                CTA and no manager warp;
  *                every worker taking every step of a region); one manager
  *                warp is added.  0 for the default of each base (64 for
  *                bases 4 and 8, 384 for 16); SP_AUTOTUNE to time the

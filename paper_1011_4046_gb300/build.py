@@ -22,7 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sp_api.cu", "sp_kernels.cu", "sp_octant.cu", "sp_model.cu", "sp_noalloc.cu", "sp_peaks.cu", "planner.cpp"]
+SOURCES = ["sp_api.cu", "sp_kernels.cu", "sp_octant.cu", "sp_lattice.cu", "sp_model.cu", "sp_noalloc.cu", "sp_peaks.cu",
+           "planner.cpp", "lattice.cpp"]
 
 
 def nvcc() -> str:

@@ -122,6 +122,17 @@ LAT_HD int lat_layer_count(int s, int64_t T) { return (int)((T - 1) / s) + 4; }
 LAT_HD int lat_min_layer() { return -3; }
 LAT_HD int64_t lat_per_layer(const LatGeom &g) { return 4ll * g.M[0] * g.M[1] * g.M[2]; }
 
+// Layer numbering across calls.  Done flags hold absolute layer numbers and
+// are never cleared: a call of `layers` layers numbers them
+// last + 1 .. last + layers (last: the largest number used before, 0
+// initially, with flags starting at 0), so every wait of the call (for layer
+// number >= its first + 1 ... ) is above every value a previous call wrote.
+LAT_HD void lat_next_epoch(int *last, int layers, int *first)
+{
+    *first = *last + 1;
+    *last += layers;
+}
+
 // Centre of region idx of layer L in units of s: a_d in [0, 4 M_d), all
 // congruent to L mod 2, a_0 + a_1 + a_2 congruent to -L mod 4.
 LAT_HD void lat_centre(const LatGeom &g, int L, int64_t idx, int a[3])

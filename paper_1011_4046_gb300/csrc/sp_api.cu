@@ -20,6 +20,8 @@
 #include "sp_device.cuh"
 #include "sp_kernels.h"
 
+#include "lattice.h"
+
 namespace sp {
 cudaError_t model_buckets(const sp_model *m, const float *X, long long n, unsigned char *prio, cudaStream_t st);
 }
@@ -47,6 +49,14 @@ struct TablesOnDevice {
     unsigned short *d_imp = nullptr;
     int2 *d_exp = nullptr;
     sp::Succ *d_reuse = nullptr;  // mailbox-reuse successors, kMaxSameSucc per type
+};
+
+// The 4-cube lattice tables of one size s (lattice.h) on the device.
+struct LatOnDevice {
+    sp::LatticeTables host;
+    unsigned long long *d_cell = nullptr;
+    unsigned short *d_imp = nullptr;
+    unsigned *d_rec = nullptr;
 };
 
 // One persistent launch per region base: simulations of the same base share a
@@ -182,6 +192,17 @@ struct sp_grid {
     std::vector<long long> mb_slot;   // float2 offset of band slot 1 (0: one slot for every band)
     std::vector<long long> mb_elems;  // float2 elements per slot
     int mb_slots = 1;                 // SP_OPT_MAILBOX_SLOTS, applied by sp_region_plan
+    int shape_opt = SP_SHAPE_SPLIT;   // SP_OPT_REGION_SHAPE, applied by sp_region_plan
+    int shape = SP_SHAPE_SPLIT;       // of the current plan
+    // lattice plans: tables by size s, phi at odd levels of a call per
+    // simulation, done flags of every group ([4][regions per layer] each)
+    std::map<int, LatOnDevice> lat;
+    std::vector<float2 *> phi_odd;
+    int *d_lat_flags = nullptr;
+    std::vector<size_t> lat_flag_off;  // per group
+    sp::LatSimDev *d_lsims = nullptr;
+    size_t cap_lsims = 0;
+    std::vector<sp::LatSimDev> up_lsims;
     std::vector<std::array<long long, sp::kTypes>> mb_type_off;
     // launch scratch
     int *d_counters = nullptr, *d_queue = nullptr;
@@ -605,6 +626,18 @@ void free_plan(sp_grid *g)
     g->groups.clear();
     for (float2 *m : g->mbox) cudaFree(m);
     g->mbox.clear();
+    for (auto &kv : g->lat) {
+        cudaFree(kv.second.d_cell);
+        cudaFree(kv.second.d_imp);
+        cudaFree(kv.second.d_rec);
+    }
+    g->lat.clear();
+    for (float2 *f : g->phi_odd) cudaFree(f);
+    g->phi_odd.clear();
+    cudaFree(g->d_lat_flags);
+    g->d_lat_flags = nullptr;
+    g->lat_flag_off.clear();
+    g->shape = SP_SHAPE_SPLIT;
     if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);
     g->region_graph.exec = nullptr;
     g->region_graph.key.clear();
@@ -795,6 +828,179 @@ int run_region_call(sp_grid *g, const std::vector<GroupLaunch> &groups, int64_t 
     return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
 }
 
+// A lattice call: per group (lattice size), the reset (ticket counter, error
+// word, layer epoch) and the persistent kernel over all its simulations'
+// regions; then, for an odd step count, phi (left in the odd-level array)
+// copied back to the caller's array.  Timing events 1 and 2 bracket the
+// kernels.
+struct LatLaunch {
+    GroupCfg cfg;
+    sp::LatArgs a;
+};
+
+int enqueue_lattice_call(sp_grid *g, const std::vector<LatLaunch> &launches, int64_t n_steps, bool timing,
+                         bool capturing)
+{
+    cudaError_t e = cudaSuccess;
+    auto mark = [&](cudaEvent_t ev) {
+        if (e == cudaSuccess)
+            e = capturing ? cudaEventRecordWithFlags(ev, g->stream, cudaEventRecordExternal)
+                          : cudaEventRecord(ev, g->stream);
+    };
+    for (size_t i = 0; i < launches.size() && e == cudaSuccess; ++i) {
+        const LatLaunch &l = launches[i];
+        e = sp::launch_lattice_reset(l.a.ctl, l.a.Lcount, g->stream);
+        if (timing && i == 0) mark(g->ev[1]);
+        if (e == cudaSuccess) e = sp::launch_lattice(l.a, l.cfg.threads, l.cfg.smem, l.cfg.grid, g->stream);
+    }
+    if (launches.empty() && timing) mark(g->ev[1]);
+    if (timing) mark(g->ev[2]);
+    if (n_steps & 1)
+        for (int s = 0; s < g->n_sims && e == cudaSuccess; ++s)
+            e = cudaMemcpyAsync(g->phi[s], g->phi_odd[s], (size_t)sites_of(g->p[s]) * sizeof(float2),
+                                cudaMemcpyDeviceToDevice, g->stream);
+    return e == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+int run_lattice_call(sp_grid *g, const std::vector<LatLaunch> &launches, int64_t n_steps, bool timing)
+{
+    if (g->stream == nullptr || !g->use_graphs) return enqueue_lattice_call(g, launches, n_steps, timing, false);
+    std::vector<unsigned char> key;
+    append_key(&key, (int)SP_SHAPE_LATTICE);
+    append_key(&key, n_steps);
+    append_key(&key, timing);
+    append_key(&key, launches.size());
+    for (const LatLaunch &l : launches) {
+        append_key(&key, l.cfg);
+        append_key(&key, l.a);
+    }
+    for (int s = 0; s < g->n_sims; ++s) {
+        append_key(&key, g->phi[s]);
+        append_key(&key, g->phi_odd[s]);
+    }
+    RegionGraph &rg = g->region_graph;
+    if (!rg.exec || rg.key != key) {
+        if (rg.exec) cudaGraphExecDestroy(rg.exec);
+        rg.exec = nullptr;
+        rg.key.clear();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return SP_ECUDA;
+        const int rc = enqueue_lattice_call(g, launches, n_steps, timing, true);
+        e = cudaStreamEndCapture(g->stream, &graph);
+        if (rc != SP_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != SP_OK ? rc : SP_ECUDA;
+        }
+        e = cudaGraphInstantiate(&rg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            rg.exec = nullptr;
+            return SP_ECUDA;
+        }
+        rg.key = key;
+    }
+    return cudaGraphLaunch(rg.exec, g->stream) == cudaSuccess ? SP_OK : SP_ECUDA;
+}
+
+// The region path of sp_evolve for a lattice plan: every step count runs as
+// regions (layers cut by the call's first and last levels).
+int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
+{
+    if (n_steps > 0x3fffffffll) return SP_EINVAL;
+    std::vector<sp::LatSimDev> sims;
+    std::vector<LatLaunch> launches;
+    std::vector<size_t> sim_off;
+    long long trace_total = 0;
+    g->last_tile_base.assign(g->n_sims, 0);
+    g->last_tiles.assign(g->n_sims, 0);
+    for (size_t gi = 0; gi < g->groups.size(); ++gi) {
+        const GroupCfg &c = g->groups[gi];
+        const int s = c.B / 4;
+        const LatOnDevice &ld = g->lat.at(s);
+        const sp::LatticeTables &t = ld.host;
+        const int Lcount = sp::lat_layer_count(s, n_steps);
+        LatLaunch l;
+        l.cfg = c;
+        sp::LatArgs &a = l.a;
+        std::memset(&a, 0, sizeof a);  // padding too: the bytes are a graph key
+        const size_t first = sims.size();
+        long long per_layer_all = 0;
+        for (int sim = 0; sim < g->n_sims; ++sim) {
+            if (g->B[sim] != c.B) continue;
+            sp::LatSimDev d;
+            std::memset(&d, 0, sizeof d);
+            for (int k = 0; k < 3; ++k) {
+                d.n[k] = g->p[sim].n[k];
+                d.M[k] = d.n[k] / c.B;
+            }
+            d.region_base = per_layer_all;
+            d.per_layer = 4ll * d.M[0] * d.M[1] * d.M[2];
+            d.coef = g->d_coef + (size_t)sim * n_steps;
+            d.q = phys_const(g->p[sim]);
+            d.phi0 = g->phi[sim];
+            d.phi1 = g->phi_odd[sim];
+            d.pc = g->pc[sim];
+            d.trace_base = trace_total;
+            g->last_tile_base[sim] = (unsigned)trace_total;
+            g->last_tiles[sim] = (unsigned)(d.per_layer * Lcount);
+            trace_total += d.per_layer * Lcount;
+            per_layer_all += d.per_layer;
+            sims.push_back(d);
+        }
+        if (per_layer_all == 0) continue;
+        if (per_layer_all * Lcount > 0xfffffff0ll || trace_total > 0x7fffffffll) return SP_EINVAL;
+        a.n_sims = (int)(sims.size() - first);
+        a.s = s;
+        a.K = t.K;
+        a.T = (int)n_steps;
+        a.n_slots = t.n_slots;
+        a.n_foot = t.n_foot;
+        a.Lcount = Lcount;
+        a.per_layer_all = (unsigned)per_layer_all;
+        a.total = (unsigned)(per_layer_all * Lcount);
+        a.cell = ld.d_cell;
+        a.imp = ld.d_imp;
+        a.slot_rec = ld.d_rec;
+        a.flags = g->d_lat_flags + g->lat_flag_off[gi];
+        a.ctl = g->d_ctl + gi;
+        a.fault_drop = g->fault_drop;
+        for (int k = 0; k <= t.K; ++k) {
+            a.cell_off[k] = t.cell_off[k];
+            a.imp_off[k] = t.imp_off[k];
+        }
+        sim_off.push_back(first);
+        launches.push_back(l);
+    }
+    cudaError_t e = grow(&g->d_lsims, &g->cap_lsims, sims.size());
+    if (e == cudaSuccess && trace) e = grow(&g->d_trace, &g->cap_trace, 2 * (size_t)trace_total);
+    if (e != cudaSuccess) return SP_ENOMEM;
+    for (size_t i = 0; i < launches.size(); ++i) {
+        launches[i].a.sims = g->d_lsims + sim_off[i];
+        launches[i].a.trace = trace ? g->d_trace : nullptr;
+    }
+    if (sims.size() != g->up_lsims.size() ||
+        std::memcmp(sims.data(), g->up_lsims.data(), sims.size() * sizeof(sp::LatSimDev)) != 0) {
+        e = cudaMemcpyAsync(g->d_lsims, sims.data(), sims.size() * sizeof(sp::LatSimDev), cudaMemcpyHostToDevice,
+                            g->stream);
+        if (e != cudaSuccess) return SP_ECUDA;
+        g->up_lsims = sims;
+    }
+    if (g->up_limit != g->wait_limit_ns) {
+        unsigned long long lim = g->wait_limit_ns;
+        for (int i = 0; i < kMaxGroups && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(&g->d_ctl[i].wait_limit_ns, &lim, sizeof lim, cudaMemcpyHostToDevice, g->stream);
+        if (e != cudaSuccess) return SP_ECUDA;
+        g->up_limit = lim;
+    }
+    if (trace) g->trace_total = (unsigned)trace_total;
+    g->last_traced = trace;
+    g->last_features = false;
+    g->last_total = (unsigned)trace_total;
+    g->prev_trace_ok = false;
+    return run_lattice_call(g, launches, n_steps, timing);
+}
+
 // Worker counts of the region kernel (every worker does every step).
 bool valid_threads(int t)
 {
@@ -885,6 +1091,94 @@ int plan_fixed(sp_grid *g, const std::vector<int> &Bs, int threads, int order, c
         }
         g->mbox.push_back(m);
     }
+    g->planned = true;
+    return SP_OK;
+}
+
+// Lattice plans (SP_SHAPE_LATTICE): B = 4s per simulation.  Tables per
+// distinct s, one launch configuration per s (largest first), the odd-level
+// phi array of every simulation and the done flags of every group.
+int choose_lattice_B(const sp_params &p, int requested)
+{
+    auto ok = [&](int B) {
+        if (B < 4 || B > 4 * sp::kLatMaxS || B % 4) return false;
+        for (int d = 0; d < 3; ++d)
+            if (p.n[d] % B != 0) return false;
+        return true;
+    };
+    if (requested) return ok(requested) ? requested : -1;
+    for (int B : {16, 8, 4})
+        if (ok(B)) return B;
+    return -1;
+}
+
+int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
+{
+    free_plan(g);
+    if (g->model) sp_model_destroy(g->model);
+    g->model = nullptr;
+    if (threads == 0) threads = 128;
+    if (!sp::lattice_valid_threads(threads)) return SP_EINVAL;
+    g->B = Bs;
+    g->max_B = 0;
+    cudaError_t e = cudaSuccess;
+    for (int sim = 0; sim < g->n_sims; ++sim) {
+        g->max_B = std::max(g->max_B, Bs[sim]);
+        const int s = Bs[sim] / 4;
+        if (g->lat.count(s)) continue;
+        LatOnDevice &ld = g->lat[s];
+        if (!sp::build_lattice_tables(s, &ld.host).empty()) return SP_EINVAL;
+        const sp::LatticeTables &t = ld.host;
+        e = cudaMalloc((void **)&ld.d_cell, t.cell.size() * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp, std::max<size_t>(t.imp.size(), 1) * sizeof(uint16_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_rec, t.slot_rec.size() * sizeof(uint32_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !t.imp.empty())
+            e = cudaMemcpy(ld.d_imp, t.imp.data(), t.imp.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ld.d_rec, t.slot_rec.data(), t.slot_rec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            free_plan(g);
+            return SP_ENOMEM;
+        }
+    }
+    size_t flags = 0;
+    for (auto it = g->lat.rbegin(); it != g->lat.rend(); ++it) {
+        const sp::LatticeTables &t = it->second.host;
+        GroupCfg c;
+        c.B = 4 * it->first;
+        c.threads = threads;
+        c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot);
+        if (c.smem > 227 * 1024) return SP_EINVAL;
+        e = sp::lattice_occupancy(threads, c.smem, &c.ctas_per_sm);
+        if (e != cudaSuccess || c.ctas_per_sm < 1) return SP_EINVAL;
+        c.grid = c.ctas_per_sm * g->sm_count;
+        g->groups.push_back(c);
+        g->lat_flag_off.push_back(flags);
+        long long per_layer = 0;
+        for (int sim = 0; sim < g->n_sims; ++sim)
+            if (g->B[sim] == c.B) per_layer += 4ll * (g->p[sim].n[0] / c.B) * (g->p[sim].n[1] / c.B) * (g->p[sim].n[2] / c.B);
+        if (per_layer > 0x7fffffffll) return SP_EINVAL;
+        flags += 4 * (size_t)per_layer;
+    }
+    if ((int)g->groups.size() > kMaxGroups) return SP_EINVAL;
+    e = cudaMalloc((void **)&g->d_lat_flags, std::max<size_t>(flags, 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_lat_flags, 0, std::max<size_t>(flags, 1) * sizeof(int), g->stream);
+    for (int sim = 0; sim < g->n_sims && e == cudaSuccess; ++sim) {
+        float2 *f = nullptr;
+        e = cudaMalloc((void **)&f, (size_t)sites_of(g->p[sim]) * sizeof(float2));
+        if (e == cudaSuccess) g->phi_odd.push_back(f);
+    }
+    if (e != cudaSuccess) {
+        free_plan(g);
+        return SP_ENOMEM;
+    }
+    g->order = SP_ORDER_STATIC;
+    g->threads = threads;
+    g->mb_slot.assign(g->n_sims, 0);
+    g->mb_elems.assign(g->n_sims, 0);
+    g->shape = SP_SHAPE_LATTICE;
     g->planned = true;
     return SP_OK;
 }
@@ -991,6 +1285,90 @@ int autotune(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, 
     return SP_OK;
 }
 
+// Autotuner of lattice plans: for every lattice size B = 4s that divides
+// every side (and every worker count when block_shape is SP_AUTOTUNE), a
+// scratch grid of the simulations cut to at most 128 cells per side (a
+// multiple of B) runs 32-step calls from a copy of the current state; the
+// candidate with the least time per site-update (best of two after a
+// warm-up call) wins.
+int autotune_lattice(sp_grid *g, int base_B, int block_shape, std::vector<int> *best_B, int *best_threads)
+{
+    std::vector<int> sizes;
+    if (base_B == SP_AUTOTUNE) {
+        for (int B = 8; B <= 4 * sp::kLatMaxS; B += 4) {
+            bool ok = true;
+            for (int s = 0; s < g->n_sims && ok; ++s) ok = choose_lattice_B(g->p[s], B) == B;
+            if (ok) sizes.push_back(B);
+        }
+    } else {
+        for (int s = 0; s < g->n_sims; ++s)
+            if (choose_lattice_B(g->p[s], base_B) < 0) return SP_EINVAL;
+        sizes.push_back(base_B ? base_B : 0);
+    }
+    if (sizes.empty()) return SP_EINVAL;
+    const std::vector<int> shapes =
+        block_shape == SP_AUTOTUNE ? std::vector<int>{64, 128, 256} : std::vector<int>{block_shape ? block_shape : 128};
+    constexpr int kTrialSteps = 32;
+    double best = 0.0;
+    bool have = false;
+    for (int B : sizes) {
+        std::vector<int> Bs(g->n_sims);
+        std::vector<sp_params> tp = g->p;
+        double updates = 0.0;
+        for (int s = 0; s < g->n_sims; ++s) {
+            Bs[s] = choose_lattice_B(g->p[s], B);
+            for (int d = 0; d < 3; ++d)
+                if (tp[s].n[d] > 128) tp[s].n[d] = (128 / Bs[s]) * Bs[s];
+            tp[s].damp_steps = 0;
+            updates += (double)sites_of(tp[s]) * kTrialSteps;
+        }
+        sp_grid *t = nullptr;
+        int rc = sp_grid_create(tp.data(), g->n_sims, nullptr, g->stream, &t);
+        if (rc != SP_OK) return rc;
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < g->n_sims && e == cudaSuccess; ++s) {
+            const size_t sites = (size_t)sites_of(tp[s]);
+            e = cudaMemcpyAsync(t->phi[s], g->phi[s], sites * sizeof(float2), cudaMemcpyDeviceToDevice, g->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t->pc[s], g->pc[s], sites * sizeof(float4), cudaMemcpyDeviceToDevice, g->stream);
+        }
+        if (e != cudaSuccess) {
+            sp_destroy(t);
+            return SP_ECUDA;
+        }
+        for (int nt : shapes) {
+            rc = plan_lattice(t, Bs, nt);
+            if (rc == SP_EINVAL) continue;  // does not fit this device
+            float ms = 0.0f;
+            for (int rep = 0; rep < 3 && rc == SP_OK; ++rep) {
+                rc = sp_evolve(t, kTrialSteps, SP_RESTART | SP_TIMING);
+                float m = 0.0f;
+                if (rc == SP_OK && cudaEventElapsedTime(&m, t->ev[0], t->ev[3]) != cudaSuccess) rc = SP_ECUDA;
+                if (rep == 1 || (rep == 2 && m < ms)) ms = m;
+            }
+            if (rc != SP_OK) {
+                sp_destroy(t);
+                return rc;
+            }
+            ++g->tune.candidates;
+            const double per = ms / updates;
+            if ((B == 16 || B == 0) && nt == 128) g->tune.default_ms = ms;
+            if (!have || per < best) {
+                best = per;
+                have = true;
+                *best_B = Bs;
+                *best_threads = nt;
+                g->tune.best_ms = ms;
+            }
+        }
+        sp_destroy(t);
+    }
+    if (!have) return SP_EINVAL;
+    g->tune.autotuned = 1;
+    g->tune.trial_steps = kTrialSteps;
+    return SP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1083,6 +1461,25 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
 int sp_region_plan(sp_grid *g, int32_t base_B, int32_t block_shape, int32_t order, const char *model_path)
 {
     if (!g) return SP_EINVAL;
+    if (g->shape_opt == SP_SHAPE_LATTICE) {
+        // congruent regions in a fixed topological (layer) order: nothing to learn
+        if (order != SP_ORDER_STATIC) return SP_EINVAL;
+        if (block_shape != 0 && block_shape != SP_AUTOTUNE && !sp::lattice_valid_threads(block_shape))
+            return SP_EINVAL;
+        g->tune = TuneReport();
+        std::vector<int> Bs(g->n_sims);
+        int threads = block_shape;
+        if (base_B == SP_AUTOTUNE || block_shape == SP_AUTOTUNE) {
+            const int rc = autotune_lattice(g, base_B, block_shape, &Bs, &threads);
+            if (rc != SP_OK) return rc;
+        } else {
+            for (int s = 0; s < g->n_sims; ++s) {
+                Bs[s] = choose_lattice_B(g->p[s], base_B);
+                if (Bs[s] < 0) return SP_EINVAL;
+            }
+        }
+        return plan_lattice(g, Bs, threads);
+    }
     // bases are powers of two: the kernels decode cell indices with shifts
     if (base_B != 0 && base_B != SP_AUTOTUNE && base_B != 4 && base_B != 8 && base_B != 16 && base_B != 32)
         return SP_EINVAL;
@@ -1146,6 +1543,9 @@ int sp_evolve(sp_grid *g, int64_t n_steps, uint32_t flags)
     if (mono) {
         for (int s = 0; s < g->n_sims && rc == SP_OK; ++s)
             rc = sweep_steps(g, s, n_steps, 0, g->d_coef + (size_t)s * n_steps);
+    } else if (g->shape == SP_SHAPE_LATTICE) {
+        if (flags & SP_FEATURES) return SP_EINVAL;  // congruent regions: no cost features
+        rc = evolve_lattice(g, n_steps, (flags & SP_TRACE) != 0, timing);
     } else {
         // whole bands as regions: one persistent launch per region base over all
         // simulations of that base; region ids run on across the groups
@@ -1313,6 +1713,10 @@ int sp_set_option(sp_grid *g, int32_t option, int64_t value)
         if (value != 1 && value != 2) return SP_EINVAL;
         g->mb_slots = (int)value;
         return SP_OK;
+    case SP_OPT_REGION_SHAPE:
+        if (value != SP_SHAPE_SPLIT && value != SP_SHAPE_LATTICE) return SP_EINVAL;
+        g->shape_opt = (int)value;
+        return SP_OK;
     default:
         return SP_EINVAL;
     }
@@ -1421,6 +1825,34 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
     }
     case SP_SURF_PLAN: {
         if (dst_bytes < sizeof(sp_plan_info) || !g->planned) return SP_EINVAL;
+        if (g->shape == SP_SHAPE_LATTICE) {
+            const sp::LatticeTables &t = g->lat.at(g->B[sim] / 4).host;
+            const int64_t per_layer = 4ll * (p.n[0] / g->B[sim]) * (p.n[1] / g->B[sim]) * (p.n[2] / g->B[sim]);
+            sp_plan_info info;
+            std::memset(&info, 0, sizeof info);
+            info.base_B = g->B[sim];
+            for (const GroupCfg &c : g->groups)
+                if (c.B == g->B[sim]) {
+                    info.threads = c.threads;
+                    info.ctas_per_sm = c.ctas_per_sm;
+                    info.grid = c.grid;
+                }
+            info.regions_per_band = per_layer;
+            info.updates_per_band = per_layer * t.updates;
+            info.bytes_read_per_band = per_layer * t.bytes_read;
+            info.bytes_written_per_band = per_layer * t.bytes_written;
+            info.bytes_per_update = (double)(t.bytes_read + t.bytes_written) / (double)t.updates;
+            info.mailbox_slots = 0;
+            info.mailbox_bytes = sites * (int64_t)sizeof(float2);
+            info.region_shape = SP_SHAPE_LATTICE;
+            info.autotuned = g->tune.autotuned;
+            info.tune_candidates = g->tune.candidates;
+            info.tune_best_ms = g->tune.best_ms;
+            info.tune_default_ms = g->tune.default_ms;
+            if (dst_is_device) e = cudaMemcpy(dst, &info, sizeof info, cudaMemcpyHostToDevice);
+            else std::memcpy(dst, &info, sizeof info);
+            return cuda_err(e);
+        }
         const TablesOnDevice &td = g->tables[g->B[sim]];
         sp::PlanStats ps = sp::plan_stats(td.host, p.n);
         if (td.octant) {  // the cluster kernel moves the octant tables' traffic
@@ -1515,6 +1947,7 @@ int sp_destroy(sp_grid *g)
     cudaFree(g->d_feat);
     cudaFree(g->d_simf);
     cudaFree(g->d_prio);
+    cudaFree(g->d_lsims);
     if (g->model) sp_model_destroy(g->model);
     if (g->sweep_graph.exec) cudaGraphExecDestroy(g->sweep_graph.exec);
     if (g->region_graph.exec) cudaGraphExecDestroy(g->region_graph.exec);

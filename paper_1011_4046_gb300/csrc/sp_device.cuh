@@ -152,6 +152,45 @@ struct alignas(128) Ctl {
     unsigned long long wait_limit_ns;  // per-wait bound for every spin
     unsigned int bcount[kBuckets];     // learned ordering: band-0 seeds per bucket,
     unsigned int bcursor[kBuckets];    // and the next free position of each bucket's run
+    // lattice launches: absolute number of the call's first layer, and the
+    // last absolute layer number any call of this control block has used
+    // (the reset kernel starts every call above it, so done flags, which
+    // only grow, never need clearing)
+    int epoch;
+    int last_layer;
+};
+
+// One simulation of a lattice launch (4-cube regions, lattice.h).
+struct alignas(16) LatSimDev {
+    int n[3], M[3];             // sides, N_d = 4 s M_d
+    long long region_base;      // first region of this simulation within a layer of the launch
+    long long per_layer;        // 4 M_0 M_1 M_2
+    const LevelCoef *coef;      // coef[tau - 1]: coefficients of relative level tau of this call
+    PhysConst q;
+    float2 *phi0, *phi1;        // phi at even / odd levels of the call (phi0: the caller's array)
+    float4 *pc;                 // (pi, c), one array
+    long long trace_base;       // trace / fault-injection id of this simulation's first region
+};
+
+// Launch arguments of the lattice kernel.  Regions are handed out by ticket
+// in layer order; region t of the launch is region j = t mod per_layer_all
+// of layer -3 + t / per_layer_all, j running over the simulations' regions
+// in turn.  flags[(layer & 3) * per_layer_all + j] holds the absolute
+// number of the last layer whose region j finished.
+struct LatArgs {
+    const LatSimDev *sims;
+    int n_sims, s, K, T;
+    int n_slots, n_foot, Lcount, pad0;
+    long long fault_drop;            // region id (as in the trace) that never reports done (-1: none)
+    unsigned per_layer_all, total;
+    const unsigned long long *cell;  // cell entries (lattice.h), all levels
+    const unsigned short *imp;       // import entries, all levels
+    const unsigned *slot_rec;        // slot records
+    int *flags;
+    Ctl *ctl;
+    unsigned long long *trace;       // optional (start, end) globaltimer per region: simulation by
+                                     // simulation, layer by layer (trace_base + layer * per_layer + idx)
+    int cell_off[4 * 6 + 1], imp_off[4 * 6 + 1];
 };
 
 struct RegionArgs {

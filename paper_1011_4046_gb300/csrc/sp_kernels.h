@@ -31,3 +31,14 @@ cudaError_t region_oct_clusters(size_t smem, int *clusters);
 cudaError_t launch_region_oct(const RegionArgs &a, size_t smem, int clusters, cudaStream_t st);
 int region_oct_workers();
 }  // namespace sp
+
+namespace sp {
+// The 4-cube lattice kernel (sp_lattice.cu): dynamic shared memory of one
+// region, worker counts, occupancy, the per-call reset (ticket counter,
+// error word, layer epoch) and the launch.
+size_t lattice_smem_bytes(int n_slots, int n_foot);
+bool lattice_valid_threads(int threads);
+cudaError_t lattice_occupancy(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_lattice_reset(Ctl *ctl, int layers, cudaStream_t st);
+cudaError_t launch_lattice(const LatArgs &a, int threads, size_t smem, int grid, cudaStream_t st);
+}  // namespace sp

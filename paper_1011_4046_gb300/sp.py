@@ -52,6 +52,9 @@ SP_OPT_WAIT_LIMIT_NS = 1
 SP_OPT_FAULT_DROP_RELEASE = 2
 SP_OPT_GRAPHS = 3
 SP_OPT_MAILBOX_SLOTS = 4
+SP_OPT_REGION_SHAPE = 5
+SP_SHAPE_SPLIT = 0
+SP_SHAPE_LATTICE = 1
 SP_MODEL_FEATURES = 16
 SP_MODEL_PARAMS = 5313
 
@@ -109,7 +112,7 @@ class sp_plan_info(ctypes.Structure):
         ("tune_best_ms", ctypes.c_double),
         ("tune_default_ms", ctypes.c_double),
         ("mailbox_slots", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("region_shape", ctypes.c_int32),
     ]
 
 
@@ -364,7 +367,11 @@ class Grid:
         rc, self.h = sp_grid_create(self.params, ptrs, self.stream.cuda_stream)
         _check(rc, "sp_grid_create")
 
-    def plan(self, base_B=0, threads=0, order=SP_ORDER_STATIC, model_path=None):
+    def plan(self, base_B=0, threads=0, order=SP_ORDER_STATIC, model_path=None, shape=None):
+        """Region plan; shape (SP_SHAPE_SPLIT or SP_SHAPE_LATTICE) sets
+        SP_OPT_REGION_SHAPE first when given."""
+        if shape is not None:
+            self.set_option(SP_OPT_REGION_SHAPE, shape)
         _check(sp_region_plan(self.h, base_B, threads, order, model_path), "sp_region_plan")
 
     def set_option(self, option, value):

@@ -87,4 +87,5 @@ def lx():
     L.lx_stats.argtypes = [ctypes.c_int, i64p]
     L.lx_level.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     L.lx_plant.argtypes = [ctypes.c_int]
+    L.lx_epochs.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     return L

@@ -355,6 +355,14 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
 
 void lx_plant(int which) { g_plant = which; }
 
+// Layer numbering of a sequence of calls (layers[i] layers each): the first
+// number of every call, as the reset kernel computes it.
+void lx_epochs(const int *layers, int n, int *first)
+{
+    int last = 0;
+    for (int i = 0; i < n; ++i) sp::lat_next_epoch(&last, layers[i], &first[i]);
+}
+
 // Table statistics of size s: updates, slots, footprint cells, imports
 // (full, phi), exports (phi, (pi, c)), bytes read, bytes written, largest level.
 int lx_stats(int s, int64_t *out)

@@ -111,7 +111,8 @@ def test_header_constants_match_the_binding():
     text = open(sp.HEADER).read()
     import re
     for name in ("SP_AUTOTUNE", "SP_FEATURES", "SP_SURF_FEATURES", "SP_SURF_LEVEL", "SP_OPT_WAIT_LIMIT_NS",
-                 "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_OPT_MAILBOX_SLOTS", "SP_MODEL_PARAMS",
+                 "SP_OPT_FAULT_DROP_RELEASE", "SP_OPT_GRAPHS", "SP_OPT_MAILBOX_SLOTS", "SP_OPT_REGION_SHAPE",
+                 "SP_SHAPE_SPLIT", "SP_SHAPE_LATTICE", "SP_MODEL_PARAMS",
                  "SP_MODEL_FEATURES",
                  "SP_ORDER_STATIC", "SP_ORDER_LEARNED", "SP_TIMING", "SP_TRACE", "SP_FP32_KAHAN",
                  "SP_NOALLOC_MAX_SITES", "SP_NOALLOC_MAX_STEPS"):

@@ -193,3 +193,25 @@ def test_race_check_catches_planted_mistakes(lx, plant, expect):
             assert any(e in msg.value.decode() for e in expect), msg.value.decode()
     finally:
         lx.lx_plant(0)
+
+
+def test_layer_numbers_of_successive_calls_never_reuse_flag_values(lx):
+    """Done flags are never cleared: a call waits for 'flag >= its layer
+    number - 1'.  For any sequence of calls (long ones followed by short
+    ones included), every layer number a call waits for exceeds every value
+    an earlier call wrote, and the first call waits only for values above
+    the flags' initial 0."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        n = int(rng.integers(1, 12))
+        s = int(rng.integers(1, 7))
+        steps = rng.integers(1, 200, size=n)
+        layers = np.array([(int(t) - 1) // s + 4 for t in steps], dtype=np.int32)
+        first = np.zeros(n, dtype=np.int32)
+        lx.lx_epochs(layers.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n,
+                     first.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        written_max = 0
+        for i in range(n):
+            waits_min = first[i]  # layer 1 of the call waits for its layer 0: number first
+            assert waits_min > written_max
+            written_max = max(written_max, first[i] + layers[i] - 1)
