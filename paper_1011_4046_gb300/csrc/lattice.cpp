@@ -4,8 +4,8 @@
 #include "lattice.h"
 
 #include <algorithm>
-#include <cstdlib>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <set>
 
@@ -31,9 +31,9 @@ R3 add(R3 a, const int d[3]) { return {a.x + d[0], a.y + d[1], a.z + d[2]}; }
 
 int dot(const int s[3], R3 r) { return s[0] * r.x + s[1] * r.y + s[2] * r.z; }
 
-// Local level k (0 <= k < 4s) and offset r of point (t, x) of the infinite
-// lattice (region forms f_i = t + sigma_i . x, region n_i = floor(f_i / 4s)),
-// with the region's layer and centre; used to locate producers.
+// Local level k and offset r of point (t, x) of the infinite lattice (forms
+// f_i = t + sigma_i . x, region n_i = floor(f_i / 4s), bottom vertex of
+// region n at t = s (n_1 + n_2 + n_3 + n_4)); used to locate producers.
 void locate(int s, int t, R3 x, int *k, R3 *r)
 {
     const int w = 4 * s;
@@ -63,6 +63,11 @@ std::string fail(const char *fmt, int a = 0, int b = 0, int c = 0)
     char buf[200];
     std::snprintf(buf, sizeof buf, fmt, a, b, c);
     return buf;
+}
+
+void pad4(std::vector<uint32_t> *v)
+{
+    while (v->size() % 4) v->push_back(0u);
 }
 
 }  // namespace
@@ -100,7 +105,6 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         }
     for (const R3 &r : used)
         if (std::abs(r.x) > R || std::abs(r.y) > R || std::abs(r.z) > R) return fail("halo cell beyond |r| = 2s");
-    std::map<R3, int> slot, pcidx;
     std::map<std::pair<int, int>, std::pair<int, int>> rows;  // (z, y) -> x range
     for (const R3 &r : used) {
         auto key = std::make_pair(r.z, r.y);
@@ -112,70 +116,107 @@ std::string build_lattice_tables(int s, LatticeTables *t)
             it->second.second = std::max(it->second.second, r.x);
         }
     }
+    t->rb_side = 4 * s + 1;
+    const int W = t->rb_side;
+    if (W * W > (int)kLatRowMask + 1) return fail("%d rows exceed the entries' row field", W * W);
+    auto row_index = [&](int y, int z) { return (y + R) * W + z + R; };
+    std::vector<int> row_base((size_t)W * W, 0);
+    std::map<R3, int> slot, pcidx;
     int ns = 0, nf = 0;
-    for (const auto &row : rows)  // std::map: ascending (z, y)
+    for (const auto &row : rows) {  // std::map: ascending (z, y)
+        const int z = row.first.first, y = row.first.second;
+        row_base[row_index(y, z)] = ns - row.second.first;
         for (int x = row.second.first; x <= row.second.second; ++x) {
-            const R3 r = {x, row.first.second, row.first.first};
+            const R3 r = {x, y, z};
             slot[r] = ns++;
             if (foot.count(r)) pcidx[r] = nf++;
         }
+    }
     t->n_slots = ns;
     t->n_foot = nf;
-    if (ns > (1 << kLatCellSlotBits)) return fail("%d slots exceed 12-bit indices", ns);
-    t->slot_rec.assign(ns, 0);
-    for (const auto &e : slot) {
+    if (ns > 4096 || nf > 4096) return fail("%d slots exceed the kernel's 12-bit indices", ns);
+
+    // per-row constants: neighbour steps, (pi, c) offset, row base and offset
+    t->row_nb.assign((size_t)W * W, 0);
+    t->row_xy.assign((size_t)W * W, 0);
+    for (int y = -R; y <= R; ++y)
+        for (int z = -R; z <= R; ++z) {
+            const int i = row_index(y, z);
+            if (row_base[i] < -32768 || row_base[i] > 32767) return fail("row base beyond 16 bits");
+            t->row_xy[i] = (uint32_t)(uint16_t)(int16_t)row_base[i] | (uint32_t)(y + R) << 16 | (uint32_t)(z + R) << 21;
+        }
+    std::map<int, std::vector<int>> row_vals;  // row -> (dym, dyp, dzm, dzp, dpc), from its footprint cells
+    for (const auto &e : pcidx) {
         const R3 &r = e.first;
-        uint32_t rec = (uint32_t)(r.x + R) | (uint32_t)(r.y + R) << 5 | (uint32_t)(r.z + R) << 10;
-        auto p = pcidx.find(r);
-        if (p != pcidx.end()) rec |= (uint32_t)p->second << 15 | 1u << 27;
-        t->slot_rec[e.second] = rec;
+        const int sl = slot.at(r);
+        std::vector<int> v = {slot.at({r.x, r.y - 1, r.z}) - sl, slot.at({r.x, r.y + 1, r.z}) - sl,
+                              slot.at({r.x, r.y, r.z - 1}) - sl, slot.at({r.x, r.y, r.z + 1}) - sl, e.second - sl};
+        const int i = row_index(r.y, r.z);
+        auto it = row_vals.find(i);
+        if (it == row_vals.end())
+            row_vals[i] = v;
+        else if (it->second != v)
+            return fail("neighbour steps or (pi, c) offset vary along a row");
     }
+    for (const auto &rv : row_vals) {
+        const std::vector<int> &v = rv.second;
+        if (v[0] < -128 || v[0] > 127 || v[1] < -128 || v[1] > 127) return fail("y step beyond 8 bits");
+        if (v[2] < -2048 || v[2] > 2047 || v[3] < -2048 || v[3] > 2047) return fail("z step beyond 12 bits");
+        if (v[4] < -4096 || v[4] > 4095) return fail("(pi, c) offset beyond 13 bits");
+        t->row_nb[rv.first] = (uint64_t)(uint8_t)(int8_t)v[0] | (uint64_t)(uint8_t)(int8_t)v[1] << 8 |
+                              (uint64_t)(v[2] & 0xfff) << 16 | (uint64_t)(v[3] & 0xfff) << 28 |
+                              (uint64_t)(v[4] & 0x1fff) << 40;
+    }
+    auto entry_of = [&](const R3 &r) {
+        return (uint32_t)slot.at(r) | (uint32_t)row_index(r.y, r.z) << kLatRowShift;
+    };
 
     // cell entries with export flags
     t->cell_off.assign(K + 1, 0);
+    t->cell_n.assign(K, 0);
     for (int k = 0; k < K; ++k) {
         t->cell_off[k] = (int32_t)t->cell.size();
         for (const R3 &r : lev[k]) {
-            const int sl = slot.at(r);
-            const int ym = slot.at({r.x, r.y - 1, r.z}) - sl, yp = slot.at({r.x, r.y + 1, r.z}) - sl;
-            const int zm = slot.at({r.x, r.y, r.z - 1}) - sl, zp = slot.at({r.x, r.y, r.z + 1}) - sl;
-            if (ym < -128 || ym > 127 || yp < -128 || yp > 127) return fail("y slot step %d / %d beyond 8 bits", ym, yp);
-            if (zm < -512 || zm > 511 || zp < -512 || zp > 511) return fail("z slot step %d / %d beyond 10 bits", zm, zp);
-            if (slot.at({r.x - 1, r.y, r.z}) != sl - 1 || slot.at({r.x + 1, r.y, r.z}) != sl + 1)
-                return fail("x neighbours of a cell are not adjacent slots");
-            bool ephi = false;
+            for (const auto &d : kNb)
+                if (!slot.count(add(r, d))) return fail("neighbour without a slot at level %d", k);
             const bool epc = !(k + 1 < K && levset[k + 1].count(r));
             // phi(k, r) is read at level k + 1 by r and its six neighbours
-            if (epc) ephi = true;
+            bool ephi = epc;
             for (const auto &d : kNb)
                 if (!(k + 1 < K && levset[k + 1].count(add(r, d)))) ephi = true;
-            uint64_t e = (uint64_t)sl | (uint64_t)pcidx.at(r) << 12 | (uint64_t)(uint8_t)(int8_t)ym << 24 |
-                         (uint64_t)(uint8_t)(int8_t)yp << 32 | (uint64_t)(zm & 1023) << 40 | (uint64_t)(zp & 1023) << 50;
+            uint32_t e = entry_of(r);
             if (ephi) e |= kLatExpPhi, ++t->exports_phi;
             if (epc) e |= kLatExpPc, ++t->exports_pc;
             t->cell.push_back(e);
         }
+        t->cell_n[k] = (int32_t)t->cell.size() - t->cell_off[k];
+        pad4(&t->cell);
+        t->max_cell_n = std::max(t->max_cell_n, (int)t->cell.size() - t->cell_off[k]);
     }
     t->cell_off[K] = (int32_t)t->cell.size();
 
     // imports before level k: full (cells entering), phi only (neighbours outside)
     t->imp_off.assign(K + 1, 0);
+    t->imp_n.assign(K, 0);
     for (int k = 0; k < K; ++k) {
         t->imp_off[k] = (int32_t)t->imp.size();
-        std::set<int> full, phi;
+        std::set<R3> full, phi;
         for (const R3 &r : lev[k]) {
-            if (!(k > 0 && levset[k - 1].count(r))) full.insert(slot.at(r));
+            if (!(k > 0 && levset[k - 1].count(r))) full.insert(r);
             for (const auto &d : kNb) {
                 const R3 q = add(r, d);
                 if ((k > 0 && levset[k - 1].count(q)) || levset[k].count(q)) continue;
-                phi.insert(slot.at(q));
+                phi.insert(q);
             }
         }
-        std::vector<uint16_t> list;
-        for (int sl : full) list.push_back((uint16_t)(sl | kLatImpFull));
-        for (int sl : phi) list.push_back((uint16_t)sl);
-        std::sort(list.begin(), list.end(), [](uint16_t a, uint16_t b) { return (a & 0x7fff) < (b & 0x7fff); });
-        t->imp.insert(t->imp.end(), list.begin(), list.end());
+        std::vector<std::pair<int, uint32_t>> list;  // ascending slots
+        for (const R3 &r : full) list.push_back({slot.at(r), entry_of(r) | kLatImpFull});
+        for (const R3 &r : phi) list.push_back({slot.at(r), entry_of(r)});
+        std::sort(list.begin(), list.end());
+        for (const auto &e : list) t->imp.push_back(e.second);
+        t->imp_n[k] = (int32_t)list.size();
+        pad4(&t->imp);
+        t->max_imp_n = std::max(t->max_imp_n, (int)t->imp.size() - t->imp_off[k]);
         t->imports_full += (int64_t)full.size();
         t->imports_phi += (int64_t)phi.size();
     }
@@ -183,39 +224,71 @@ std::string build_lattice_tables(int s, LatticeTables *t)
     t->bytes_read = 24 * t->imports_full + 8 * t->imports_phi;
     t->bytes_written = 8 * t->exports_phi + 16 * t->exports_pc;
 
-    // check 1: every value level k reads is computed at level k - 1 or imported before level k
-    std::map<R3, int> by_slot_r;
-    for (const auto &e : slot) by_slot_r[e.first] = e.second;
+    // decode an entry as the kernel does: offset, neighbour slots, (pi, c) index
+    auto decode = [&](uint32_t e, R3 *r, int nb[7], int *pc) {
+        const int sl = lat_slot(e), row = lat_row(e);
+        t->offset_of(sl, row, &r->x, &r->y, &r->z);
+        const uint64_t v = t->row_nb[row];
+        nb[0] = sl, nb[1] = sl - 1, nb[2] = sl + 1;
+        nb[3] = sl + lat_dym(v), nb[4] = sl + lat_dyp(v), nb[5] = sl + lat_dzm(v), nb[6] = sl + lat_dzp(v);
+        *pc = sl + lat_dpc(v);
+    };
+
+    // check 1: entries decode to their cells, and every value level k reads
+    // is computed at level k - 1 or imported before level k
     for (int k = 0; k < K; ++k) {
         std::set<int> have_phi, have_pc;
         if (k > 0)
-            for (const R3 &r : lev[k - 1]) have_phi.insert(slot.at(r)), have_pc.insert(slot.at(r));
-        for (int i = t->imp_off[k]; i < t->imp_off[k + 1]; ++i) {
-            const int sl = t->imp[i] & 0x7fff;
-            if (have_phi.count(sl)) return fail("level %d imports a value it already holds", k);
-            have_phi.insert(sl);
-            if (t->imp[i] & kLatImpFull) have_pc.insert(sl);
+            for (int i = t->cell_off[k - 1]; i < t->cell_off[k - 1] + t->cell_n[k - 1]; ++i) {
+                R3 r;
+                int nb[7], pc;
+                decode(t->cell[i], &r, nb, &pc);
+                have_phi.insert(nb[0]);
+                have_pc.insert(pc);
+            }
+        for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i) {
+            R3 r;
+            int nb[7], pc;
+            decode(t->imp[i], &r, nb, &pc);
+            if (slot.at(r) != nb[0]) return fail("import entry does not decode to its cell (level %d)", k);
+            if (have_phi.count(nb[0])) return fail("level %d imports a value it already holds", k);
+            have_phi.insert(nb[0]);
+            if (t->imp[i] & kLatImpFull) {
+                if (pc != pcidx.at(r)) return fail("full import with a wrong (pi, c) index");
+                have_pc.insert(pc);
+            }
         }
-        for (const R3 &r : lev[k]) {
-            if (!have_pc.count(slot.at(r)) || !have_phi.count(slot.at(r))) return fail("level %d lacks a cell's own state", k);
-            for (const auto &d : kNb)
-                if (!have_phi.count(slot.at(add(r, d)))) return fail("level %d lacks a neighbour's phi", k);
+        int n = 0;
+        for (int i = t->cell_off[k]; i < t->cell_off[k] + t->cell_n[k]; ++i, ++n) {
+            R3 r;
+            int nb[7], pc;
+            decode(t->cell[i], &r, nb, &pc);
+            if (!(r == lev[k][n]) || slot.at(r) != nb[0] || pc != pcidx.at(r))
+                return fail("cell entry does not decode to its cell (level %d)", k);
+            for (int d = 0; d < 6; ++d)
+                if (nb[1 + d] != slot.at(add(r, kNb[d]))) return fail("neighbour slot wrong at level %d", k);
+            if (!have_pc.count(pc) || !have_phi.count(nb[0])) return fail("level %d lacks a cell's own state", k);
+            for (int d = 1; d < 7; ++d)
+                if (!have_phi.count(nb[d])) return fail("level %d lacks a neighbour's phi", k);
         }
     }
 
     // check 2: every import is exported by the region computing it.  Place
     // the region at the origin (centre 0, bottom vertex at t = 0); the value
     // imported before level k is at (k - 1, r).
-    std::vector<std::map<R3, uint64_t>> entry(K);
+    std::vector<std::map<R3, uint32_t>> entry(K);
     for (int k = 0; k < K; ++k)
-        for (int i = t->cell_off[k]; i < t->cell_off[k + 1]; ++i) {
-            const uint32_t rec = t->slot_rec[t->cell[i] & 0xfff];
-            entry[k][{(int)(rec & 31) - R, (int)(rec >> 5 & 31) - R, (int)(rec >> 10 & 31) - R}] = t->cell[i];
+        for (int i = t->cell_off[k]; i < t->cell_off[k] + t->cell_n[k]; ++i) {
+            R3 r;
+            int nb[7], pc;
+            decode(t->cell[i], &r, nb, &pc);
+            entry[k][r] = t->cell[i];
         }
     for (int k = 0; k < K; ++k)
-        for (int i = t->imp_off[k]; i < t->imp_off[k + 1]; ++i) {
-            const uint32_t rec = t->slot_rec[t->imp[i] & 0x7fff];
-            const R3 r = {(int)(rec & 31) - R, (int)(rec >> 5 & 31) - R, (int)(rec >> 10 & 31) - R};
+        for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i) {
+            R3 r;
+            int nb[7], pc;
+            decode(t->imp[i], &r, nb, &pc);
             int kp;
             R3 rp;
             locate(s, k - 1, r, &kp, &rp);
@@ -224,7 +297,8 @@ std::string build_lattice_tables(int s, LatticeTables *t)
             auto it = entry[kp].find(rp);
             if (it == entry[kp].end()) return fail("producer cell missing at level %d", kp);
             if (!(it->second & kLatExpPhi)) return fail("imported phi not exported (level %d)", k);
-            if ((t->imp[i] & kLatImpFull) && !(it->second & kLatExpPc)) return fail("imported (pi, c) not exported (level %d)", k);
+            if ((t->imp[i] & kLatImpFull) && !(it->second & kLatExpPc))
+                return fail("imported (pi, c) not exported (level %d)", k);
         }
     // check 3: the local membership agrees with the lattice forms for every
     // point of the region placed at the origin

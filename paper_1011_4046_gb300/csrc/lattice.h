@@ -65,37 +65,64 @@ namespace sp {
 constexpr int kLatMinS = 1;
 constexpr int kLatMaxS = 6;  // slot indices are 12 bits, coordinates 5 bits per axis
 
-// Cell entry of one computed cell (64 bits), the kernel's per-level work list:
-//   bits  0..11 shared-memory slot of the cell (its phi in both parity buffers)
-//   bits 12..23 index of its (pi, c) pair (footprint cells only)
-//   bits 24..31 slot(y - 1) - slot (signed 8 bits); bits 32..39 slot(y + 1) - slot
-//   bits 40..49 slot(z - 1) - slot (signed 10 bits); bits 50..59 slot(z + 1) - slot
-//   bit 60 export phi at this level; bit 61 export (pi, c) at this level
-// x neighbours are slot - 1 and slot + 1 (rows are contiguous in x).
-constexpr int kLatCellSlotBits = 12;
-constexpr uint64_t kLatExpPhi = 1ull << 60;
-constexpr uint64_t kLatExpPc = 1ull << 61;
+// Shared-memory phi slots are laid out in rows of constant (y, z), each
+// contiguous in x, rows in (z, y) order: slot(r) = row_base(row) + rx with
+// row = (ry + 2s) (4s + 1) + rz + 2s.  The x neighbours are slot - 1 and
+// slot + 1; the y and z neighbours and the (pi, c) index follow from
+// per-row constants:
+//   row_nb (64 bits): slot(y - 1) - slot (bits 0..7, signed),
+//     slot(y + 1) - slot (8..15), slot(z - 1) - slot (16..27, signed 12 bits),
+//     slot(z + 1) - slot (28..39), pc - slot (40..52, signed 13 bits);
+//   row_xy (32 bits): row_base (bits 0..15, signed) | (ry + 2s) << 16 |
+//     (rz + 2s) << 21, for the cell's offset from the region's centre.
+// Cell entry (32 bits), the per-level work list:
+//   bits 0..11 slot; bits 12..21 row; bit 22 export phi at this level;
+//   bit 23 export (pi, c) at this level.
+// Import entry (32 bits): slot | row << 12 | full << 22.  A full import
+// loads phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k;
+// otherwise only phi(k-1) of a neighbour outside the region.
+// Every level's lists start on a 16-byte boundary (padded with zero entries
+// to a multiple of four).
+constexpr uint32_t kLatSlotMask = 0xfffu;
+constexpr int kLatRowShift = 12;
+constexpr uint32_t kLatRowMask = 0x3ffu;
+constexpr uint32_t kLatExpPhi = 1u << 22;
+constexpr uint32_t kLatExpPc = 1u << 23;
+constexpr uint32_t kLatImpFull = 1u << 22;
 
-// Import entry (16 bits): slot | full << 15.  A full import loads phi(k-1)
-// and (pi, c)(k-1) of a cell entering the region at level k; otherwise only
-// phi(k-1) of a neighbour outside the region.
-constexpr uint16_t kLatImpFull = 1u << 15;
+LAT_HD int lat_slot(uint32_t e) { return (int)(e & kLatSlotMask); }
+LAT_HD int lat_row(uint32_t e) { return (int)((e >> kLatRowShift) & kLatRowMask); }
+LAT_HD int lat_sext(uint64_t v, int bits) { return (int)((int64_t)(v << (64 - bits)) >> (64 - bits)); }
+LAT_HD int lat_dym(uint64_t nb) { return lat_sext(nb, 8); }
+LAT_HD int lat_dyp(uint64_t nb) { return lat_sext(nb >> 8, 8); }
+LAT_HD int lat_dzm(uint64_t nb) { return lat_sext(nb >> 16, 12); }
+LAT_HD int lat_dzp(uint64_t nb) { return lat_sext(nb >> 28, 12); }
+LAT_HD int lat_dpc(uint64_t nb) { return lat_sext(nb >> 40, 13); }
+LAT_HD int lat_row_base(uint32_t xy) { return (int)(int16_t)(xy & 0xffffu); }
 
-// Slot record (32 bits): (rx + 2s) | (ry + 2s) << 5 | (rz + 2s) << 10 |
-// (pi, c) index << 15 | footprint << 27.  Offsets r are relative to the
-// region's centre, |r_d| <= 2s.
 struct LatticeTables {
-    int s = 0, K = 0;           // K = 4s levels per region
-    int n_slots = 0, n_foot = 0;  // phi slots (footprint + halo, row layout), (pi, c) slots
-    std::vector<uint64_t> cell;   // level k: cell[cell_off[k] .. cell_off[k+1])
-    std::vector<int32_t> cell_off;  // K + 1
-    std::vector<uint16_t> imp;    // before level k: imp[imp_off[k] .. imp_off[k+1]), ascending slots
-    std::vector<int32_t> imp_off;   // K + 1
-    std::vector<uint32_t> slot_rec;  // n_slots
+    int s = 0, K = 0;             // K = 4s levels per region
+    int n_slots = 0, n_foot = 0;  // phi slots (footprint + halo), (pi, c) slots
+    int rb_side = 0;              // 4s + 1: rows are indexed (ry + 2s) rb_side + rz + 2s
+    std::vector<uint64_t> row_nb;   // rb_side^2
+    std::vector<uint32_t> row_xy;   // rb_side^2
+    std::vector<uint32_t> cell;     // level k: cell[cell_off[k] .. cell_off[k] + cell_n[k]), padded
+    std::vector<int32_t> cell_off, cell_n;  // K + 1 offsets (multiples of 4), K counts
+    std::vector<uint32_t> imp;      // before level k: imp[imp_off[k] .. imp_off[k] + imp_n[k]), padded
+    std::vector<int32_t> imp_off, imp_n;
+    int max_cell_n = 0, max_imp_n = 0;  // padded to multiples of 4
     // one whole region: site-updates, bytes read and written (this design)
     int64_t updates = 0, bytes_read = 0, bytes_written = 0;
     int64_t imports_full = 0, imports_phi = 0, exports_phi = 0, exports_pc = 0;
     int max_level_cells = 0;
+    // offset of the cell in slot sl of row `row` from the region's centre
+    void offset_of(int sl, int row, int *rx, int *ry, int *rz) const
+    {
+        const uint32_t xy = row_xy[row];
+        *rx = sl - lat_row_base(xy);
+        *ry = (int)((xy >> 16) & 31u) - 2 * s;
+        *rz = (int)((xy >> 21) & 31u) - 2 * s;
+    }
 };
 
 // Builds the tables of lattice size s (kLatMinS..kLatMaxS) and checks them:
@@ -134,15 +161,17 @@ LAT_HD void lat_next_epoch(int *last, int layers, int *first)
 }
 
 // Centre of region idx of layer L in units of s: a_d in [0, 4 M_d), all
-// congruent to L mod 2, a_0 + a_1 + a_2 congruent to -L mod 4.
-LAT_HD void lat_centre(const LatGeom &g, int L, int64_t idx, int a[3])
+// congruent to L mod 2, a_0 + a_1 + a_2 congruent to -L mod 4.  (I: the
+// index type; the kernel uses 32-bit indices within one simulation.)
+template <class I>
+LAT_HD void lat_centre(const LatGeom &g, int L, I idx, int a[3])
 {
     const int p = L & 1;
     const int q = ((-L - 3 * p) & 3) >> 1;  // parity of a'_0 + a'_1 + a'_2, a_d = 2 a'_d + p
-    const int64_t h = idx % g.M[0];
-    const int64_t rest = idx / g.M[0];
-    const int b1 = (int)(rest % (2 * g.M[1]));
-    const int b2 = (int)(rest / (2 * g.M[1]));
+    const I h = idx % (I)g.M[0];
+    const I rest = idx / (I)g.M[0];
+    const int b1 = (int)(rest % (I)(2 * g.M[1]));
+    const int b2 = (int)(rest / (I)(2 * g.M[1]));
     const int b0 = 2 * (int)h + ((q + b1 + b2) & 1);
     a[0] = 2 * b0 + p;
     a[1] = 2 * b1 + p;
@@ -150,10 +179,11 @@ LAT_HD void lat_centre(const LatGeom &g, int L, int64_t idx, int a[3])
 }
 
 // Inverse of lat_centre (a_d reduced mod 4 M_d by the caller).
-LAT_HD int64_t lat_index(const LatGeom &g, const int a[3])
+template <class I>
+LAT_HD I lat_index(const LatGeom &g, const int a[3])
 {
     const int b0 = a[0] >> 1, b1 = a[1] >> 1, b2 = a[2] >> 1;
-    return ((int64_t)b2 * (2 * g.M[1]) + b1) * g.M[0] + (b0 >> 1);
+    return ((I)b2 * (I)(2 * g.M[1]) + (I)b1) * (I)g.M[0] + (I)(b0 >> 1);
 }
 
 // Centre shift (units of s) from a region to its predecessor n - e_i; the
@@ -171,14 +201,24 @@ LAT_HD int lat_wrap(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// Index of the predecessor n - e_i of region (L, idx) in layer L - 1.
-LAT_HD int64_t lat_pred(const LatGeom &g, int L, int64_t idx, int i)
+// Index of the predecessor n - e_i of the region with centre a (layer L) in
+// layer L - 1.
+template <class I>
+LAT_HD I lat_pred_of(const LatGeom &g, const int a[3], int i)
 {
-    int a[3], d[3];
-    lat_centre(g, L, idx, a);
+    int b[3], d[3];
     lat_pred_shift(i, d);
-    for (int k = 0; k < 3; ++k) a[k] = lat_wrap(a[k] + d[k], 4 * g.M[k]);
-    return lat_index(g, a);
+    for (int k = 0; k < 3; ++k) b[k] = lat_wrap(a[k] + d[k], 4 * g.M[k]);
+    return lat_index<I>(g, b);
+}
+
+// Index of the predecessor n - e_i of region (L, idx) in layer L - 1.
+template <class I>
+LAT_HD I lat_pred(const LatGeom &g, int L, I idx, int i)
+{
+    int a[3];
+    lat_centre(g, L, idx, a);
+    return lat_pred_of<I>(g, a, i);
 }
 
 }  // namespace sp

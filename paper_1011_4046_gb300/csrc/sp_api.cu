@@ -54,9 +54,10 @@ struct TablesOnDevice {
 // The 4-cube lattice tables of one size s (lattice.h) on the device.
 struct LatOnDevice {
     sp::LatticeTables host;
-    unsigned long long *d_cell = nullptr;
-    unsigned short *d_imp = nullptr;
-    unsigned *d_rec = nullptr;
+    uint32_t *d_cell = nullptr;
+    uint32_t *d_imp = nullptr;
+    uint64_t *d_nb = nullptr;
+    uint32_t *d_xy = nullptr;
 };
 
 // One persistent launch per region base: simulations of the same base share a
@@ -629,7 +630,8 @@ void free_plan(sp_grid *g)
     for (auto &kv : g->lat) {
         cudaFree(kv.second.d_cell);
         cudaFree(kv.second.d_imp);
-        cudaFree(kv.second.d_rec);
+        cudaFree(kv.second.d_nb);
+        cudaFree(kv.second.d_xy);
     }
     g->lat.clear();
     for (float2 *f : g->phi_odd) cudaFree(f);
@@ -961,13 +963,19 @@ int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
         a.total = (unsigned)(per_layer_all * Lcount);
         a.cell = ld.d_cell;
         a.imp = ld.d_imp;
-        a.slot_rec = ld.d_rec;
+        a.row_nb = ld.d_nb;
+        a.row_xy = ld.d_xy;
+        a.max_cell_n = t.max_cell_n;
         a.flags = g->d_lat_flags + g->lat_flag_off[gi];
         a.ctl = g->d_ctl + gi;
         a.fault_drop = g->fault_drop;
         for (int k = 0; k <= t.K; ++k) {
             a.cell_off[k] = t.cell_off[k];
             a.imp_off[k] = t.imp_off[k];
+            if (k < t.K) {
+                a.cell_n[k] = t.cell_n[k];
+                a.imp_n[k] = t.imp_n[k];
+            }
         }
         sim_off.push_back(first);
         launches.push_back(l);
@@ -1117,8 +1125,7 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
     free_plan(g);
     if (g->model) sp_model_destroy(g->model);
     g->model = nullptr;
-    if (threads == 0) threads = 128;
-    if (!sp::lattice_valid_threads(threads)) return SP_EINVAL;
+    if (threads != 0 && !sp::lattice_valid_threads(threads)) return SP_EINVAL;
     g->B = Bs;
     g->max_B = 0;
     cudaError_t e = cudaSuccess;
@@ -1129,15 +1136,18 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         LatOnDevice &ld = g->lat[s];
         if (!sp::build_lattice_tables(s, &ld.host).empty()) return SP_EINVAL;
         const sp::LatticeTables &t = ld.host;
-        e = cudaMalloc((void **)&ld.d_cell, t.cell.size() * sizeof(unsigned long long));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp, std::max<size_t>(t.imp.size(), 1) * sizeof(uint16_t));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_rec, t.slot_rec.size() * sizeof(uint32_t));
+        e = cudaMalloc((void **)&ld.d_cell, t.cell.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp, std::max<size_t>(t.imp.size(), 4) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_nb, t.row_nb.size() * sizeof(uint64_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_xy, t.row_xy.size() * sizeof(uint32_t));
         if (e == cudaSuccess)
-            e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !t.imp.empty())
-            e = cudaMemcpy(ld.d_imp, t.imp.data(), t.imp.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(ld.d_imp, t.imp.data(), t.imp.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(ld.d_rec, t.slot_rec.data(), t.slot_rec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(ld.d_nb, t.row_nb.data(), t.row_nb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ld.d_xy, t.row_xy.data(), t.row_xy.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_plan(g);
             return SP_ENOMEM;
@@ -1148,10 +1158,13 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         const sp::LatticeTables &t = it->second.host;
         GroupCfg c;
         c.B = 4 * it->first;
+        // default: the fewest workers (at least 128) whose registers hold a level's entries
         c.threads = threads;
-        c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot);
-        if (c.smem > 227 * 1024) return SP_EINVAL;
-        e = sp::lattice_occupancy(threads, c.smem, &c.ctas_per_sm);
+        for (int nt : {128, 256, 512})
+            if (!c.threads && sp::lattice_threads_fit(nt, t.max_imp_n)) c.threads = nt;
+        c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot, t.rb_side, t.max_cell_n);
+        if (c.smem > 227 * 1024 || !sp::lattice_threads_fit(c.threads, t.max_imp_n)) return SP_EINVAL;
+        e = sp::lattice_occupancy(c.threads, c.smem, &c.ctas_per_sm);
         if (e != cudaSuccess || c.ctas_per_sm < 1) return SP_EINVAL;
         c.grid = c.ctas_per_sm * g->sm_count;
         g->groups.push_back(c);
@@ -1307,7 +1320,7 @@ int autotune_lattice(sp_grid *g, int base_B, int block_shape, std::vector<int> *
     }
     if (sizes.empty()) return SP_EINVAL;
     const std::vector<int> shapes =
-        block_shape == SP_AUTOTUNE ? std::vector<int>{64, 128, 256} : std::vector<int>{block_shape ? block_shape : 128};
+        block_shape == SP_AUTOTUNE ? std::vector<int>{64, 128, 256, 512} : std::vector<int>{block_shape};
     constexpr int kTrialSteps = 32;
     double best = 0.0;
     bool have = false;
@@ -1352,7 +1365,7 @@ int autotune_lattice(sp_grid *g, int base_B, int block_shape, std::vector<int> *
             }
             ++g->tune.candidates;
             const double per = ms / updates;
-            if ((B == 16 || B == 0) && nt == 128) g->tune.default_ms = ms;
+            if ((B == 16 || B == 0) && (nt == 128 || nt == 0)) g->tune.default_ms = ms;
             if (!have || per < best) {
                 best = per;
                 have = true;

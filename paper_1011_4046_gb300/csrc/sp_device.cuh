@@ -183,14 +183,17 @@ struct LatArgs {
     int n_slots, n_foot, Lcount, pad0;
     long long fault_drop;            // region id (as in the trace) that never reports done (-1: none)
     unsigned per_layer_all, total;
-    const unsigned long long *cell;  // cell entries (lattice.h), all levels
-    const unsigned short *imp;       // import entries, all levels
-    const unsigned *slot_rec;        // slot records
+    const uint32_t *cell;            // cell entries (lattice.h), all levels (16-byte aligned per level)
+    const uint32_t *imp;             // import entries, all levels
+    const uint64_t *row_nb;          // (4s + 1)^2 row records: neighbour steps, (pi, c) offset
+    const uint32_t *row_xy;          // (4s + 1)^2 row records: slot base, (y, z) offsets
+    int max_cell_n, pad1;            // longest level's cell list (padded)
     int *flags;
     Ctl *ctl;
     unsigned long long *trace;       // optional (start, end) globaltimer per region: simulation by
                                      // simulation, layer by layer (trace_base + layer * per_layer + idx)
-    int cell_off[4 * 6 + 1], imp_off[4 * 6 + 1];
+    int cell_off[4 * 6 + 1], imp_off[4 * 6 + 1];  // per level (entries)
+    int cell_n[4 * 6], imp_n[4 * 6];
 };
 
 struct RegionArgs {
@@ -288,6 +291,11 @@ __device__ __forceinline__ void named_arrive(int id, int nthreads)
 __device__ __forceinline__ void st_release_gpu(int *p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(int *p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int atom_add_acq_rel_gpu(int *p, int v)

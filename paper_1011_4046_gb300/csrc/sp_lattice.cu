@@ -14,8 +14,17 @@
 //      sp_update.h), writing every value another region needs (a per-cell
 //      flag of the tables) straight into the state arrays,
 //   4. reports done with a release store of its layer number.
+// The per-level lists (cell and import entries, lattice.h) are the same for
+// every region: a level's cell entries are copied into shared memory a level
+// ahead (cp.async), each thread's import entries are held in registers a
+// level ahead, so no table read waits on memory.  A cell's neighbours and
+// (pi, c) slot follow from its slot and one 64-bit per-row record; the row
+// tables are copied into shared memory once per launch.
+//
 // Regions are handed out by ticket in layer order (one atomic per region,
-// taken a region ahead).  A ticket's predecessors hold smaller tickets, and
+// taken a region ahead; the next region's predecessor flags are read early,
+// relaxed, and one fence per region serves as the release of its writes and
+// the acquire of those reads).  A ticket's predecessors hold smaller tickets, and
 // a CTA holding a ticket is running or will run it next, so the waits always
 // end; each is bounded anyway.  The manager of the paper (Sec. 4) is thus
 // reduced to a counter and one flag per region.
@@ -30,50 +39,51 @@ namespace sp {
 
 namespace {
 
+// Import entries per thread and level held in registers (loaded a level ahead).
+constexpr int kLatUI = 4;
+
+// Shared-memory layout of one region (bytes): (pi, c) slots, the two phi
+// buffers, the row tables and a ring of two levels' cell entries.
+struct LatSmem {
+    size_t pc, ph0, ph1, nb, xy, ring, total;
+    __host__ __device__ LatSmem(int n_slots, int n_foot, int W, int max_cell_n)
+    {
+        pc = 0;
+        ph0 = 16 * (size_t)n_foot;
+        ph1 = ph0 + 8 * (size_t)n_slots;
+        nb = ph1 + 8 * (size_t)n_slots;
+        nb = (nb + 15) & ~(size_t)15;
+        xy = nb + 8 * (size_t)W * W;
+        ring = (xy + 4 * (size_t)W * W + 15) & ~(size_t)15;
+        total = ring + 2 * 4 * (size_t)max_cell_n;
+    }
+};
+
 struct LatRegion {
     int sim, L, Labs, tau_b, k_lo, k_hi;
     int c[3];        // centre, cells
     unsigned t, j;   // ticket, region within the layer (all simulations)
     long long id;    // trace / fault-injection id
+    int pred[4];     // predecessors' flag indices (-1: none)
 };
 
-__device__ __forceinline__ int sext10(unsigned v) { return ((int)(v & 1023u) ^ 512) - 512; }
-
-__device__ __forceinline__ long long site_at(const LatSimDev &sd, const int c[3], unsigned rec, int R)
+// Decode ticket t (no waiting).  Returns false when the tickets are exhausted.
+__device__ bool lat_decode(const LatArgs &a, unsigned t, int epoch, LatRegion *out)
 {
-    int x = c[0] + (int)(rec & 31u) - R;
-    int y = c[1] + (int)((rec >> 5) & 31u) - R;
-    int z = c[2] + (int)((rec >> 10) & 31u) - R;
-    x += x < 0 ? sd.n[0] : 0;
-    x -= x >= sd.n[0] ? sd.n[0] : 0;
-    y += y < 0 ? sd.n[1] : 0;
-    y -= y >= sd.n[1] ? sd.n[1] : 0;
-    z += z < 0 ? sd.n[2] : 0;
-    z -= z >= sd.n[2] ? sd.n[2] : 0;
-    return (long long)x + (long long)sd.n[0] * ((long long)y + (long long)sd.n[1] * z);
-}
-
-// Thread 0: decode ticket t and wait (bounded) for its predecessors.  Sets
-// *stop when the tickets are exhausted or a wait gave up.
-__device__ void lat_claim(const LatArgs &a, unsigned t, int epoch, LatRegion *out, int *stop)
-{
-    if (t >= a.total) {
-        *stop = 1;
-        return;
-    }
+    if (t >= a.total) return false;
     const unsigned li = t / a.per_layer_all;
     const unsigned j = t - li * a.per_layer_all;
     int sim = 0;
     while (sim + 1 < a.n_sims && (long long)j >= a.sims[sim + 1].region_base) ++sim;
     const LatSimDev &sd = a.sims[sim];
-    const long long idx = (long long)j - sd.region_base;
+    const int idx = (int)((long long)j - sd.region_base);  // < 2^31 regions per layer of one simulation
     LatGeom g;
     g.s = a.s;
     g.M[0] = sd.M[0], g.M[1] = sd.M[1], g.M[2] = sd.M[2];
     const int L = lat_min_layer() + (int)li;
     int ctr[3];
     lat_centre(g, L, idx, ctr);
-    LatRegion r;
+    LatRegion &r = *out;
     r.sim = sim;
     r.L = L;
     r.Labs = epoch + (int)li;
@@ -84,161 +94,269 @@ __device__ void lat_claim(const LatArgs &a, unsigned t, int epoch, LatRegion *ou
     r.t = t;
     r.j = j;
     r.id = sd.trace_base + (long long)li * sd.per_layer + idx;
-    if (li > 0) {
-        const unsigned long long t0 = globaltimer_ns();
-        const unsigned long long limit = a.ctl->wait_limit_ns;
-        const int need = r.Labs - 1;
-        const int *fl = a.flags + (size_t)((need & 3) * a.per_layer_all) + sd.region_base;
-        for (int i = 0; i < 4; ++i) {
-            const int *f = fl + lat_pred(g, L, idx, i);
-            unsigned spins = 0;
-            while (ld_acquire_gpu(f) < need) {
-                if ((++spins & 63u) == 0) {
-                    if (ld_relaxed_gpu(&a.ctl->error) != 0) {
-                        *stop = 1;
-                        return;
-                    }
-                    if (globaltimer_ns() - t0 > limit) {
-                        if (atomicCAS(&a.ctl->error, 0, (int)kDevTimeout) == 0) a.ctl->error_info = (int)t;
-                        *stop = 1;
-                        return;
-                    }
-                }
-                __nanosleep(100);
-            }
-        }
-    }
-    *out = r;
+    const long long base = (long long)((r.Labs - 1) & 3) * a.per_layer_all + sd.region_base;
+    for (int i = 0; i < 4; ++i) r.pred[i] = li > 0 ? (int)(base + lat_pred_of<int>(g, ctr, i)) : -1;
+    return true;
 }
 
-// Copies (cp.async) of the values imported before level k: phi(k - 1) of the
-// halo into phi buffer (k - 1) & 1, and (pi, c)(k - 1) of cells entering.
-template <int NW>
-__device__ __forceinline__ void lat_imports(const LatArgs &a, const LatSimDev &sd, const LatRegion &r, int k, int lo,
-                                            int hi, float4 *s_pc, float2 *s_ph, const float2 *gphi, int R)
+// Thread 0: bounded wait until every predecessor of r has reported done
+// (acquire).  False (and the error word set) when a wait gave up or another
+// CTA failed.
+__device__ bool lat_wait(const LatArgs &a, const LatRegion &r)
 {
-    for (int i = lo + (int)threadIdx.x; i < hi; i += NW) {
-        const unsigned e = __ldg(a.imp + i);
-        const unsigned sl = e & 0x7fffu;
-        const unsigned rec = __ldg(a.slot_rec + sl);
-        const long long g = site_at(sd, r.c, rec, R);
-        cp_async8(s_ph + sl, gphi + g);
-        if (e & kLatImpFull) cp_async16(s_pc + ((rec >> 15) & 0xfffu), sd.pc + g);
+    const int need = r.Labs - 1;
+    const unsigned long long t0 = globaltimer_ns();
+    const unsigned long long limit = a.ctl->wait_limit_ns;
+    for (int i = 0; i < 4; ++i) {
+        if (r.pred[i] < 0) continue;
+        unsigned spins = 0;
+        while (ld_acquire_gpu(a.flags + r.pred[i]) < need) {
+            if ((++spins & 63u) == 0) {
+                if (ld_relaxed_gpu(&a.ctl->error) != 0) return false;
+                if (globaltimer_ns() - t0 > limit) {
+                    if (atomicCAS(&a.ctl->error, 0, (int)kDevTimeout) == 0) a.ctl->error_info = (int)r.t;
+                    return false;
+                }
+            }
+            __nanosleep(100);
+        }
     }
+    return true;
+}
+
+// Site index of the cell at offset r from the region's centre: one wrap per
+// axis where the region crosses the grid's seam, plain arithmetic elsewhere.
+struct SiteMap {
+    int n0, n1, n2;
+    int c0, c1, c2;
+    long long gc;  // site index of the centre
+    bool nowrap;
+    __device__ __forceinline__ long long at(int rx, int ry, int rz) const
+    {
+        if (nowrap) return gc + rx + (long long)n0 * (ry + n1 * rz);
+        int x = c0 + rx, y = c1 + ry, z = c2 + rz;
+        x += x < 0 ? n0 : 0;
+        x -= x >= n0 ? n0 : 0;
+        y += y < 0 ? n1 : 0;
+        y -= y >= n1 ? n1 : 0;
+        z += z < 0 ? n2 : 0;
+        z -= z >= n2 ? n2 : 0;
+        return (long long)x + (long long)n0 * ((long long)y + (long long)n1 * z);
+    }
+    // the cell in slot sl of a row with record xy
+    __device__ __forceinline__ long long of(int sl, uint32_t xy, int R) const
+    {
+        return at(sl - lat_row_base(xy), (int)((xy >> 16) & 31u) - R, (int)((xy >> 21) & 31u) - R);
+    }
+};
+
+template <int NW>
+__device__ __forceinline__ void load_imports(uint32_t (&v)[kLatUI], const uint32_t *__restrict__ tab, int off, int n)
+{
+#pragma unroll
+    for (int u = 0; u < kLatUI; ++u) {
+        const int i = (int)threadIdx.x + u * NW;
+        v[u] = i < n ? __ldg(tab + off + i) : 0u;
+    }
+}
+
+// cp.async of the values in entries v (imports of one level: phi of one
+// level into s_ph, and (pi, c) of full imports).
+template <int NW>
+__device__ __forceinline__ void issue_imports(const uint32_t (&v)[kLatUI], int n, const SiteMap &sm,
+                                              const uint64_t *s_nb, const uint32_t *s_xy, int R, float4 *s_pc,
+                                              float2 *s_ph, const float2 *gphi, const float4 *gpc)
+{
+#pragma unroll
+    for (int u = 0; u < kLatUI; ++u) {
+        if ((int)threadIdx.x + u * NW < n) {
+            const uint32_t e = v[u];
+            const int sl = lat_slot(e), row = lat_row(e);
+            const long long g = sm.of(sl, s_xy[row], R);
+            cp_async8(s_ph + sl, gphi + g);
+            if (e & kLatImpFull) cp_async16(s_pc + sl + lat_dpc(s_nb[row]), gpc + g);
+        }
+    }
+}
+
+// cp.async of the cell entries of one level (16-byte chunks; lists are padded)
+template <int NW>
+__device__ __forceinline__ void copy_entries(uint32_t *ring, const uint32_t *__restrict__ tab, int off, int n)
+{
+    const int n4 = (n + 3) & ~3;
+    for (int i = 4 * (int)threadIdx.x; i < n4; i += 4 * NW) cp_async16(ring + i, tab + off + i);
 }
 
 constexpr int kLatMinBlocks = 6;
 
 template <int NW>
-__global__ void __launch_bounds__(NW, (NW <= 128 ? kLatMinBlocks : 2)) lattice_kernel(const LatArgs a)
+__global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks : NW <= 256 ? 3 : 1))
+    lattice_kernel(const LatArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_cell_off[4 * kLatMaxS + 1], s_imp_off[4 * kLatMaxS + 1];
+    __shared__ int s_cell_off[4 * kLatMaxS + 1], s_cell_n[4 * kLatMaxS], s_imp_off[4 * kLatMaxS + 1],
+        s_imp_n[4 * kLatMaxS];
     __shared__ LatRegion s_reg;
     __shared__ int s_stop;
-    float4 *s_pc = reinterpret_cast<float4 *>(smem);
-    float2 *s_ph0 = reinterpret_cast<float2 *>(smem + 16 * (size_t)a.n_foot);
-    float2 *s_ph1 = s_ph0 + a.n_slots;
     const int tid = threadIdx.x;
-    const int R = 2 * a.s;
+    const int R = 2 * a.s, W = 4 * a.s + 1;
+    const LatSmem L(a.n_slots, a.n_foot, W, a.max_cell_n);
+    float4 *s_pc = reinterpret_cast<float4 *>(smem + L.pc);
+    float2 *s_ph0 = reinterpret_cast<float2 *>(smem + L.ph0);
+    float2 *s_ph1 = reinterpret_cast<float2 *>(smem + L.ph1);
+    uint64_t *s_nb = reinterpret_cast<uint64_t *>(smem + L.nb);
+    uint32_t *s_xy = reinterpret_cast<uint32_t *>(smem + L.xy);
+    uint32_t *s_ring = reinterpret_cast<uint32_t *>(smem + L.ring);
     if (tid <= a.K) {
         s_cell_off[tid] = a.cell_off[tid];
         s_imp_off[tid] = a.imp_off[tid];
+        if (tid < a.K) {
+            s_cell_n[tid] = a.cell_n[tid];
+            s_imp_n[tid] = a.imp_n[tid];
+        }
     }
+    for (int i = tid; i < W * W; i += NW) {
+        s_nb[i] = a.row_nb[i];
+        s_xy[i] = a.row_xy[i];
+    }
+    // thread 0's control state: the next ticket, and early (relaxed) reads of
+    // the flags of the region that ticket names
     unsigned next = 0;
     int epoch = 0;
+    int fv[4] = {0, 0, 0, 0};
+    bool early = false;
     if (tid == 0) {
         epoch = *(volatile int *)&a.ctl->epoch;
         s_stop = 0;
-        next = atomicAdd(&a.ctl->head, 1u);
-        lat_claim(a, next, epoch, &s_reg, &s_stop);
-        if (!s_stop) next = atomicAdd(&a.ctl->head, 1u);
+        const unsigned t = atomicAdd(&a.ctl->head, 1u);
+        if (!lat_decode(a, t, epoch, &s_reg) || !lat_wait(a, s_reg))
+            s_stop = 1;
+        else
+            next = atomicAdd(&a.ctl->head, 1u);
     }
     __syncthreads();
     while (!s_stop) {
         const LatRegion r = s_reg;
-        const LatSimDev &sd = a.sims[r.sim];
+        const LatSimDev &sdr = a.sims[r.sim];
+        SiteMap sm;
+        sm.n0 = sdr.n[0], sm.n1 = sdr.n[1], sm.n2 = sdr.n[2];
+        sm.c0 = r.c[0], sm.c1 = r.c[1], sm.c2 = r.c[2];
+        sm.gc = (long long)sm.c0 + (long long)sm.n0 * ((long long)sm.c1 + (long long)sm.n1 * sm.c2);
+        sm.nowrap = sm.c0 >= R && sm.c0 + R < sm.n0 && sm.c1 >= R && sm.c1 + R < sm.n1 && sm.c2 >= R &&
+                    sm.c2 + R < sm.n2;
+        const PhysConst q = sdr.q;
+        const LevelCoef *__restrict__ coef = sdr.coef;
+        float2 *const g_even = sdr.phi0;
+        float2 *const g_odd = sdr.phi1;
+        float4 *const gpc = sdr.pc;
         unsigned long long t_start = 0;
         if (tid == 0 && a.trace) t_start = globaltimer_ns();
-        const PhysConst q = sd.q;
-        float2 *const g_even = sd.phi0, *const g_odd = sd.phi1;
         const int par0 = r.tau_b & 1;  // level k of the region is global parity par0 ^ (k & 1)
+
         // a region cut by the call's first level: its own cells of level k_lo - 1, whole
         if (r.k_lo > 0) {
             const int kb = r.k_lo - 1;
             float2 *s_ph = (kb & 1) ? s_ph1 : s_ph0;
             const float2 *gp = (par0 ^ (kb & 1)) ? g_odd : g_even;
-            for (int i = s_cell_off[kb] + tid; i < s_cell_off[kb + 1]; i += NW) {
-                const unsigned long long e = __ldg(a.cell + i);
-                const unsigned sl = (unsigned)e & 0xfffu;
-                const long long g = site_at(sd, r.c, __ldg(a.slot_rec + sl), R);
+            const int off = s_cell_off[kb], n = s_cell_n[kb];
+            for (int i = tid; i < n; i += NW) {
+                const uint32_t e = __ldg(a.cell + off + i);
+                const int sl = lat_slot(e), row = lat_row(e);
+                const long long g = sm.of(sl, s_xy[row], R);
                 cp_async8(s_ph + sl, gp + g);
-                cp_async16(s_pc + ((unsigned)(e >> 12) & 0xfffu), sd.pc + g);
+                cp_async16(s_pc + sl + lat_dpc(s_nb[row]), gpc + g);
             }
         }
+        copy_entries<NW>(s_ring + (r.k_lo & 1) * a.max_cell_n, a.cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
+        uint32_t imp[kLatUI];
+        load_imports<NW>(imp, a.imp, s_imp_off[r.k_lo], s_imp_n[r.k_lo]);
         {
             const int kb = r.k_lo - 1;
-            lat_imports<NW>(a, sd, r, r.k_lo, s_imp_off[r.k_lo], s_imp_off[r.k_lo + 1], s_pc, (kb & 1) ? s_ph1 : s_ph0,
-                            (par0 ^ (kb & 1)) ? g_odd : g_even, R);
+            issue_imports<NW>(imp, s_imp_n[r.k_lo], sm, s_nb, s_xy, R, s_pc, (kb & 1) ? s_ph1 : s_ph0,
+                              (par0 ^ (kb & 1)) ? g_odd : g_even, gpc);
         }
+        if (r.k_lo < r.k_hi) load_imports<NW>(imp, a.imp, s_imp_off[r.k_lo + 1], s_imp_n[r.k_lo + 1]);
+        LevelCoef co = coef[r.tau_b + r.k_lo - 1];
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
         for (int k = r.k_lo; k <= r.k_hi; ++k) {
             const int odd = k & 1;
-            const float2 *rd = odd ? s_ph0 : s_ph1;
-            float2 *wr = odd ? s_ph1 : s_ph0;
-            if (k < r.k_hi) {  // next level's imports: values of level k, into buffer k & 1
-                lat_imports<NW>(a, sd, r, k + 1, s_imp_off[k + 1], s_imp_off[k + 2], s_pc, wr, (par0 ^ odd) ? g_odd : g_even,
-                                R);
+            const float2 *__restrict__ rd = odd ? s_ph0 : s_ph1;
+            float2 *__restrict__ wr = odd ? s_ph1 : s_ph0;
+            LevelCoef co_next = co;
+            if (k < r.k_hi) {
+                // imports of level k + 1 (values of level k, into buffer k & 1), the
+                // cell entries of level k + 1, then the import entries of level k + 2
+                issue_imports<NW>(imp, s_imp_n[k + 1], sm, s_nb, s_xy, R, s_pc, wr, (par0 ^ odd) ? g_odd : g_even,
+                                  gpc);
+                copy_entries<NW>(s_ring + ((k + 1) & 1) * a.max_cell_n, a.cell, s_cell_off[k + 1], s_cell_n[k + 1]);
                 cp_async_commit();
+                if (k + 1 < r.k_hi) load_imports<NW>(imp, a.imp, s_imp_off[k + 2], s_imp_n[k + 2]);
+                co_next = coef[r.tau_b + k];
             }
-            const LevelCoef co = sd.coef[r.tau_b + k - 1];
+            if (tid == 0 && k == r.k_lo) {
+                // every thread has copied the descriptor: decode the next
+                // region into it and read its predecessors' flags early
+                early = lat_decode(a, next, epoch, &s_reg);
+                if (early)
+                    for (int i = 0; i < 4; ++i)
+                        fv[i] = s_reg.pred[i] >= 0 ? ld_relaxed_gpu(a.flags + s_reg.pred[i]) : 0x7fffffff;
+            }
             float2 *gout = (par0 ^ odd) ? g_odd : g_even;
             const bool all = k == r.k_hi;
-            for (int i = s_cell_off[k] + tid; i < s_cell_off[k + 1]; i += NW) {
-                const unsigned long long e = __ldg(a.cell + i);
-                const int sl = (int)((unsigned)e & 0xfffu);
-                const int pcx = (int)((unsigned)(e >> 12) & 0xfffu);
-                const int ym = (int)(signed char)(unsigned char)(e >> 24);
-                const int yp = (int)(signed char)(unsigned char)(e >> 32);
-                const int zm = sext10((unsigned)(e >> 40));
-                const int zp = sext10((unsigned)(e >> 50));
+            const int n = s_cell_n[k];
+            const uint32_t *ent = s_ring + odd * a.max_cell_n;
+#pragma unroll 2
+            for (int i = tid; i < n; i += NW) {
+                const uint32_t e = ent[i];
+                const int sl = lat_slot(e), row = lat_row(e);
+                const uint64_t nb = s_nb[row];
+                const int pcx = sl + lat_dpc(nb);
                 const float4 v = s_pc[pcx];
                 float2 pi = make_float2(v.x, v.y), cc = make_float2(v.z, v.w);
-                const float2 out = site_update(rd[sl], rd[sl - 1], rd[sl + 1], rd[sl + ym], rd[sl + yp], rd[sl + zm],
-                                               rd[sl + zp], pi, cc, co, q);
+                const float2 out = site_update(rd[sl], rd[sl - 1], rd[sl + 1], rd[sl + lat_dym(nb)], rd[sl + lat_dyp(nb)],
+                                               rd[sl + lat_dzm(nb)], rd[sl + lat_dzp(nb)], pi, cc, co, q);
                 wr[sl] = out;
-                s_pc[pcx] = make_float4(pi.x, pi.y, cc.x, cc.y);
+                const float4 pcv = make_float4(pi.x, pi.y, cc.x, cc.y);
+                s_pc[pcx] = pcv;
                 const bool ephi = all || (e & kLatExpPhi), epc = all || (e & kLatExpPc);
                 if (ephi || epc) {
-                    const long long g = site_at(sd, r.c, __ldg(a.slot_rec + sl), R);
+                    const long long g = sm.of(sl, s_xy[row], R);
                     if (ephi) gout[g] = out;
-                    if (epc) sd.pc[g] = make_float4(pi.x, pi.y, cc.x, cc.y);
+                    if (epc) gpc[g] = pcv;
                 }
             }
             cp_async_wait_all();
             __syncthreads();
+            co = co_next;
         }
         if (tid == 0) {
             if (a.trace) {
                 a.trace[2 * r.id] = t_start;
                 a.trace[2 * r.id + 1] = globaltimer_ns();
             }
-            if (r.id != a.fault_drop) {
-                fence_acq_rel_gpu();
-                st_release_gpu(a.flags + (size_t)((r.Labs & 3) * a.per_layer_all) + r.j, r.Labs);
+            // One fence: release of this region's writes (made before the
+            // barrier above by every thread) to the flag store after it, and
+            // acquire for the early flag reads before it.
+            fence_acq_rel_gpu();
+            if (r.id != a.fault_drop) st_relaxed_gpu(a.flags + (size_t)((r.Labs & 3) * a.per_layer_all) + r.j, r.Labs);
+            if (!early) {
+                s_stop = 1;
+            } else {
+                const int need = s_reg.Labs - 1;
+                bool ready = true;
+                for (int i = 0; i < 4; ++i) ready = ready && fv[i] >= need;
+                if (!ready && !lat_wait(a, s_reg)) s_stop = 1;
+                if (!s_stop) next = atomicAdd(&a.ctl->head, 1u);
             }
-            lat_claim(a, next, epoch, &s_reg, &s_stop);
-            if (!s_stop) next = atomicAdd(&a.ctl->head, 1u);
         }
         __syncthreads();
     }
 }
 
 // Before every lattice call: a fresh ticket counter and error word, and the
-// call's layers numbered last_layer + 1 .. last_layer + layers, above every
-// done flag written before (the flags start at 0 and last_layer at 0).
+// call's layers numbered above every done flag written before.
 __global__ void lattice_reset_kernel(Ctl *ctl, int layers)
 {
     ctl->head = 0;
@@ -256,18 +374,40 @@ cudaError_t lattice_launch_t(const LatArgs &a, size_t smem, int grid, cudaStream
     return cudaGetLastError();
 }
 
+const void *lattice_fn(int threads)
+{
+    switch (threads) {
+    case 64:
+        return (const void *)lattice_kernel<64>;
+    case 128:
+        return (const void *)lattice_kernel<128>;
+    case 256:
+        return (const void *)lattice_kernel<256>;
+    case 512:
+        return (const void *)lattice_kernel<512>;
+    default:
+        return nullptr;
+    }
+}
+
 }  // namespace
 
-size_t lattice_smem_bytes(int n_slots, int n_foot) { return 16 * (size_t)n_foot + 16 * (size_t)n_slots; }
+size_t lattice_smem_bytes(int n_slots, int n_foot, int rb_side, int max_cell_n)
+{
+    return LatSmem(n_slots, n_foot, rb_side, max_cell_n).total;
+}
 
-bool lattice_valid_threads(int threads) { return threads == 64 || threads == 128 || threads == 256; }
+bool lattice_valid_threads(int threads) { return lattice_fn(threads) != nullptr; }
+
+// A worker count fits a lattice size when every level's imports fit the
+// entries each thread holds in registers.
+bool lattice_threads_fit(int threads, int max_imports) { return max_imports <= kLatUI * threads; }
 
 cudaError_t lattice_occupancy(int threads, size_t smem, int *blocks_per_sm)
 {
     *blocks_per_sm = 0;
-    const void *f = threads == 64 ? (const void *)lattice_kernel<64>
-                    : threads == 128 ? (const void *)lattice_kernel<128>
-                                     : (const void *)lattice_kernel<256>;
+    const void *f = lattice_fn(threads);
+    if (!f) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
@@ -288,6 +428,8 @@ cudaError_t launch_lattice(const LatArgs &a, int threads, size_t smem, int grid,
         return lattice_launch_t<128>(a, smem, grid, st);
     case 256:
         return lattice_launch_t<256>(a, smem, grid, st);
+    case 512:
+        return lattice_launch_t<512>(a, smem, grid, st);
     default:
         return cudaErrorInvalidValue;
     }

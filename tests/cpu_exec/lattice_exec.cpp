@@ -121,7 +121,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     c.Lcount = sp::lat_layer_count(s, nsteps);
     c.per_layer = sp::lat_per_layer(c.g);
     const int64_t sites = c.sites(), nreg = c.regions();
-    const int R = 2 * s;
 
     // global arrays with level tags
     std::vector<f2> P[2];
@@ -162,7 +161,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                 int d[3], b[3];
                 sp::lat_pred_shift(i, d);
                 for (int k = 0; k < 3; ++k) b[k] = sp::lat_wrap(a[k] - d[k], 4 * c.g.M[k]);
-                const int64_t sid = (int64_t)(L + 1 - c.Lmin) * c.per_layer + sp::lat_index(c.g, b);
+                const int64_t sid = (int64_t)(L + 1 - c.Lmin) * c.per_layer + sp::lat_index<int64_t>(c.g, b);
                 if (--cnt[sid] == 0) ready.push_back(sid);
             }
         }
@@ -177,7 +176,11 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         for (int k = 0; k < 3; ++k)
             if (a[k] < 0 || a[k] >= 4 * c.g.M[k] || ((a[k] - L) & 1)) return err("centre out of range"), finish(-1);
         if ((((a[0] + a[1] + a[2] + L) % 4) + 4) % 4 != 0) return err("centre off the layer's lattice"), finish(-1);
-        if (sp::lat_index(c.g, a) != id % c.per_layer) return err("lat_index does not invert lat_centre"), finish(-1);
+        if (sp::lat_index<int64_t>(c.g, a) != id % c.per_layer) return err("lat_index does not invert lat_centre"), finish(-1);
+        if (sp::lat_index<int32_t>(c.g, a) != (int32_t)(id % c.per_layer)) return err("32-bit index differs"), finish(-1);
+        int a32[3];
+        sp::lat_centre(c.g, L, (int32_t)(id % c.per_layer), a32);
+        if (a32[0] != a[0] || a32[1] != a[1] || a32[2] != a[2]) return err("32-bit centre differs"), finish(-1);
     }
 
     std::vector<f2> ps[2];
@@ -185,11 +188,8 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     std::vector<float> pcs;
     std::vector<int> tpc;
     std::vector<char> inflight_phi, inflight_pc;
-    auto rec_r = [&](int sl, int *rx, int *ry, int *rz) {
-        const uint32_t r = t.slot_rec[sl];
-        *rx = (int)(r & 31) - R, *ry = (int)(r >> 5 & 31) - R, *rz = (int)(r >> 10 & 31) - R;
-    };
-    auto pc_of = [&](int sl) { return (int)(t.slot_rec[sl] >> 15 & 0xfff); };
+    auto slot_of = [&](uint32_t e) { return sp::lat_slot(e); };
+    auto pc_of = [&](uint32_t e) { return sp::lat_slot(e) + sp::lat_dpc(t.row_nb[sp::lat_row(e)]); };
 
     for (int64_t id : order) {
         const int L = c.layer(id);
@@ -201,9 +201,11 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         for (int p = 0; p < 2; ++p) ps[p].assign(t.n_slots, {0, 0}), tps[p].assign(t.n_slots, -999);
         pcs.assign(4 * (size_t)t.n_foot, 0.0f), tpc.assign(t.n_foot, -999);
         inflight_phi.assign(t.n_slots, 0), inflight_pc.assign(t.n_foot, 0);
-        auto load = [&](int sl, bool full, int k) {  // value of local level k (global tau_b + k)
+        auto load = [&](uint32_t en, bool full, int k) {  // value of local level k (global tau_b + k)
+            const int sl = slot_of(en);
+            if (sl < 0 || sl >= t.n_slots) return err("slot out of range");
             int rx, ry, rz;
-            rec_r(sl, &rx, &ry, &rz);
+            t.offset_of(sl, sp::lat_row(en), &rx, &ry, &rz);
             const int64_t g = site_of(c, a, rx, ry, rz);
             const int tau = tau_b + k, par = g_plant == 1 ? 0 : tau & 1;
             if (tagP[par][g] != tau) return err("import of phi sees level " + std::to_string(tagP[par][g]) +
@@ -212,7 +214,8 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             ps[k & 1][sl] = P[par][g];
             tps[k & 1][sl] = k;
             if (full) {
-                const int pi = pc_of(sl);
+                const int pi = pc_of(en);
+                if (pi < 0 || pi >= t.n_foot) return err("(pi, c) index out of range");
                 if (tagG[g] != tau) return err("import of (pi, c) sees a wrong level");
                 log.push_back({2 * sites + g, (int32_t)id, tau, false, k + 1});
                 std::memcpy(&pcs[4 * pi], &G[4 * g], 16);
@@ -222,29 +225,32 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         };
         // cut region: its own cells of level k_lo - 1, whole, from the state at t0
         if (k_lo > 0)
-            for (int i = t.cell_off[k_lo - 1]; i < t.cell_off[k_lo]; ++i)
-                if (!load((int)(t.cell[i] & 0xfff), true, k_lo - 1)) return finish(-1);
-        for (int i = t.imp_off[k_lo]; i < t.imp_off[k_lo + 1]; ++i)
-            if (!load(t.imp[i] & 0x7fff, (t.imp[i] & sp::kLatImpFull) != 0, k_lo - 1)) return finish(-1);
+            for (int i = t.cell_off[k_lo - 1]; i < t.cell_off[k_lo - 1] + t.cell_n[k_lo - 1]; ++i)
+                if (!load(t.cell[i], true, k_lo - 1)) return finish(-1);
+        for (int i = t.imp_off[k_lo]; i < t.imp_off[k_lo] + t.imp_n[k_lo]; ++i)
+            if (!load(t.imp[i], (t.imp[i] & sp::kLatImpFull) != 0, k_lo - 1)) return finish(-1);
         for (int k = k_lo; k <= k_hi; ++k) {
             // next level's imports are in flight during this level
             std::vector<int> fl_phi, fl_pc;
             if (k < k_hi)
-                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 2]; ++i) {
-                    const int sl = t.imp[i] & 0x7fff;
+                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 1] + t.imp_n[k + 1]; ++i) {
+                    const int sl = slot_of(t.imp[i]);
                     inflight_phi[sl] = 1, fl_phi.push_back(sl);
-                    if (t.imp[i] & sp::kLatImpFull) inflight_pc[pc_of(sl)] = 1, fl_pc.push_back(pc_of(sl));
+                    if (t.imp[i] & sp::kLatImpFull) inflight_pc[pc_of(t.imp[i])] = 1, fl_pc.push_back(pc_of(t.imp[i]));
                 }
             const int tau = tau_b + k;
             const float *cf = coef4 + 4 * (tau - 1);
             const sp::LevelCoef co = {cf[0], cf[1], cf[2], 0.0f};
             const int rp = (k - 1) & 1, wp = k & 1;
-            for (int i = t.cell_off[k]; i < t.cell_off[k + 1]; ++i) {
-                const uint64_t en = t.cell[i];
-                const int sl = (int)(en & 0xfff), pi = (int)(en >> 12 & 0xfff);
-                const int ym = (int8_t)(en >> 24 & 0xff), yp = (int8_t)(en >> 32 & 0xff);
-                const int zm = ((int)(en >> 40 & 1023) ^ 512) - 512, zp = ((int)(en >> 50 & 1023) ^ 512) - 512;
-                const int nb[7] = {sl, sl - 1, sl + 1, sl + ym, sl + yp, sl + zm, sl + zp};
+            for (int i = t.cell_off[k]; i < t.cell_off[k] + t.cell_n[k]; ++i) {
+                const uint32_t en = t.cell[i];
+                const int sl = sp::lat_slot(en), pi = pc_of(en);
+                const uint64_t rn = t.row_nb[sp::lat_row(en)];
+                int rx, ry, rz;
+                t.offset_of(sl, sp::lat_row(en), &rx, &ry, &rz);
+                if (pi < 0 || pi >= t.n_foot) return err("(pi, c) index out of range"), finish(-1);
+                const int nb[7] = {sl, sl - 1, sl + 1, sl + sp::lat_dym(rn), sl + sp::lat_dyp(rn), sl + sp::lat_dzm(rn),
+                                   sl + sp::lat_dzp(rn)};
                 for (int j = 0; j < 7; ++j) {
                     if (nb[j] < 0 || nb[j] >= t.n_slots) return err("neighbour slot out of range"), finish(-1);
                     if (tps[rp][nb[j]] != k - 1) return err("level " + std::to_string(k) + " reads a phi slot holding level " +
@@ -258,8 +264,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                 ps[wp][sl] = out, tps[wp][sl] = k;
                 pcs[4 * pi] = p.x, pcs[4 * pi + 1] = p.y, pcs[4 * pi + 2] = cc.x, pcs[4 * pi + 3] = cc.y;
                 tpc[pi] = k;
-                int rx, ry, rz;
-                rec_r(sl, &rx, &ry, &rz);
                 const int64_t g = site_of(c, a, rx, ry, rz);
                 if (++computed[(size_t)(tau - 1) * sites + g] != 1) return err("a site-update computed twice"), finish(-1);
                 const bool cut_top = k == k_hi;
@@ -278,8 +282,8 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             for (int sl : fl_phi) inflight_phi[sl] = 0;
             for (int pi : fl_pc) inflight_pc[pi] = 0;
             if (k < k_hi)
-                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 2]; ++i)
-                    if (!load(t.imp[i] & 0x7fff, (t.imp[i] & sp::kLatImpFull) != 0, k)) return finish(-1);
+                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 1] + t.imp_n[k + 1]; ++i)
+                    if (!load(t.imp[i], (t.imp[i] & sp::kLatImpFull) != 0, k)) return finish(-1);
         }
     }
     for (size_t i = 0; i < computed.size(); ++i)
@@ -299,7 +303,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             int d[3], b[3];
             sp::lat_pred_shift(i, d);
             for (int k = 0; k < 3; ++k) b[k] = sp::lat_wrap(a[k] - d[k], 4 * c.g.M[k]);
-            const int64_t v = (int64_t)(L + 1 - c.Lmin) * c.per_layer + sp::lat_index(c.g, b);
+            const int64_t v = (int64_t)(L + 1 - c.Lmin) * c.per_layer + sp::lat_index<int64_t>(c.g, b);
             // v's predecessor i must be u
             if (sp::lat_pred(c.g, L + 1, v % c.per_layer, i) != u % c.per_layer) return err("pred/succ mismatch"), finish(-1);
             reach[u * words + v / 64] |= 1ull << (v % 64);
@@ -380,10 +384,10 @@ int lx_level(int s, int k, int32_t *xyz, int max)
 {
     sp::LatticeTables t;
     if (!sp::build_lattice_tables(s, &t).empty() || k < 0 || k >= t.K) return -1;
-    const int n = t.cell_off[k + 1] - t.cell_off[k];
+    const int n = t.cell_n[k];
     for (int i = 0; i < n && i < max; ++i) {
-        const uint32_t r = t.slot_rec[t.cell[t.cell_off[k] + i] & 0xfff];
-        xyz[3 * i] = (int)(r & 31) - 2 * s, xyz[3 * i + 1] = (int)(r >> 5 & 31) - 2 * s, xyz[3 * i + 2] = (int)(r >> 10 & 31) - 2 * s;
+        const uint32_t e = t.cell[t.cell_off[k] + i];
+        t.offset_of(sp::lat_slot(e), sp::lat_row(e), &xyz[3 * i], &xyz[3 * i + 1], &xyz[3 * i + 2]);
     }
     return n;
 }

@@ -78,14 +78,27 @@ def test_lattice_bit_exact_vs_monolithic(B, n, calls, nu):
     assert_bit_equal(reg, run(p, st, calls, mono=True)[0])
 
 
-@pytest.mark.parametrize("threads", [64, 256])
-def test_lattice_worker_counts(threads):
-    n, steps = (48, 32, 32), 24
+@pytest.mark.parametrize("B,threads", [(16, 256), (16, 512), (8, 64), (12, 64)])
+def test_lattice_worker_counts(B, threads):
+    n, steps = (48, 48, 48), 24
     p = params_for(n, 2.0, steps)
     st = inputs.initial_state(n, 5, "phase")
-    reg, info = run(p, st, [steps], base_B=16, threads=threads)
+    reg, info = run(p, st, [steps], base_B=B, threads=threads)
     assert info["threads"] == threads
     assert_bit_equal(reg, run(p, st, [steps], mono=True)[0])
+
+
+def test_lattice_worker_count_too_small_is_refused():
+    """Each worker holds at most six cells and four imports of a level in
+    registers: at s = 4 (660 cells in the widest level) 64 workers cannot,
+    and the plan says so instead of running."""
+    p = params_for((32, 32, 32), 0.0, 8)
+    g = sp.Grid([p])
+    try:
+        g.set_option(sp.SP_OPT_REGION_SHAPE, sp.SP_SHAPE_LATTICE)
+        assert sp.sp_region_plan(g.h, 16, 64, sp.SP_ORDER_STATIC, None) == sp.SP_EINVAL
+    finally:
+        g.close()
 
 
 def test_lattice_several_simulations_in_one_call():
