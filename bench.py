@@ -49,8 +49,11 @@ NU, TAU0, LAM, ETA, DX, DT = 2.0, 10.0, 2.0, 1.0, 1.0, 0.25
 SEED = 0
 # The workloads: grid side, leapfrog steps of the whole run, steps per bench
 # step (one sp_evolve call), region base.
-BIG = dict(N=1280, STEPS=2048, PER_STEP=64, B=16)
-SMALL = dict(N=128, STEPS=256, PER_STEP=256, B=16)
+BIG = dict(N=1280, STEPS=2048, PER_STEP=64, B=16, SHAPE="split")
+SMALL = dict(N=128, STEPS=256, PER_STEP=256, B=16, SHAPE="split")
+# Lattice regions (4-cubes of edge B = 4s): 128-step bench steps (each call
+# pays for the layers cut by its first and last levels once).
+LATTICE_PER_STEP = 128
 # Sample of the big workload that the FP64 oracle times on the host cores: the
 # first SAMPLE_Z planes of its initial field as a periodic slab.
 SAMPLE_Z = 32
@@ -62,6 +65,8 @@ MONO_BYTES_PER_UPDATE = 48.0
 # On-chip (shared-memory) bytes per site-update of the region kernel: seven
 # phi reads (8 B) and one phi write, one (pi, c) read and write (16 B each).
 SMEM_BYTES_PER_UPDATE = 7 * 8 + 8 + 2 * 16
+# the lattice kernel also reads its cell entry (4 B) and row record (8 B)
+SMEM_BYTES_PER_UPDATE_LATTICE = SMEM_BYTES_PER_UPDATE + 4 + 8
 # Shared-memory bandwidth of one GB300, nominal: 128 B per clock per SM (the
 # fallback when the measured peak is not available).
 SMS, SMEM_BYTES_PER_CLOCK = 152, 128
@@ -73,8 +78,21 @@ METRIC = "lattice site-updates/s"
 
 def workload_name(w):
     n, steps = w["N"], w["STEPS"]
+    regions = (f"4-cube lattice regions of edge B={w['B']}" if w.get("SHAPE") == "lattice"
+               else f"region base B={w['B']}")
     return (f"{n}^3 matter era (nu=2, tau0=10, tau_ref={TAU0 + steps * DT:g}), lambda=2, eta=1, dx=1, dt=0.25, "
-            f"random-phase init seed 0, {steps} leapfrog steps, region base B={w['B']}")
+            f"random-phase init seed 0, {steps} leapfrog steps, {regions}")
+
+
+def lattice_layers(B, steps):
+    """Layers of lattice regions a call of `steps` levels meets (lattice.h)."""
+    return (steps - 1) // (B // 4) + 4
+
+
+def shape_const(shape):
+    from paper_1011_4046_gb300 import sp
+
+    return sp.SP_SHAPE_LATTICE if shape == "lattice" else sp.SP_SHAPE_SPLIT
 
 
 def peaks():
@@ -87,29 +105,39 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# the region kernel and everything that shapes what it moves (tables, launch)
-KERNEL_SOURCES = ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
-                  "paper_1011_4046_gb300/csrc/sp_update.h", "paper_1011_4046_gb300/csrc/sp_api.cu",
-                  "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h",
-                  "paper_1011_4046_gb300/csrc/sp_region_common.cuh"]
+# the region kernels and everything that shapes what they move (tables, launch)
+KERNEL_SOURCES = {
+    "split": ["paper_1011_4046_gb300/csrc/sp_kernels.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
+              "paper_1011_4046_gb300/csrc/sp_update.h", "paper_1011_4046_gb300/csrc/sp_api.cu",
+              "paper_1011_4046_gb300/csrc/planner.cpp", "paper_1011_4046_gb300/csrc/planner.h",
+              "paper_1011_4046_gb300/csrc/sp_region_common.cuh"],
+    "lattice": ["paper_1011_4046_gb300/csrc/sp_lattice.cu", "paper_1011_4046_gb300/csrc/sp_device.cuh",
+                "paper_1011_4046_gb300/csrc/sp_update.h", "paper_1011_4046_gb300/csrc/sp_api.cu",
+                "paper_1011_4046_gb300/csrc/lattice.cpp", "paper_1011_4046_gb300/csrc/lattice.h"],
+}
+TRAFFIC_RECORD = {"split": "region_kernel_traffic.json", "lattice": "lattice_kernel_traffic.json"}
 
 
-def ncu_traffic(base, updates_per_launch):
-    """DRAM bytes (read + written) per region-kernel launch, from the committed
-    ncu record: its bytes per site-update, measured on a smaller grid of the
-    same kernel and base whose state and mailboxes are far larger than L2,
-    times the site-updates of this launch.  None when the kernel sources
-    changed since the record was taken or the base differs."""
+def kernel_sources_hash(shape):
     import hashlib
 
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES[shape]:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(base, updates_per_launch, shape="split"):
+    """DRAM bytes (read + written) per region-kernel launch, from the committed
+    ncu record of that kernel: its bytes per site-update, measured on a
+    smaller grid of the same kernel and base whose state (and mailboxes) are
+    far larger than L2, times the site-updates of this launch.  None when the
+    kernel sources changed since the record was taken or the base differs."""
     try:
-        with open(os.path.join(ROOT, "profiles", "region_kernel_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", TRAFFIC_RECORD[shape])) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        for s in KERNEL_SOURCES:
-            with open(os.path.join(ROOT, s), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest()[:16] != rec["kernel_sources_sha256_16"] or int(rec["region_base"]) != int(base):
+        if kernel_sources_hash(shape) != rec["kernel_sources_sha256_16"] or int(rec["region_base"]) != int(base):
             return None
         per_update = (rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]) / rec["site_updates"]
         return per_update * updates_per_launch
@@ -182,12 +210,12 @@ def parse_clocks(lines):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def smem_roofline(updates, kernel_ms, clk, measured_gbs=None):
+def smem_roofline(updates, kernel_ms, clk, measured_gbs=None, bytes_per_update=SMEM_BYTES_PER_UPDATE):
     """On-chip line of the region kernel: its shared-memory bytes per launch
     over the launch time, against the device's measured shared-memory read
     bandwidth (sp_measure_peaks) when given, else the nominal bandwidth at the
     SM clock sampled during the timed region (or the maximum clock)."""
-    achieved = SMEM_BYTES_PER_UPDATE * updates / (kernel_ms / 1e3) / 1e9
+    achieved = bytes_per_update * updates / (kernel_ms / 1e3) / 1e9
     if measured_gbs:
         peak, kind = measured_gbs, "measured (sp_measure_peaks: conflict-free 16-byte shared-memory reads, all SMs)"
     else:
@@ -195,7 +223,7 @@ def smem_roofline(updates, kernel_ms, clk, measured_gbs=None):
         peak = SMS * SMEM_BYTES_PER_CLOCK * mhz * 1e6 / 1e9
         kind = f"nominal (152 SMs x 128 B/clock at {mhz:.0f} MHz)"
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": kind, "bytes_per_update": SMEM_BYTES_PER_UPDATE}
+            "peak_kind": kind, "bytes_per_update": bytes_per_update}
 
 
 def alu_roofline(updates, kernel_ms, measured_tflops):
@@ -324,10 +352,18 @@ def run_grid(args, w, extra=None):
         pic.zero_()
         g.set_level(0, 0)
 
+    shape = w.get("SHAPE", "split")
+    lattice = shape == "lattice"
     g = sp.Grid([p], states=[(phi, pic)], stream=stream)
-    g.plan(base_B=B if args.base == 0 else args.base, threads=args.threads)
+    g.plan(base_B=B if args.base == 0 else args.base, threads=args.threads, shape=shape_const(shape))
     info = g.plan_info(0)
     base = info["base_B"]
+    regions_per_call = int(info["regions_per_band"] * (lattice_layers(base, PER) if lattice else PER // (base // 2)))
+    if lattice:
+        c_upd, c_rd, c_wr = sp.sp_lattice_call_bytes(base, PER)
+        alg_bytes = (c_rd + c_wr) / c_upd
+    else:
+        alg_bytes = ALG_BYTES_PER_UPDATE[base]
     calls = args.warmup + args.steps
     sched = pass_schedule(calls, PER, STEPS)
 
@@ -370,8 +406,7 @@ def run_grid(args, w, extra=None):
         rc = sp.sp_evolve(g.h, PER, sp.SP_TRACE)
         if rc != 0:
             raise sp.SpError(rc, "sp_evolve (trace)")
-        regions = int(info["regions_per_band"] * (PER // (base // 2)))
-        utilisation = trace_utilisation(g.trace(0, regions), info["grid"])
+        utilisation = trace_utilisation(g.trace(0, regions_per_call), info["grid"])
 
     # ---- e2e through the C ABI: state in host memory, copied in and out every step ----
     e2e = None
@@ -437,8 +472,10 @@ def run_grid(args, w, extra=None):
 
     hbm, peak_kind = peaks()
     kern_mean = sum(kern_ms) / len(kern_ms)
-    achieved = ALG_BYTES_PER_UPDATE[base] * updates / (kern_mean / 1e3) / 1e9
+    achieved = alg_bytes * updates / (kern_mean / 1e3) / 1e9
     wl = dict(w, B=base)
+    kernel_name = "lattice_kernel" if lattice else "region_kernel"
+    smem_bytes = SMEM_BYTES_PER_UPDATE_LATTICE if lattice else SMEM_BYTES_PER_UPDATE
     out = {
         "metric": METRIC,
         "value": value,
@@ -453,26 +490,26 @@ def run_grid(args, w, extra=None):
         "dtype": "f32",
         "data": "synthetic (seeded random-phase field)",
         "config": {"workload": workload_name(wl), "grid": N, "leapfrog_steps": STEPS,
-                   "leapfrog_steps_per_bench_step": PER, "region_base": base,
+                   "leapfrog_steps_per_bench_step": PER, "region_base": base, "region_shape": shape,
                    "bench_step": f"one sp_evolve call of {PER} leapfrog steps continuing the run "
                                  f"(start levels {sched[args.warmup]}..{sched[-1]} timed); the initial field is "
                                  f"restored when a pass reaches level {STEPS}",
-                   "regions_per_bench_step": int(info["regions_per_band"] * (PER // (base // 2))),
+                   "regions_per_bench_step": regions_per_call,
                    "threads_per_cta": info["threads"], "ctas": info["grid"],
                    "mailbox_slots": info["mailbox_slots"], "mailbox_bytes": info["mailbox_bytes"],
                    "l2": ("inputs larger than L2 (state 24 B/site = "
-                          f"{24 * sites / 1e9:.1f} GB plus mailboxes), no flush" if N >= 512 else
-                          "state and mailboxes partly L2-resident (see extra key)"),
+                          f"{24 * sites / 1e9:.1f} GB plus " + ("the odd-level phi array" if lattice else "mailboxes")
+                          + "), no flush" if N >= 512 else "state partly L2-resident (see extra key)"),
                    "init_s": init_s, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "monolithic": mono,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": ncu_traffic(base, updates),
-                     "kernel": "region_kernel", "kernel_ms": kern_mean,
-                     "alg_bytes_per_update": ALG_BYTES_PER_UPDATE[base],
-                     "design_bytes_per_update": info["bytes_per_update"],
-                     "traffic_from": "profiles/region_kernel_traffic.json scaled by site-updates per launch"},
-        "roofline_smem": smem_roofline(updates, kern_mean, clk, peaks_onchip[0]),
+                     "traffic": ncu_traffic(base, updates, shape),
+                     "kernel": kernel_name, "kernel_ms": kern_mean,
+                     "alg_bytes_per_update": alg_bytes,
+                     "design_bytes_per_update": alg_bytes if lattice else info["bytes_per_update"],
+                     "traffic_from": f"profiles/{TRAFFIC_RECORD[shape]} scaled by site-updates per launch"},
+        "roofline_smem": smem_roofline(updates, kern_mean, clk, peaks_onchip[0], smem_bytes),
         "roofline_alu": alu_roofline(updates, kern_mean, peaks_onchip[1]),
         "measured_onchip_peaks": {"smem_gbs": peaks_onchip[0], "fp32_tflops": peaks_onchip[1]},
         "e2e": e2e,
@@ -499,13 +536,13 @@ def run_small(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
-    w = SMALL
+    w = dict(SMALL, SHAPE=args.shape)
     N, STEPS = w["N"], w["STEPS"]
     p = sp.make_params(N, dx=DX, dt=DT, lam=LAM, eta=ETA, nu=NU, tau0=TAU0, tau_ref=TAU0 + STEPS * DT)
     st = inputs.initial_state((N, N, N), SEED, "phase", eta=ETA)
     init_dev = torch.from_numpy(sp.pack_state(*st)).to(dev)
     g = sp.Grid([p], stream=stream)
-    g.plan(base_B=w["B"])
+    g.plan(base_B=w["B"], shape=shape_const(w["SHAPE"]))
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     updates = N ** 3 * STEPS
     res = {}
@@ -530,11 +567,16 @@ def run_small(args):
     g.close()
     hbm, _ = peaks()
     kern = res["regions"][2]
+    if w["SHAPE"] == "lattice":
+        c_upd, c_rd, c_wr = sp.sp_lattice_call_bytes(w["B"], STEPS)
+        alg = (c_rd + c_wr) / c_upd
+    else:
+        alg = ALG_BYTES_PER_UPDATE[w["B"]]
     return {"workload": workload_name(w), "value": res["regions"][0], "unit": "site-updates/s",
             "ms_per_step": res["regions"][1], "steps": args.small_steps,
             "monolithic": {"value": res["monolithic"][0], "ms_per_step": res["monolithic"][1],
                            "speedup_of_regions": res["regions"][0] / res["monolithic"][0]},
-            "roofline_frac": ALG_BYTES_PER_UPDATE[w["B"]] * updates / (kern / 1e3) / 1e9 / hbm,
+            "roofline_frac": alg * updates / (kern / 1e3) / 1e9 / hbm,
             "l2": "flushed (512 MiB write) before every step; state restored on device outside timing"}
 
 
@@ -693,6 +735,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-levels", type=int, default=4, help="leapfrog steps per reference-arm step")
     ap.add_argument("--base", type=int, default=0, help="region base (0: the workload's)")
+    ap.add_argument("--shape", default="split", choices=["split", "lattice"],
+                    help="region geometry: split tiling (pyramids and wedges) or the paper's 4-cube lattice")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--grid", type=int, default=0, help="grid side (profiling of smaller cases only)")
     ap.add_argument("--per-step", type=int, default=0, help="leapfrog steps per bench step (profiling only)")
@@ -711,7 +755,9 @@ def main():
     else:
         setup_dist()
         ws, rank, _ = dist_env()
-        w = dict(BIG)
+        w = dict(BIG, SHAPE=args.shape)
+        if args.shape == "lattice":
+            w["PER_STEP"] = LATTICE_PER_STEP
         if args.grid:
             w["N"] = args.grid
         if args.per_step:

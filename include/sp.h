@@ -351,6 +351,19 @@ int sp_sweep_noalloc(const sp_params *p, void *phi_dev, void *pic_dev, int64_t l
                      void *cuda_stream);
 
 /*
+ * sp_lattice_call_bytes -- what a call of n_steps levels moves with lattice
+ * regions of edge B = 4s (SP_SHAPE_LATTICE): site-updates and HBM bytes read
+ * and written by one region column (one region position in every layer of
+ * the call; a layer holds 4 M_x M_y M_z regions), including the whole-state
+ * loads of the regions cut by the call's first level and the whole-state
+ * exports of those cut by its last.  bytes / updates is the call's
+ * algorithmic bytes per site-update (paper Sec. 3: surface over volume).
+ * Host only, no device work.  Errors: SP_EINVAL (B not 4..24 in steps of 4,
+ * n_steps < 1, a NULL output).
+ */
+int sp_lattice_call_bytes(int32_t B, int64_t n_steps, int64_t *updates, int64_t *bytes_read, int64_t *bytes_written);
+
+/*
  * sp_measure_peaks -- measured on-chip peaks of the current device, for the
  * roofline lines of the region kernel (its shared-memory traffic and its
  * FP32 arithmetic; the HBM line uses a measured copy bandwidth): the

@@ -312,4 +312,30 @@ std::string build_lattice_tables(int s, LatticeTables *t)
     return std::string();
 }
 
+LatCallStats lattice_call_stats(const LatticeTables &t, int64_t T)
+{
+    LatCallStats st;
+    if (T < 1 || t.K == 0) return st;
+    const int s = t.s, K = t.K, Lcount = lat_layer_count(s, T);
+    for (int li = 0; li < Lcount; ++li) {
+        const int L = lat_min_layer() + li;
+        const int64_t tau_b = 1 + (int64_t)s * L;
+        const int k_lo = tau_b < 1 ? (int)(1 - tau_b) : 0;
+        const int k_hi = (int)std::min<int64_t>(K - 1, T - tau_b);
+        if (k_lo > 0) st.bytes_read += 24 * (int64_t)t.cell_n[k_lo - 1];
+        for (int k = k_lo; k <= k_hi; ++k) {
+            st.updates += t.cell_n[k];
+            for (int i = t.imp_off[k]; i < t.imp_off[k] + t.imp_n[k]; ++i)
+                st.bytes_read += (t.imp[i] & kLatImpFull) ? 24 : 8;
+            for (int i = t.cell_off[k]; i < t.cell_off[k] + t.cell_n[k]; ++i) {
+                const uint32_t e = t.cell[i];
+                const bool all = k == k_hi;
+                if (all || (e & kLatExpPhi)) st.bytes_written += 8;
+                if (all || (e & kLatExpPc)) st.bytes_written += 16;
+            }
+        }
+    }
+    return st;
+}
+
 }  // namespace sp

@@ -125,6 +125,17 @@ struct LatticeTables {
     }
 };
 
+// Site-updates and bytes moved by one region column (one region position in
+// every layer) of a call of T levels: regions cut by the call's first level
+// also load their level-(k_lo - 1) cells whole (24 bytes each), regions cut by
+// its last level export their top level's cells whole (24 bytes each; cells
+// already flagged are not counted twice).  Every layer has the same number
+// of regions, so bytes / updates is the call's bytes per site-update.
+struct LatCallStats {
+    int64_t updates = 0, bytes_read = 0, bytes_written = 0;
+};
+LatCallStats lattice_call_stats(const LatticeTables &t, int64_t T);
+
 // Builds the tables of lattice size s (kLatMinS..kLatMaxS) and checks them:
 // the cell count 16 s^4; that every value a level reads is in shared memory
 // from the previous level or imported before it; that every import is

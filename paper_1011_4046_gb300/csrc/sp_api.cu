@@ -1937,6 +1937,19 @@ int sp_read_surface(const sp_grid *gc, int32_t sim, int32_t what, void *dst, siz
     }
 }
 
+int sp_lattice_call_bytes(int32_t B, int64_t n_steps, int64_t *updates, int64_t *bytes_read, int64_t *bytes_written)
+{
+    if (B < 4 || B > 4 * sp::kLatMaxS || B % 4 || n_steps < 1 || !updates || !bytes_read || !bytes_written)
+        return SP_EINVAL;
+    sp::LatticeTables t;
+    if (!sp::build_lattice_tables(B / 4, &t).empty()) return SP_EINVAL;
+    const sp::LatCallStats st = sp::lattice_call_stats(t, n_steps);
+    *updates = st.updates;
+    *bytes_read = st.bytes_read;
+    *bytes_written = st.bytes_written;
+    return SP_OK;
+}
+
 int sp_destroy(sp_grid *g)
 {
     if (!g) return SP_EINVAL;

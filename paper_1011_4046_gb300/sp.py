@@ -161,6 +161,8 @@ def load(build_if_missing: bool = False):
         lib.sp_sweep_noalloc.argtypes = [ctypes.POINTER(sp_params), vp, vp, ctypes.c_int64, ctypes.c_int64, vp]
         lib.sp_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
         lib.sp_measure_peaks.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.sp_lattice_call_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, i64p, i64p, i64p]
         lib.sp_strerror.argtypes = [ctypes.c_int]
         lib.sp_strerror.restype = ctypes.c_char_p
         fp = ctypes.POINTER(ctypes.c_float)
@@ -236,6 +238,15 @@ def sp_measure_peaks(stream=0):
     rc = load().sp_measure_peaks(ctypes.c_void_p(int(stream)), ctypes.byref(smem), ctypes.byref(fp32))
     _check(rc, "sp_measure_peaks")
     return smem.value, fp32.value
+
+
+def sp_lattice_call_bytes(B, n_steps):
+    """(site-updates, bytes read, bytes written) of one lattice region column
+    over a call of n_steps levels (host only)."""
+    u, r, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().sp_lattice_call_bytes(int(B), int(n_steps), ctypes.byref(u), ctypes.byref(r), ctypes.byref(w)),
+           "sp_lattice_call_bytes")
+    return u.value, r.value, w.value
 
 
 # ------------------------------------------------------------ helpers

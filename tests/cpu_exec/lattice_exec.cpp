@@ -100,7 +100,8 @@ int lx_sweep(int nx, int ny, int nz, int nsteps, const float *coef4, float dt, f
 // Runs one call of nsteps levels as lattice regions of size s.  mode 0: the
 // kernel's ticket order (layer by layer); 1: seeded random ready region;
 // 2: the most recently readied region first.  Returns 0, or -1 with msg.
-// stats (optional, 4 int64): regions, race-checked reads, writes, site-updates.
+// stats (optional, 6 int64): regions, race-checked reads, writes, site-updates
+// of one region, bytes read and written from and to the state arrays.
 int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_seed, const float *coef4, float dt,
            float inv_dx2, float eta2, float *phi, float *pc, char *msg, int msglen, int64_t *stats)
 {
@@ -353,7 +354,15 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
 
     std::memcpy(phi, P[g_plant == 1 ? 0 : nsteps & 1].data(), sites * 8);
     std::memcpy(pc, G.data(), sites * 16);
-    if (stats) stats[0] = nreg, stats[1] = nreads, stats[2] = nwrites, stats[3] = (int64_t)t.updates;
+    if (stats) {
+        stats[0] = nreg, stats[1] = nreads, stats[2] = nwrites, stats[3] = (int64_t)t.updates;
+        int64_t br = 0, bw = 0;
+        for (const Access &x : log) {
+            const int64_t b = x.loc >= 2 * sites ? 16 : 8;
+            (x.write ? bw : br) += b;
+        }
+        stats[4] = br, stats[5] = bw;
+    }
     return finish(0);
 }
 

@@ -36,31 +36,43 @@ def test_alu_line_counts_the_site_update_flops():
     assert r["frac"] == pytest.approx(r["achieved"] / 50.0) and r["bound"] == "alu"
 
 
-def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
-    """roofline.traffic comes from the committed ncu record only while every
-    source that shapes the region kernel's memory traffic is byte-identical to
-    the one the record was taken on and the region base is the record's; it
-    is the record's bytes per site-update times the launch's site-updates."""
+@pytest.mark.parametrize("shape", ["split", "lattice"])
+def test_traffic_record_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch, shape):
+    """roofline.traffic comes from the committed ncu record of the kernel
+    (region or lattice) only while every source that shapes that kernel's
+    memory traffic is byte-identical to the one the record was taken on and
+    the region base is the record's; it is the record's bytes per site-update
+    times the launch's site-updates."""
     import hashlib
     import json
 
-    for i, rel in enumerate(bench.KERNEL_SOURCES):
+    for i, rel in enumerate(bench.KERNEL_SOURCES[shape]):
         p = tmp_path / rel
         p.parent.mkdir(parents=True, exist_ok=True)
         p.write_text(f"source {i}\n")
     h = hashlib.sha256()
-    for rel in bench.KERNEL_SOURCES:
+    for rel in bench.KERNEL_SOURCES[shape]:
         h.update((tmp_path / rel).read_bytes())
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "region_kernel_traffic.json").write_text(json.dumps({
+    (tmp_path / "profiles" / bench.TRAFFIC_RECORD[shape]).write_text(json.dumps({
         "kernel_sources_sha256_16": h.hexdigest()[:16], "region_base": 16, "site_updates": 4,
         "dram_bytes_read_per_launch": 7, "dram_bytes_write_per_launch": 5}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic(16, 4) == 12
-    assert bench.ncu_traffic(16, 40) == 120
-    assert bench.ncu_traffic(32, 4) is None
-    (tmp_path / bench.KERNEL_SOURCES[0]).write_text("changed\n")
-    assert bench.ncu_traffic(16, 4) is None
+    assert bench.ncu_traffic(16, 4, shape) == 12
+    assert bench.ncu_traffic(16, 40, shape) == 120
+    assert bench.ncu_traffic(32, 4, shape) is None
+    other = "lattice" if shape == "split" else "split"
+    assert bench.ncu_traffic(16, 4, other) is None  # the other kernel's record is absent here
+    (tmp_path / bench.KERNEL_SOURCES[shape][0]).write_text("changed\n")
+    assert bench.ncu_traffic(16, 4, shape) is None
+
+
+def test_lattice_layers_match_the_library():
+    """The bench counts a lattice call's regions with the layer rule of
+    lattice.h: three layers cut by the call's first level plus one per s
+    levels."""
+    assert bench.lattice_layers(16, 128) == 35 and bench.lattice_layers(16, 64) == 19
+    assert bench.lattice_layers(8, 1) == 4 and bench.lattice_layers(24, 50) == 12
 
 
 def test_pass_schedule_continues_and_restarts():

@@ -116,7 +116,7 @@ def _run(lx, s, n, steps, mode, order_seed, phi0, pc0, coef):
     fp = ctypes.POINTER(ctypes.c_float)
     f, p = phi0.copy(), pc0.copy()
     msg = ctypes.create_string_buffer(256)
-    st = (I64 * 4)()
+    st = (I64 * 6)()
     rc = lx.lx_run(s, *n, steps, mode, order_seed, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
                    f.view(np.float32).ctypes.data_as(fp), p.ctypes.data_as(fp), msg, 256, st)
     assert rc == 0, msg.value.decode()
@@ -215,3 +215,39 @@ def test_layer_numbers_of_successive_calls_never_reuse_flag_values(lx):
             waits_min = first[i]  # layer 1 of the call waits for its layer 0: number first
             assert waits_min > written_max
             written_max = max(written_max, first[i] + layers[i] - 1)
+
+
+@pytest.mark.parametrize("s,n,steps", [(2, (16, 8, 24), 21), (4, (16, 16, 16), 19), (4, (32, 16, 16), 64),
+                                       (3, (12, 24, 12), 1)])
+def test_call_bytes_match_the_executed_accesses(lx, s, n, steps):
+    """The library's per-call byte count (sp_lattice_call_bytes, one region
+    column) times the regions per layer equals the bytes the scaffold's
+    execution actually moved to and from the state arrays (its access log);
+    its update count is the grid's sites times the call's levels."""
+    from paper_1011_4046_gb300 import sp
+
+    phi0, pc0 = _state(n, 4)
+    coef = _coef_table(steps, 0.0, 0.25, 2.0, 1.0, 1.0)
+    _, _, st = _run(lx, s, n, steps, 0, 0, phi0, pc0, coef)
+    per_layer = 4 * np.prod([v // (4 * s) for v in n])
+    upd, rd, wr = sp.sp_lattice_call_bytes(4 * s, steps)
+    assert upd * per_layer == np.prod(n) * steps
+    assert rd * per_layer == st[4]
+    assert wr * per_layer == st[5]
+
+
+def test_call_bytes_approach_the_region_figure():
+    """Long calls converge to the full region's 14.69 B per site-update at
+    s = 4; the cut layers at a call's two ends add a share that shrinks as
+    1 / steps."""
+    from paper_1011_4046_gb300 import sp
+
+    prev = None
+    for steps in (16, 64, 256, 2048):
+        upd, rd, wr = sp.sp_lattice_call_bytes(16, steps)
+        b = (rd + wr) / upd
+        assert b > 14.69
+        if prev is not None:
+            assert b < prev
+        prev = b
+    assert prev < 14.69 * 1.02
