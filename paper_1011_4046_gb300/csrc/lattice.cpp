@@ -14,6 +14,7 @@ namespace sp {
 namespace {
 
 constexpr int kSig[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+
 constexpr int kNb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
 
 struct R3 {
@@ -122,19 +123,79 @@ std::string build_lattice_tables(int s, LatticeTables *t)
     auto row_index = [&](int y, int z) { return (y + R) * W + z + R; };
     std::vector<int> row_base((size_t)W * W, 0);
     std::map<R3, int> slot, pcidx;
-    int ns = 0, nf = 0;
-    for (const auto &row : rows) {  // std::map: ascending (z, y)
-        const int z = row.first.first, y = row.first.second;
-        row_base[row_index(y, z)] = ns - row.second.first;
-        for (int x = row.second.first; x <= row.second.second; ++x) {
-            const R3 r = {x, y, z};
-            slot[r] = ns++;
-            if (foot.count(r)) pcidx[r] = nf++;
+    // Bank-friendly layout: every phi slot and every (pi, c) index is
+    // congruent to x + a y + b z mod 16, so that the neighbours of 16 cells
+    // with distinct residues (one half-warp's 8-byte accesses) again have
+    // distinct residues, and so do their (pi, c) slots mod 8 for each group of
+    // eight lanes (16-byte accesses).  Rows are chained so that each starts on
+    // its residue, taking the row that needs the least padding next; (a, b)
+    // is the pair with the smallest shared-memory footprint.
+    int bank_a = 0, bank_b = 0;
+    auto residue = [&](int x, int y, int z) { return (((x + bank_a * y + bank_b * z) % 16) + 16) % 16; };
+    auto chain = [&](const std::map<std::pair<int, int>, std::pair<int, int>> &rws, std::map<R3, int> *index,
+                     const std::set<R3> *only, int *count, std::vector<int> *base) {
+        std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> todo(rws.begin(), rws.end());
+        std::vector<char> done(todo.size(), 0);
+        int pos = 0;
+        for (size_t placed = 0; placed < todo.size(); ++placed) {
+            int pick = -1, best_gap = 16;
+            for (size_t i = 0; i < todo.size() && best_gap > 0; ++i) {
+                if (done[i]) continue;
+                const int want = residue(todo[i].second.first, todo[i].first.second, todo[i].first.first);
+                const int gap = ((want - pos % 16) + 16) % 16;
+                if (gap < best_gap) best_gap = gap, pick = (int)i;
+            }
+            pos += best_gap;
+            done[pick] = 1;
+            const int z = todo[pick].first.first, y = todo[pick].first.second;
+            const int xlo = todo[pick].second.first, xhi = todo[pick].second.second;
+            if (base) (*base)[row_index(y, z)] = pos - xlo;
+            if (index)
+                for (int x = xlo; x <= xhi; ++x) {
+                    const R3 r = {x, y, z};
+                    if (!only || only->count(r)) (*index)[r] = pos + (x - xlo);
+                }
+            pos += xhi - xlo + 1;
+        }
+        *count = pos;
+    };
+    std::map<std::pair<int, int>, std::pair<int, int>> frows;  // footprint rows (z, y) -> x range
+    for (const R3 &r : foot) {
+        auto key = std::make_pair(r.z, r.y);
+        auto it = frows.find(key);
+        if (it == frows.end())
+            frows[key] = {r.x, r.x};
+        else {
+            it->second.first = std::min(it->second.first, r.x);
+            it->second.second = std::max(it->second.second, r.x);
         }
     }
+    {
+        int best = 1 << 30, ba = 0, bb = 0;
+        for (int a = 0; a < 16; ++a)
+            for (int b = 0; b < 16; ++b) {
+                bank_a = a, bank_b = b;
+                int n1 = 0, n2 = 0;
+                chain(rows, nullptr, nullptr, &n1, nullptr);
+                chain(frows, nullptr, nullptr, &n2, nullptr);
+                if (16 * n1 + 16 * n2 < best) best = 16 * n1 + 16 * n2, ba = a, bb = b;
+            }
+        bank_a = ba, bank_b = bb;
+    }
+    int ns = 0, nf = 0;
+    chain(rows, &slot, nullptr, &ns, &row_base);
+    chain(frows, &pcidx, &foot, &nf, nullptr);
+    t->bank_a = bank_a;
+    t->bank_b = bank_b;
+    for (const auto &e : slot)
+        if (e.second % 16 != residue(e.first.x, e.first.y, e.first.z)) return fail("slot off its bank residue");
+    for (const auto &e : pcidx)
+        if (e.second % 16 != residue(e.first.x, e.first.y, e.first.z)) return fail("(pi, c) index off its bank residue");
     t->n_slots = ns;
-    t->n_foot = nf;
-    if (ns > 4096 || nf > 4096) return fail("%d slots exceed the kernel's 12-bit indices", ns);
+    t->n_foot = nf;  // (pi, c) slots, padding included
+    t->foot_cells = (int)foot.size();
+    t->halo_cells = (int)(used.size() - foot.size());
+    if (ns > 8192 || nf > 8192) return fail("%d slots exceed the kernel's 13-bit indices", ns);
 
     // per-row constants: neighbour steps, (pi, c) offset, row base and offset
     t->row_nb.assign((size_t)W * W, 0);
@@ -158,18 +219,43 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         else if (it->second != v)
             return fail("neighbour steps or (pi, c) offset vary along a row");
     }
+    t->row_pc.assign((size_t)W * W, 0);
     for (const auto &rv : row_vals) {
         const std::vector<int> &v = rv.second;
-        if (v[0] < -128 || v[0] > 127 || v[1] < -128 || v[1] > 127) return fail("y step beyond 8 bits");
-        if (v[2] < -2048 || v[2] > 2047 || v[3] < -2048 || v[3] > 2047) return fail("z step beyond 12 bits");
-        if (v[4] < -4096 || v[4] > 4095) return fail("(pi, c) offset beyond 13 bits");
-        t->row_nb[rv.first] = (uint64_t)(uint8_t)(int8_t)v[0] | (uint64_t)(uint8_t)(int8_t)v[1] << 8 |
-                              (uint64_t)(v[2] & 0xfff) << 16 | (uint64_t)(v[3] & 0xfff) << 28 |
-                              (uint64_t)(v[4] & 0x1fff) << 40;
+        for (int i = 0; i < 4; ++i)
+            if (v[i] < -4096 || v[i] > 4095) return fail("neighbour step beyond 13 bits");
+        t->row_nb[rv.first] = (uint64_t)(uint16_t)(int16_t)v[0] | (uint64_t)(uint16_t)(int16_t)v[1] << 16 |
+                              (uint64_t)(uint16_t)(int16_t)v[2] << 32 | (uint64_t)(uint16_t)(int16_t)v[3] << 48;
+        t->row_pc[rv.first] = v[4];
     }
     auto entry_of = [&](const R3 &r) {
         return (uint32_t)slot.at(r) | (uint32_t)row_index(r.y, r.z) << kLatRowShift;
     };
+
+    // Each level's cells in groups of 16 with distinct slot residues mod 16
+    // (one half-warp), taken in row order with a cell deferred while its
+    // residue is taken; within a group, residues 0..7 first (two groups of
+    // eight lanes with distinct residues mod 8).
+    for (int k = 0; k < K; ++k) {
+        std::vector<R3> pool = lev[k], out;
+        while (!pool.empty()) {
+            std::vector<R3> lo, hi, rest;
+            unsigned used = 0;
+            for (const R3 &r : pool) {
+                const int res = slot.at(r) % 16;
+                if (lo.size() + hi.size() < 16 && !(used >> res & 1u)) {
+                    used |= 1u << res;
+                    (res < 8 ? lo : hi).push_back(r);
+                } else {
+                    rest.push_back(r);
+                }
+            }
+            out.insert(out.end(), lo.begin(), lo.end());
+            out.insert(out.end(), hi.begin(), hi.end());
+            pool.swap(rest);
+        }
+        lev[k] = out;
+    }
 
     // cell entries with export flags
     t->cell_off.assign(K + 1, 0);
@@ -231,7 +317,7 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         const uint64_t v = t->row_nb[row];
         nb[0] = sl, nb[1] = sl - 1, nb[2] = sl + 1;
         nb[3] = sl + lat_dym(v), nb[4] = sl + lat_dyp(v), nb[5] = sl + lat_dzm(v), nb[6] = sl + lat_dzp(v);
-        *pc = sl + lat_dpc(v);
+        *pc = sl + t->row_pc[row];
     };
 
     // check 1: entries decode to their cells, and every value level k reads

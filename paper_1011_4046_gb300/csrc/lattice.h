@@ -66,38 +66,41 @@ constexpr int kLatMinS = 1;
 constexpr int kLatMaxS = 6;  // slot indices are 12 bits, coordinates 5 bits per axis
 
 // Shared-memory phi slots are laid out in rows of constant (y, z), each
-// contiguous in x, rows in (z, y) order: slot(r) = row_base(row) + rx with
-// row = (ry + 2s) (4s + 1) + rz + 2s.  The x neighbours are slot - 1 and
-// slot + 1; the y and z neighbours and the (pi, c) index follow from
-// per-row constants:
-//   row_nb (64 bits): slot(y - 1) - slot (bits 0..7, signed),
-//     slot(y + 1) - slot (8..15), slot(z - 1) - slot (16..27, signed 12 bits),
-//     slot(z + 1) - slot (28..39), pc - slot (40..52, signed 13 bits);
+// contiguous in x: slot(r) = row_base(row) + rx with
+// row = (ry + 2s) (4s + 1) + rz + 2s.  Rows are placed so that every slot,
+// and every (pi, c) index, is congruent to rx + a ry + b rz mod 16 (a, b
+// chosen per size): 16 cells with distinct residues then read their phi and
+// all six neighbours without shared-memory bank conflicts, and groups of 8
+// of them their (pi, c) too.  The x neighbours are slot - 1 and slot + 1; the
+// y and z neighbours and the (pi, c) index follow from per-row constants:
+//   row_nb (64 bits): slot(y - 1) - slot, slot(y + 1) - slot,
+//     slot(z - 1) - slot, slot(z + 1) - slot (signed 16 bits each, low first);
+//   row_pc (32 bits): pc - slot;
 //   row_xy (32 bits): row_base (bits 0..15, signed) | (ry + 2s) << 16 |
 //     (rz + 2s) << 21, for the cell's offset from the region's centre.
 // Cell entry (32 bits), the per-level work list:
-//   bits 0..11 slot; bits 12..21 row; bit 22 export phi at this level;
-//   bit 23 export (pi, c) at this level.
-// Import entry (32 bits): slot | row << 12 | full << 22.  A full import
+//   bits 0..12 slot; bits 13..22 row; bit 23 export phi at this level;
+//   bit 24 export (pi, c) at this level.  Each level's list is ordered so
+//   that every 16 consecutive entries have distinct slot residues mod 16,
+//   the first and last 8 of them distinct residues mod 8.
+// Import entry (32 bits): slot | row << 13 | full << 23.  A full import
 // loads phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k;
 // otherwise only phi(k-1) of a neighbour outside the region.
 // Every level's lists start on a 16-byte boundary (padded with zero entries
 // to a multiple of four).
-constexpr uint32_t kLatSlotMask = 0xfffu;
-constexpr int kLatRowShift = 12;
+constexpr uint32_t kLatSlotMask = 0x1fffu;
+constexpr int kLatRowShift = 13;
 constexpr uint32_t kLatRowMask = 0x3ffu;
-constexpr uint32_t kLatExpPhi = 1u << 22;
-constexpr uint32_t kLatExpPc = 1u << 23;
-constexpr uint32_t kLatImpFull = 1u << 22;
+constexpr uint32_t kLatExpPhi = 1u << 23;
+constexpr uint32_t kLatExpPc = 1u << 24;
+constexpr uint32_t kLatImpFull = 1u << 23;
 
 LAT_HD int lat_slot(uint32_t e) { return (int)(e & kLatSlotMask); }
 LAT_HD int lat_row(uint32_t e) { return (int)((e >> kLatRowShift) & kLatRowMask); }
-LAT_HD int lat_sext(uint64_t v, int bits) { return (int)((int64_t)(v << (64 - bits)) >> (64 - bits)); }
-LAT_HD int lat_dym(uint64_t nb) { return lat_sext(nb, 8); }
-LAT_HD int lat_dyp(uint64_t nb) { return lat_sext(nb >> 8, 8); }
-LAT_HD int lat_dzm(uint64_t nb) { return lat_sext(nb >> 16, 12); }
-LAT_HD int lat_dzp(uint64_t nb) { return lat_sext(nb >> 28, 12); }
-LAT_HD int lat_dpc(uint64_t nb) { return lat_sext(nb >> 40, 13); }
+LAT_HD int lat_dym(uint64_t nb) { return (int)(int16_t)(uint16_t)(nb & 0xffffu); }
+LAT_HD int lat_dyp(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 16) & 0xffffu); }
+LAT_HD int lat_dzm(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 32) & 0xffffu); }
+LAT_HD int lat_dzp(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 48) & 0xffffu); }
 LAT_HD int lat_row_base(uint32_t xy) { return (int)(int16_t)(xy & 0xffffu); }
 
 struct LatticeTables {
@@ -105,7 +108,9 @@ struct LatticeTables {
     int n_slots = 0, n_foot = 0;  // phi slots (footprint + halo), (pi, c) slots
     int rb_side = 0;              // 4s + 1: rows are indexed (ry + 2s) rb_side + rz + 2s
     std::vector<uint64_t> row_nb;   // rb_side^2
+    std::vector<int32_t> row_pc;    // rb_side^2
     std::vector<uint32_t> row_xy;   // rb_side^2
+    int bank_a = 0, bank_b = 0;     // slot residue rx + a ry + b rz mod 16
     std::vector<uint32_t> cell;     // level k: cell[cell_off[k] .. cell_off[k] + cell_n[k]), padded
     std::vector<int32_t> cell_off, cell_n;  // K + 1 offsets (multiples of 4), K counts
     std::vector<uint32_t> imp;      // before level k: imp[imp_off[k] .. imp_off[k] + imp_n[k]), padded
@@ -115,6 +120,7 @@ struct LatticeTables {
     int64_t updates = 0, bytes_read = 0, bytes_written = 0;
     int64_t imports_full = 0, imports_phi = 0, exports_phi = 0, exports_pc = 0;
     int max_level_cells = 0;
+    int foot_cells = 0, halo_cells = 0;  // footprint and halo cells (slots without padding)
     // offset of the cell in slot sl of row `row` from the region's centre
     void offset_of(int sl, int row, int *rx, int *ry, int *rz) const
     {

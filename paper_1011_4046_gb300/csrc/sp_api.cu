@@ -57,6 +57,7 @@ struct LatOnDevice {
     uint32_t *d_cell = nullptr;
     uint32_t *d_imp = nullptr;
     uint64_t *d_nb = nullptr;
+    int32_t *d_pcoff = nullptr;
     uint32_t *d_xy = nullptr;
 };
 
@@ -631,6 +632,7 @@ void free_plan(sp_grid *g)
         cudaFree(kv.second.d_cell);
         cudaFree(kv.second.d_imp);
         cudaFree(kv.second.d_nb);
+        cudaFree(kv.second.d_pcoff);
         cudaFree(kv.second.d_xy);
     }
     g->lat.clear();
@@ -964,6 +966,7 @@ int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
         a.cell = ld.d_cell;
         a.imp = ld.d_imp;
         a.row_nb = ld.d_nb;
+        a.row_pc = ld.d_pcoff;
         a.row_xy = ld.d_xy;
         a.max_cell_n = t.max_cell_n;
         a.flags = g->d_lat_flags + g->lat_flag_off[gi];
@@ -1140,6 +1143,7 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp, std::max<size_t>(t.imp.size(), 4) * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_nb, t.row_nb.size() * sizeof(uint64_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_xy, t.row_xy.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_pcoff, t.row_pc.size() * sizeof(int32_t));
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && !t.imp.empty())
@@ -1148,6 +1152,8 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
             e = cudaMemcpy(ld.d_nb, t.row_nb.data(), t.row_nb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_xy, t.row_xy.data(), t.row_xy.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ld.d_pcoff, t.row_pc.data(), t.row_pc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             free_plan(g);
             return SP_ENOMEM;

@@ -185,7 +185,8 @@ struct LatArgs {
     unsigned per_layer_all, total;
     const uint32_t *cell;            // cell entries (lattice.h), all levels (16-byte aligned per level)
     const uint32_t *imp;             // import entries, all levels
-    const uint64_t *row_nb;          // (4s + 1)^2 row records: neighbour steps, (pi, c) offset
+    const uint64_t *row_nb;          // (4s + 1)^2 row records: neighbour steps
+    const int32_t *row_pc;           // (4s + 1)^2 row records: (pi, c) index - slot
     const uint32_t *row_xy;          // (4s + 1)^2 row records: slot base, (y, z) offsets
     int max_cell_n, pad1;            // longest level's cell list (padded)
     int *flags;

@@ -17,9 +17,10 @@
 // The per-level lists (cell and import entries, lattice.h) are the same for
 // every region: a level's cell entries are copied into shared memory a level
 // ahead (cp.async), each thread's import entries are held in registers a
-// level ahead, so no table read waits on memory.  A cell's neighbours and
-// (pi, c) slot follow from its slot and one 64-bit per-row record; the row
-// tables are copied into shared memory once per launch.
+// level ahead, so no table read waits on memory.  A cell's neighbours, its
+// (pi, c) slot and its site index follow from its slot and one 16-byte
+// per-row record in shared memory (byte offsets; the site offsets are
+// refilled for each region's grid).
 //
 // Regions are handed out by ticket in layer order (one atomic per region,
 // taken a region ahead; the next region's predecessor flags are read early,
@@ -42,19 +43,27 @@ namespace {
 // Import entries per thread and level held in registers (loaded a level ahead).
 constexpr int kLatUI = 4;
 
+// Per-row record in shared memory (16 bytes): byte offsets, from a cell's phi
+// slot, of its y - 1 / y + 1 neighbours (x: low / high 16 bits, signed) and
+// z - 1 / z + 1 neighbours (y); the byte offset of its (pi, c) slot minus
+// 16 x its phi slot (z); and, for the region being evolved, the offset that
+// turns a slot into a site index, site = centre + slot + w (rows that cross
+// the grid's seam take the wrapped path instead).
+struct alignas(16) LatRow {
+    int dy, dz, dpc, goff;
+};
+
 // Shared-memory layout of one region (bytes): (pi, c) slots, the two phi
-// buffers, the row tables and a ring of two levels' cell entries.
+// buffers, the row records and a ring of two levels' cell entries.
 struct LatSmem {
-    size_t pc, ph0, ph1, nb, xy, ring, total;
+    size_t pc, ph0, ph1, row, ring, total;
     __host__ __device__ LatSmem(int n_slots, int n_foot, int W, int max_cell_n)
     {
         pc = 0;
         ph0 = 16 * (size_t)n_foot;
         ph1 = ph0 + 8 * (size_t)n_slots;
-        nb = ph1 + 8 * (size_t)n_slots;
-        nb = (nb + 15) & ~(size_t)15;
-        xy = nb + 8 * (size_t)W * W;
-        ring = (xy + 4 * (size_t)W * W + 15) & ~(size_t)15;
+        row = (ph1 + 8 * (size_t)n_slots + 15) & ~(size_t)15;
+        ring = row + 16 * (size_t)W * W;
         total = ring + 2 * 4 * (size_t)max_cell_n;
     }
 };
@@ -124,17 +133,16 @@ __device__ bool lat_wait(const LatArgs &a, const LatRegion &r)
     return true;
 }
 
-// Site index of the cell at offset r from the region's centre: one wrap per
-// axis where the region crosses the grid's seam, plain arithmetic elsewhere.
+// Site index of the cell in slot sl of row `row`: centre + slot + row offset
+// for a region clear of the grid's seam, one wrap per axis otherwise.
 struct SiteMap {
     int n0, n1, n2;
     int c0, c1, c2;
     long long gc;  // site index of the centre
     bool nowrap;
-    __device__ __forceinline__ long long at(int rx, int ry, int rz) const
+    __device__ __forceinline__ long long wrapped(int sl, uint32_t xy, int R) const
     {
-        if (nowrap) return gc + rx + (long long)n0 * (ry + n1 * rz);
-        int x = c0 + rx, y = c1 + ry, z = c2 + rz;
+        int x = c0 + sl - lat_row_base(xy), y = c1 + (int)((xy >> 16) & 31u) - R, z = c2 + (int)((xy >> 21) & 31u) - R;
         x += x < 0 ? n0 : 0;
         x -= x >= n0 ? n0 : 0;
         y += y < 0 ? n1 : 0;
@@ -143,10 +151,9 @@ struct SiteMap {
         z -= z >= n2 ? n2 : 0;
         return (long long)x + (long long)n0 * ((long long)y + (long long)n1 * z);
     }
-    // the cell in slot sl of a row with record xy
-    __device__ __forceinline__ long long of(int sl, uint32_t xy, int R) const
+    __device__ __forceinline__ long long site(int sl, int row, const LatRow *s_row, const uint32_t *g_xy, int R) const
     {
-        return at(sl - lat_row_base(xy), (int)((xy >> 16) & 31u) - R, (int)((xy >> 21) & 31u) - R);
+        return nowrap ? gc + (sl + s_row[row].goff) : wrapped(sl, __ldg(g_xy + row), R);
     }
 };
 
@@ -161,20 +168,20 @@ __device__ __forceinline__ void load_imports(uint32_t (&v)[kLatUI], const uint32
 }
 
 // cp.async of the values in entries v (imports of one level: phi of one
-// level into s_ph, and (pi, c) of full imports).
+// level into the phi buffer at byte address phb, and (pi, c) of full imports).
 template <int NW>
 __device__ __forceinline__ void issue_imports(const uint32_t (&v)[kLatUI], int n, const SiteMap &sm,
-                                              const uint64_t *s_nb, const uint32_t *s_xy, int R, float4 *s_pc,
-                                              float2 *s_ph, const float2 *gphi, const float4 *gpc)
+                                              const LatRow *s_row, const uint32_t *s_xy, int R, char *pcb, char *phb,
+                                              const float2 *gphi, const float4 *gpc)
 {
 #pragma unroll
     for (int u = 0; u < kLatUI; ++u) {
         if ((int)threadIdx.x + u * NW < n) {
             const uint32_t e = v[u];
             const int sl = lat_slot(e), row = lat_row(e);
-            const long long g = sm.of(sl, s_xy[row], R);
-            cp_async8(s_ph + sl, gphi + g);
-            if (e & kLatImpFull) cp_async16(s_pc + sl + lat_dpc(s_nb[row]), gpc + g);
+            const long long g = sm.site(sl, row, s_row, s_xy, R);
+            cp_async8(phb + (sl << 3), gphi + g);
+            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + s_row[row].dpc, gpc + g);
         }
     }
 }
@@ -186,6 +193,8 @@ __device__ __forceinline__ void copy_entries(uint32_t *ring, const uint32_t *__r
     const int n4 = (n + 3) & ~3;
     for (int i = 4 * (int)threadIdx.x; i < n4; i += 4 * NW) cp_async16(ring + i, tab + off + i);
 }
+
+__device__ __forceinline__ float2 ld_f2(const char *base, int off) { return *reinterpret_cast<const float2 *>(base + off); }
 
 constexpr int kLatMinBlocks = 6;
 
@@ -199,14 +208,17 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
     __shared__ LatRegion s_reg;
     __shared__ int s_stop;
     const int tid = threadIdx.x;
-    const int R = 2 * a.s, W = 4 * a.s + 1;
-    const LatSmem L(a.n_slots, a.n_foot, W, a.max_cell_n);
-    float4 *s_pc = reinterpret_cast<float4 *>(smem + L.pc);
-    float2 *s_ph0 = reinterpret_cast<float2 *>(smem + L.ph0);
-    float2 *s_ph1 = reinterpret_cast<float2 *>(smem + L.ph1);
-    uint64_t *s_nb = reinterpret_cast<uint64_t *>(smem + L.nb);
-    uint32_t *s_xy = reinterpret_cast<uint32_t *>(smem + L.xy);
+    const int R = 2 * a.s, W = 4 * a.s + 1, WW = W * W;
+    const int max_cell_n = a.max_cell_n;
+    const LatSmem L(a.n_slots, a.n_foot, W, max_cell_n);
+    char *s_pcb = reinterpret_cast<char *>(smem + L.pc);
+    char *s_ph0 = reinterpret_cast<char *>(smem + L.ph0);
+    char *s_ph1 = reinterpret_cast<char *>(smem + L.ph1);
+    LatRow *s_row = reinterpret_cast<LatRow *>(smem + L.row);
+    const uint32_t *__restrict__ s_xy = a.row_xy;  // global (read through L1): wrapped sites and per-region offsets
     uint32_t *s_ring = reinterpret_cast<uint32_t *>(smem + L.ring);
+    const uint32_t *__restrict__ g_cell = a.cell;
+    const uint32_t *__restrict__ g_imp = a.imp;
     if (tid <= a.K) {
         s_cell_off[tid] = a.cell_off[tid];
         s_imp_off[tid] = a.imp_off[tid];
@@ -215,9 +227,14 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
             s_imp_n[tid] = a.imp_n[tid];
         }
     }
-    for (int i = tid; i < W * W; i += NW) {
-        s_nb[i] = a.row_nb[i];
-        s_xy[i] = a.row_xy[i];
+    for (int i = tid; i < WW; i += NW) {
+        const uint64_t nb = a.row_nb[i];
+        LatRow r;
+        r.dy = (lat_dym(nb) * 8 & 0xffff) | (lat_dyp(nb) * 8) << 16;
+        r.dz = (lat_dzm(nb) * 8 & 0xffff) | (lat_dzp(nb) * 8) << 16;
+        r.dpc = a.row_pc[i] * 16;
+        r.goff = 0;
+        s_row[i] = r;
     }
     // thread 0's control state: the next ticket, and early (relaxed) reads of
     // the flags of the region that ticket names
@@ -242,8 +259,17 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
         sm.n0 = sdr.n[0], sm.n1 = sdr.n[1], sm.n2 = sdr.n[2];
         sm.c0 = r.c[0], sm.c1 = r.c[1], sm.c2 = r.c[2];
         sm.gc = (long long)sm.c0 + (long long)sm.n0 * ((long long)sm.c1 + (long long)sm.n1 * sm.c2);
+        // the fast path needs the region clear of the seam and the row offsets
+        // within 32 bits
         sm.nowrap = sm.c0 >= R && sm.c0 + R < sm.n0 && sm.c1 >= R && sm.c1 + R < sm.n1 && sm.c2 >= R &&
-                    sm.c2 + R < sm.n2;
+                    sm.c2 + R < sm.n2 && (long long)sm.n0 * sm.n1 * (R + 1) < (1ll << 30);
+        // the rows' site offsets for this region's grid
+        if (sm.nowrap)
+            for (int i = tid; i < WW; i += NW) {
+                const uint32_t xy = __ldg(s_xy + i);
+                s_row[i].goff = sm.n0 * ((int)((xy >> 16) & 31u) - R + sm.n1 * ((int)((xy >> 21) & 31u) - R)) -
+                                lat_row_base(xy);
+            }
         const PhysConst q = sdr.q;
         const LevelCoef *__restrict__ coef = sdr.coef;
         float2 *const g_even = sdr.phi0;
@@ -252,47 +278,48 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
         unsigned long long t_start = 0;
         if (tid == 0 && a.trace) t_start = globaltimer_ns();
         const int par0 = r.tau_b & 1;  // level k of the region is global parity par0 ^ (k & 1)
+        __syncthreads();  // row offsets written
 
         // a region cut by the call's first level: its own cells of level k_lo - 1, whole
         if (r.k_lo > 0) {
             const int kb = r.k_lo - 1;
-            float2 *s_ph = (kb & 1) ? s_ph1 : s_ph0;
+            char *phb = (kb & 1) ? s_ph1 : s_ph0;
             const float2 *gp = (par0 ^ (kb & 1)) ? g_odd : g_even;
             const int off = s_cell_off[kb], n = s_cell_n[kb];
             for (int i = tid; i < n; i += NW) {
-                const uint32_t e = __ldg(a.cell + off + i);
+                const uint32_t e = __ldg(g_cell + off + i);
                 const int sl = lat_slot(e), row = lat_row(e);
-                const long long g = sm.of(sl, s_xy[row], R);
-                cp_async8(s_ph + sl, gp + g);
-                cp_async16(s_pc + sl + lat_dpc(s_nb[row]), gpc + g);
+                const long long g = sm.site(sl, row, s_row, s_xy, R);
+                cp_async8(phb + (sl << 3), gp + g);
+                cp_async16(s_pcb + (sl << 4) + s_row[row].dpc, gpc + g);
             }
         }
-        copy_entries<NW>(s_ring + (r.k_lo & 1) * a.max_cell_n, a.cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
+        copy_entries<NW>(s_ring + (r.k_lo & 1) * max_cell_n, g_cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
         uint32_t imp[kLatUI];
-        load_imports<NW>(imp, a.imp, s_imp_off[r.k_lo], s_imp_n[r.k_lo]);
+        load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo], s_imp_n[r.k_lo]);
         {
             const int kb = r.k_lo - 1;
-            issue_imports<NW>(imp, s_imp_n[r.k_lo], sm, s_nb, s_xy, R, s_pc, (kb & 1) ? s_ph1 : s_ph0,
+            issue_imports<NW>(imp, s_imp_n[r.k_lo], sm, s_row, s_xy, R, s_pcb, (kb & 1) ? s_ph1 : s_ph0,
                               (par0 ^ (kb & 1)) ? g_odd : g_even, gpc);
         }
-        if (r.k_lo < r.k_hi) load_imports<NW>(imp, a.imp, s_imp_off[r.k_lo + 1], s_imp_n[r.k_lo + 1]);
+        if (r.k_lo < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo + 1], s_imp_n[r.k_lo + 1]);
         LevelCoef co = coef[r.tau_b + r.k_lo - 1];
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
         for (int k = r.k_lo; k <= r.k_hi; ++k) {
             const int odd = k & 1;
-            const float2 *__restrict__ rd = odd ? s_ph0 : s_ph1;
-            float2 *__restrict__ wr = odd ? s_ph1 : s_ph0;
+            const char *rd = odd ? s_ph0 : s_ph1;
+            char *wr = odd ? s_ph1 : s_ph0;
             LevelCoef co_next = co;
             if (k < r.k_hi) {
                 // imports of level k + 1 (values of level k, into buffer k & 1), the
                 // cell entries of level k + 1, then the import entries of level k + 2
-                issue_imports<NW>(imp, s_imp_n[k + 1], sm, s_nb, s_xy, R, s_pc, wr, (par0 ^ odd) ? g_odd : g_even,
+                issue_imports<NW>(imp, s_imp_n[k + 1], sm, s_row, s_xy, R, s_pcb, wr, (par0 ^ odd) ? g_odd : g_even,
                                   gpc);
-                copy_entries<NW>(s_ring + ((k + 1) & 1) * a.max_cell_n, a.cell, s_cell_off[k + 1], s_cell_n[k + 1]);
+                copy_entries<NW>(s_ring + ((k + 1) & 1) * max_cell_n, g_cell, s_cell_off[k + 1], s_cell_n[k + 1]);
                 cp_async_commit();
-                if (k + 1 < r.k_hi) load_imports<NW>(imp, a.imp, s_imp_off[k + 2], s_imp_n[k + 2]);
+                if (k + 1 < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[k + 2], s_imp_n[k + 2]);
                 co_next = coef[r.tau_b + k];
             }
             if (tid == 0 && k == r.k_lo) {
@@ -304,27 +331,30 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
                         fv[i] = s_reg.pred[i] >= 0 ? ld_relaxed_gpu(a.flags + s_reg.pred[i]) : 0x7fffffff;
             }
             float2 *gout = (par0 ^ odd) ? g_odd : g_even;
-            const bool all = k == r.k_hi;
+            const uint32_t exp_phi = k == r.k_hi ? ~0u : kLatExpPhi;  // the call's last level: export all
+            const uint32_t exp_pc = k == r.k_hi ? ~0u : kLatExpPc;
             const int n = s_cell_n[k];
-            const uint32_t *ent = s_ring + odd * a.max_cell_n;
+            const uint32_t *ent = s_ring + odd * max_cell_n;
 #pragma unroll 2
             for (int i = tid; i < n; i += NW) {
                 const uint32_t e = ent[i];
                 const int sl = lat_slot(e), row = lat_row(e);
-                const uint64_t nb = s_nb[row];
-                const int pcx = sl + lat_dpc(nb);
-                const float4 v = s_pc[pcx];
+                const LatRow rr = s_row[row];
+                const int own = sl << 3;
+                const int pcoff = (sl << 4) + rr.dpc;
+                const float4 v = *reinterpret_cast<const float4 *>(s_pcb + pcoff);
                 float2 pi = make_float2(v.x, v.y), cc = make_float2(v.z, v.w);
-                const float2 out = site_update(rd[sl], rd[sl - 1], rd[sl + 1], rd[sl + lat_dym(nb)], rd[sl + lat_dyp(nb)],
-                                               rd[sl + lat_dzm(nb)], rd[sl + lat_dzp(nb)], pi, cc, co, q);
-                wr[sl] = out;
+                const float2 out = site_update(ld_f2(rd, own), ld_f2(rd, own - 8), ld_f2(rd, own + 8),
+                                               ld_f2(rd, own + (int)(short)rr.dy), ld_f2(rd, own + (rr.dy >> 16)),
+                                               ld_f2(rd, own + (int)(short)rr.dz), ld_f2(rd, own + (rr.dz >> 16)), pi,
+                                               cc, co, q);
+                *reinterpret_cast<float2 *>(wr + own) = out;
                 const float4 pcv = make_float4(pi.x, pi.y, cc.x, cc.y);
-                s_pc[pcx] = pcv;
-                const bool ephi = all || (e & kLatExpPhi), epc = all || (e & kLatExpPc);
-                if (ephi || epc) {
-                    const long long g = sm.of(sl, s_xy[row], R);
-                    if (ephi) gout[g] = out;
-                    if (epc) gpc[g] = pcv;
+                *reinterpret_cast<float4 *>(s_pcb + pcoff) = pcv;
+                if (e & (exp_phi | exp_pc)) {
+                    const long long g = sm.nowrap ? sm.gc + (sl + rr.goff) : sm.wrapped(sl, __ldg(s_xy + row), R);
+                    if (e & exp_phi) gout[g] = out;
+                    if (e & exp_pc) gpc[g] = pcv;
                 }
             }
             cp_async_wait_all();

@@ -190,7 +190,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     std::vector<int> tpc;
     std::vector<char> inflight_phi, inflight_pc;
     auto slot_of = [&](uint32_t e) { return sp::lat_slot(e); };
-    auto pc_of = [&](uint32_t e) { return sp::lat_slot(e) + sp::lat_dpc(t.row_nb[sp::lat_row(e)]); };
+    auto pc_of = [&](uint32_t e) { return sp::lat_slot(e) + t.row_pc[sp::lat_row(e)]; };
 
     for (int64_t id : order) {
         const int L = c.layer(id);
@@ -376,15 +376,16 @@ void lx_epochs(const int *layers, int n, int *first)
     for (int i = 0; i < n; ++i) sp::lat_next_epoch(&last, layers[i], &first[i]);
 }
 
-// Table statistics of size s: updates, slots, footprint cells, imports
-// (full, phi), exports (phi, (pi, c)), bytes read, bytes written, largest level.
+// Table statistics of size s: updates, phi slots, footprint cells, imports
+// (full, phi), exports (phi, (pi, c)), bytes read, bytes written, largest
+// level, (pi, c) slots, halo cells.
 int lx_stats(int s, int64_t *out)
 {
     sp::LatticeTables t;
     if (!sp::build_lattice_tables(s, &t).empty()) return -1;
-    out[0] = t.updates, out[1] = t.n_slots, out[2] = t.n_foot, out[3] = t.imports_full, out[4] = t.imports_phi;
+    out[0] = t.updates, out[1] = t.n_slots, out[2] = t.foot_cells, out[3] = t.imports_full, out[4] = t.imports_phi;
     out[5] = t.exports_phi, out[6] = t.exports_pc, out[7] = t.bytes_read, out[8] = t.bytes_written;
-    out[9] = t.max_level_cells;
+    out[9] = t.max_level_cells, out[10] = t.n_foot, out[11] = t.halo_cells;
     return 0;
 }
 

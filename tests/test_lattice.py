@@ -18,10 +18,10 @@ I64 = ctypes.c_int64
 
 
 def _stats(lx, s):
-    out = (I64 * 10)()
+    out = (I64 * 12)()
     assert lx.lx_stats(s, out) == 0
     keys = ("updates", "slots", "foot", "imp_full", "imp_phi", "exp_phi", "exp_pc", "bytes_read", "bytes_written",
-            "max_level")
+            "max_level", "pc_slots", "halo")
     return dict(zip(keys, list(out)))
 
 
@@ -92,7 +92,20 @@ def test_bytes_per_update_fall_with_region_size(lx):
         prev = b
     st = _stats(lx, 4)
     assert abs((st["bytes_read"] + st["bytes_written"]) / st["updates"] - 14.69) < 0.01
-    assert st["slots"] == 1225 and st["foot"] == 847 and st["max_level"] == 659
+    assert st["foot"] == 847 and st["foot"] + st["halo"] == 1225 and st["max_level"] == 659
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6])
+def test_bank_layout_pads_little(lx, s):
+    """The shared-memory layout that puts every slot on its bank residue
+    (x + a y + b z mod 16) pads the compact layout by at most 25 %, and by at
+    most 5 % at the sizes the kernel runs by default (s = 4, 6)."""
+    st = _stats(lx, s)
+    compact_phi, compact_pc = st["foot"] + st["halo"], st["foot"]
+    assert compact_phi <= st["slots"] <= 1.25 * compact_phi
+    assert compact_pc <= st["pc_slots"] <= 1.25 * compact_pc
+    if s in (4, 6):
+        assert st["slots"] <= 1.05 * compact_phi and st["pc_slots"] <= 1.05 * compact_pc
 
 
 def _coef_table(levels, nu, dt, lam, tau0, tau_ref):
