@@ -3,14 +3,17 @@
 Workload (the largest single-GPU configuration): the 1280^3 matter-era string
 field (nu = 2, tau0 = 10, tau_ref = tau0 + 2048 dt, lambda = 2, eta = 1,
 dx = 1, dt = 0.25), random-phase initial field from seed 0, 2048 leapfrog
-steps in FP32 with the Kahan-compensated drift, one mailbox slot.  One bench
-"step" is one pass of the whole hot path over a slice of that run: one
-sp_evolve call of 64 leapfrog steps (whole bands of regions: queue reset,
-persistent region kernel), continuing from where the previous step stopped;
-when a pass reaches level 2048 the initial field is restored (outside the
-timed region) and the run starts over.  Every band of the run has the same
-regions, so the rate over any slice is the rate of the whole run.  The
-state (50 GB) and mailboxes are far larger than L2, so no flush is needed.
+steps in FP32 with the Kahan-compensated drift, evolved as the paper's
+lattice of 4-cube regions (edge 16: 4096 site-updates over 16 levels per
+region, the state read and written in place).  One bench "step" is one pass of
+the whole hot path over a slice of that run: one sp_evolve call of 128
+leapfrog steps (ticket reset, persistent lattice kernel), continuing from
+where the previous step stopped; when a pass reaches level 2048 the initial
+field is restored (outside the timed region) and the run starts over.  Every
+call of the run has the same regions, so the rate over any slice is the rate
+of the whole run.  The state (50 GB) is far larger than L2, so no flush is
+needed.  --shape split measures the split tiling (base 16, 64-step calls of
+whole bands, mailboxes) instead.
 
 Printed (rank 0, one JSON line): value = site-updates/s from CUDA events on
 the library's stream around each sp_evolve call; the monolithic GPU sweep on
@@ -49,11 +52,13 @@ NU, TAU0, LAM, ETA, DX, DT = 2.0, 10.0, 2.0, 1.0, 1.0, 0.25
 SEED = 0
 # The workloads: grid side, leapfrog steps of the whole run, steps per bench
 # step (one sp_evolve call), region base.
-BIG = dict(N=1280, STEPS=2048, PER_STEP=64, B=16, SHAPE="split")
-SMALL = dict(N=128, STEPS=256, PER_STEP=256, B=16, SHAPE="split")
-# Lattice regions (4-cubes of edge B = 4s): 128-step bench steps (each call
-# pays for the layers cut by its first and last levels once).
-LATTICE_PER_STEP = 128
+# Default region geometry: the paper's 4-cube lattice (edge B = 4s = 16), one
+# bench step = one 128-step call (each call pays once for the layers its first
+# and last levels cut).  --shape split: the split tiling at base 16, 64-step
+# calls (whole bands).
+BIG = dict(N=1280, STEPS=2048, PER_STEP=128, B=16, SHAPE="lattice")
+SMALL = dict(N=128, STEPS=256, PER_STEP=256, B=16, SHAPE="lattice")
+SPLIT_PER_STEP = 64
 # Sample of the big workload that the FP64 oracle times on the host cores: the
 # first SAMPLE_Z planes of its initial field as a periodic slab.
 SAMPLE_Z = 32
@@ -513,7 +518,7 @@ def run_grid(args, w, extra=None):
         "roofline_alu": alu_roofline(updates, kern_mean, peaks_onchip[1]),
         "measured_onchip_peaks": {"smem_gbs": peaks_onchip[0], "fp32_tflops": peaks_onchip[1]},
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,  # per bench step: queue reset + persistent region kernel
+        "gpu_launches": 2 * args.steps,  # per bench step: ticket / queue reset + persistent region kernel
         "utilisation": utilisation,
         "clocks": clk,
         "wall_s_timed_region": wall,
@@ -735,8 +740,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-levels", type=int, default=4, help="leapfrog steps per reference-arm step")
     ap.add_argument("--base", type=int, default=0, help="region base (0: the workload's)")
-    ap.add_argument("--shape", default="split", choices=["split", "lattice"],
-                    help="region geometry: split tiling (pyramids and wedges) or the paper's 4-cube lattice")
+    ap.add_argument("--shape", default="lattice", choices=["split", "lattice"],
+                    help="region geometry: the paper's 4-cube lattice (default) or the split tiling "
+                         "(pyramids and wedges)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--grid", type=int, default=0, help="grid side (profiling of smaller cases only)")
     ap.add_argument("--per-step", type=int, default=0, help="leapfrog steps per bench step (profiling only)")
@@ -756,8 +762,8 @@ def main():
         setup_dist()
         ws, rank, _ = dist_env()
         w = dict(BIG, SHAPE=args.shape)
-        if args.shape == "lattice":
-            w["PER_STEP"] = LATTICE_PER_STEP
+        if args.shape == "split":
+            w["PER_STEP"] = SPLIT_PER_STEP
         if args.grid:
             w["N"] = args.grid
         if args.per_step:

@@ -93,11 +93,13 @@ def test_clock_parsing_reports_median_and_reasons():
     assert c == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"]}
 
 
-def test_committed_traffic_record_names_its_capture():
+@pytest.mark.parametrize("shape,kernel", [("split", "region_kernel"), ("lattice", "lattice_kernel")])
+def test_committed_traffic_record_names_its_capture(shape, kernel):
     import json
 
-    rec = json.load(open(os.path.join(ROOT, "profiles", "region_kernel_traffic.json")))
-    assert rec["kernel"] == "region_kernel" and "ncu" in rec["command"] and "--clock-control none" in rec["command"]
+    rec = json.load(open(os.path.join(ROOT, "profiles", bench.TRAFFIC_RECORD[shape])))
+    assert rec["kernel"] == kernel and "ncu" in rec["command"] and "--clock-control none" in rec["command"]
+    assert f"regex:{kernel}" in rec["command"]
     assert rec["region_base"] in (8, 16, 32) and rec["site_updates"] > 0
     assert rec["dram_bytes_read_per_launch"] > 0 and rec["dram_bytes_write_per_launch"] > 0
 
