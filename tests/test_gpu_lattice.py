@@ -207,3 +207,27 @@ def test_lattice_rate_128():
         print(f"\nlattice B={B}: {ms:.3f} ms per {steps} steps = {n ** 3 * steps / ms * 1e3:.3e} site-updates/s "
               f"({info['threads']} workers, {info['ctas_per_sm']} CTAs/SM, {info['bytes_per_update']:.2f} B/upd)")
     assert rates
+
+
+def test_lattice_autotune_picks_a_measured_size():
+    """SP_AUTOTUNE with lattice regions times every size that divides the grid
+    (and every worker count that fits) on scratch copies of the state, keeps
+    the fastest per site-update, and leaves the state untouched: the plan it
+    returns still evolves bit-exactly."""
+    n, steps = (48, 48, 48), 20
+    p = params_for(n, 2.0, steps)
+    st = inputs.initial_state(n, 9, "phase")
+    g = sp.Grid([p])
+    try:
+        g.write_state(0, *st)
+        g.set_option(sp.SP_OPT_REGION_SHAPE, sp.SP_SHAPE_LATTICE)
+        g.plan(base_B=sp.SP_AUTOTUNE, threads=sp.SP_AUTOTUNE)
+        info = g.plan_info(0)
+        assert info["autotuned"] == 1 and info["tune_candidates"] >= 3
+        assert info["base_B"] in (8, 12, 16, 24) and info["region_shape"] == sp.SP_SHAPE_LATTICE
+        assert_bit_equal(g.read_state(0), st)  # the trials ran on copies
+        g.evolve(steps)
+        got = g.read_state(0)
+    finally:
+        g.close()
+    assert_bit_equal(got, run(p, st, [steps], mono=True)[0])
