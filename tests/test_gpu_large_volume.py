@@ -1,12 +1,15 @@
 """The large-volume workload on one GPU: a 1280^3 matter-era network (nu = 2,
 lambda = 2, eta = 1, random phases, 2048 steps, energy and string length
-every 128 steps), region base 16.
+every 128 steps), as the bench runs it: 4-cube lattice regions of edge 16
+(128-step calls), and the split tiling at base 16.
 
-With the ring of two mailbox slots the sloped-surface mailboxes of this grid
-would take 2 x 169 GB, which with the 50 GB state does not fit in the GPU's
-memory; with one slot for every band (the default) they take 169 GB.  The FP64 oracle of this size is out of reach (67 GB of host state and
-4.4e12 site-updates), so parity at full size is the property that holds at
-any size: the region path equals the monolithic sweep bit for bit (phi, pi
+With the ring of two mailbox slots the split tiling's sloped-surface
+mailboxes of this grid would take 2 x 169 GB, which with the 50 GB state does
+not fit in the GPU's memory; with one slot for every band (the default) they
+take 169 GB.  Lattice regions need no mailbox, only the odd-level phi array
+(16.8 GB).  The FP64 oracle of this size is out of reach (67 GB of host state
+and 4.4e12 site-updates), so parity at full size is the property that holds
+at any size: the region path equals the monolithic sweep bit for bit (phi, pi
 and c), with the energy and string diagnostics finite along the way.
 """
 import concurrent.futures as cf
@@ -53,17 +56,21 @@ def bit_equal(a, b):
     return torch.equal(a.view(torch.float32).view(torch.int32), b.view(torch.float32).view(torch.int32))
 
 
-def test_large_volume_matter_era_region_equals_sweep():
+@pytest.mark.parametrize("shape", ["lattice", "split"])
+def test_large_volume_matter_era_region_equals_sweep(shape):
     n = (N, N, N)
     sites = N ** 3
-    need = 24 * sites + 8 * sites + 170e9 + 1e9  # state, initial phi copy, one mailbox slot, counters + queue
+    lattice = shape == "lattice"
+    # state, initial phi copy, then one mailbox slot + counters and queue (split) or the
+    # odd-level phi array + flags (lattice)
+    need = 24 * sites + 8 * sites + (8 * sites + 1e9 if lattice else 170e9 + 1e9)
     free, _ = torch.cuda.mem_get_info()
     if free < need * 1.02:
         pytest.skip(f"needs {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
     p = sp.make_params(n, dx=1.0, dt=0.25, lam=2.0, eta=1.0, nu=2.0, tau0=10.0, tau_ref=10.0 + STEPS * 0.25)
-    shape = (N, N, N)
-    phi = torch.empty(shape, dtype=torch.complex64, device="cuda")
-    pic = torch.zeros(shape + (2,), dtype=torch.complex64, device="cuda")
+    dims = (N, N, N)
+    phi = torch.empty(dims, dtype=torch.complex64, device="cuda")
+    pic = torch.zeros(dims + (2,), dtype=torch.complex64, device="cuda")
     t0 = time.time()
     fill_random_phase(phi, n, 0)
     phi0 = phi.clone()
@@ -71,10 +78,13 @@ def test_large_volume_matter_era_region_equals_sweep():
 
     g = sp.Grid([p], states=[(phi, pic)])
     try:
-        g.plan(base_B=16, threads=0)
+        g.plan(base_B=16, threads=0, shape=sp.SP_SHAPE_LATTICE if lattice else sp.SP_SHAPE_SPLIT)
         info = g.plan_info(0)
         assert info["base_B"] == 16
-        assert info["mailbox_slots"] == 1 and 0 < info["mailbox_bytes"] < 200e9
+        if lattice:
+            assert info["region_shape"] == sp.SP_SHAPE_LATTICE and info["mailbox_bytes"] == 8 * sites
+        else:
+            assert info["mailbox_slots"] == 1 and 0 < info["mailbox_bytes"] < 200e9
         diags = []
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         region_ms = 0.0
@@ -99,7 +109,7 @@ def test_large_volume_matter_era_region_equals_sweep():
         gb.close()
 
     rate = sites * STEPS / (region_ms * 1e-3)
-    print(f"\n1280^3 x {STEPS}: init {t_init:.1f} s, region path {region_ms / 1e3:.2f} s "
+    print(f"\n1280^3 x {STEPS} ({shape}): init {t_init:.1f} s, region path {region_ms / 1e3:.2f} s "
           f"({rate:.3e} site-updates/s, mailboxes {info['mailbox_bytes'] / 1e9:.1f} GB), sweep {sweep_s:.2f} s; "
           f"string length {diags[0]['string_length']:.4g} -> {diags[-1]['string_length']:.4g}, "
           f"energy {diags[0]['total']:.6g} -> {diags[-1]['total']:.6g}")
