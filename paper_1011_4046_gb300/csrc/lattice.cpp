@@ -229,7 +229,8 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         t->row_pc[rv.first] = v[4];
     }
     auto entry_of = [&](const R3 &r) {
-        return (uint32_t)slot.at(r) | (uint32_t)row_index(r.y, r.z) << kLatRowShift;
+        return (uint32_t)slot.at(r) | (uint32_t)row_index(r.y, r.z) << kLatRowShift |
+               (uint32_t)(r.x + 2 * s) << kLatRxShift;
     };
 
     // Each level's cells in groups of 16 with distinct slot residues mod 16
@@ -320,6 +321,18 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         *pc = sl + t->row_pc[row];
     };
 
+    // check 0: every entry's x field is its cell's x offset (plus 2s)
+    for (int k = 0; k < K; ++k) {
+        auto x_ok = [&](uint32_t e) {
+            int rx, ry, rz;
+            t->offset_of(lat_slot(e), lat_row(e), &rx, &ry, &rz);
+            return lat_rx2s(e) == rx + 2 * s;
+        };
+        for (int i = t->cell_off[k]; i < t->cell_off[k] + t->cell_n[k]; ++i)
+            if (!x_ok(t->cell[i])) return fail("cell entry with a wrong x field (level %d)", k);
+        for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i)
+            if (!x_ok(t->imp[i])) return fail("import entry with a wrong x field (level %d)", k);
+    }
     // check 1: entries decode to their cells, and every value level k reads
     // is computed at level k - 1 or imported before level k
     for (int k = 0; k < K; ++k) {

@@ -63,7 +63,7 @@
 namespace sp {
 
 constexpr int kLatMinS = 1;
-constexpr int kLatMaxS = 6;  // slot indices are 12 bits, coordinates 5 bits per axis
+constexpr int kLatMaxS = 6;  // slot indices are 13 bits, coordinates 5 bits per axis
 
 // Shared-memory phi slots are laid out in rows of constant (y, z), each
 // contiguous in x: slot(r) = row_base(row) + rx with
@@ -80,10 +80,12 @@ constexpr int kLatMaxS = 6;  // slot indices are 12 bits, coordinates 5 bits per
 //     (rz + 2s) << 21, for the cell's offset from the region's centre.
 // Cell entry (32 bits), the per-level work list:
 //   bits 0..12 slot; bits 13..22 row; bit 23 export phi at this level;
-//   bit 24 export (pi, c) at this level.  Each level's list is ordered so
+//   bit 24 export (pi, c) at this level; bits 25..29 the cell's x offset
+//   from the region's centre plus 2s (so a site index needs no per-cell
+//   table read beyond the row's).  Each level's list is ordered so
 //   that every 16 consecutive entries have distinct slot residues mod 16,
 //   the first and last 8 of them distinct residues mod 8.
-// Import entry (32 bits): slot | row << 13 | full << 23.  A full import
+// Import entry (32 bits): slot | row << 13 | full << 23 | (x offset + 2s) << 25.  A full import
 // loads phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k;
 // otherwise only phi(k-1) of a neighbour outside the region.
 // Every level's lists start on a 16-byte boundary (padded with zero entries
@@ -94,6 +96,8 @@ constexpr uint32_t kLatRowMask = 0x3ffu;
 constexpr uint32_t kLatExpPhi = 1u << 23;
 constexpr uint32_t kLatExpPc = 1u << 24;
 constexpr uint32_t kLatImpFull = 1u << 23;
+constexpr int kLatRxShift = 25;
+constexpr uint32_t kLatRxMask = 0x1fu;  // 4s <= 24
 
 LAT_HD int lat_slot(uint32_t e) { return (int)(e & kLatSlotMask); }
 LAT_HD int lat_row(uint32_t e) { return (int)((e >> kLatRowShift) & kLatRowMask); }
@@ -102,6 +106,8 @@ LAT_HD int lat_dyp(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 16) & 0
 LAT_HD int lat_dzm(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 32) & 0xffffu); }
 LAT_HD int lat_dzp(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 48) & 0xffffu); }
 LAT_HD int lat_row_base(uint32_t xy) { return (int)(int16_t)(xy & 0xffffu); }
+// x offset from the region's centre, plus 2s
+LAT_HD int lat_rx2s(uint32_t e) { return (int)((e >> kLatRxShift) & kLatRxMask); }
 
 struct LatticeTables {
     int s = 0, K = 0;             // K = 4s levels per region

@@ -1115,7 +1115,7 @@ int choose_lattice_B(const sp_params &p, int requested)
         if (B < 4 || B > 4 * sp::kLatMaxS || B % 4) return false;
         for (int d = 0; d < 3; ++d)
             if (p.n[d] % B != 0) return false;
-        return true;
+        return (long long)p.n[1] * p.n[2] <= 0xffffffffll;  // a row's y + n1 z is 32 bits
     };
     if (requested) return ok(requested) ? requested : -1;
     for (int B : {16, 8, 4})

@@ -19,8 +19,9 @@
 // ahead (cp.async), each thread's import entries are held in registers a
 // level ahead, so no table read waits on memory.  A cell's neighbours, its
 // (pi, c) slot and its site index follow from its slot and one 16-byte
-// per-row record in shared memory (byte offsets; the site offsets are
-// refilled for each region's grid).
+// per-row record in shared memory (byte offsets; the row's wrapped (y, z)
+// index is refilled for each region), and the site's x follows from the x
+// field of the entry, so a site index costs no branch and no table read.
 //
 // Regions are handed out by ticket in layer order (one atomic per region,
 // taken a region ahead; the next region's predecessor flags are read early,
@@ -44,17 +45,18 @@ namespace {
 constexpr int kLatUI = 4;
 
 // Per-row record in shared memory (16 bytes): byte offsets, from a cell's phi
-// slot, of its y - 1 / y + 1 neighbours (x: low / high 16 bits, signed) and
-// z - 1 / z + 1 neighbours (y); the byte offset of its (pi, c) slot minus
-// 16 x its phi slot (z); and, for the region being evolved, the offset that
-// turns a slot into a site index, site = centre + slot + w (rows that cross
-// the grid's seam take the wrapped path instead).
+// slot, of its y - 1 / y + 1 neighbours (dy: low / high 16 bits, signed) and
+// z - 1 / z + 1 neighbours (dz); the byte offset of its (pi, c) slot minus
+// 16 x its phi slot; and, for the region being evolved, the row's y + n1 z
+// (both wrapped into the grid).
 struct alignas(16) LatRow {
-    int dy, dz, dpc, goff;
+    int dy, dz, dpc;
+    unsigned yz;
 };
 
 // Shared-memory layout of one region (bytes): (pi, c) slots, the two phi
-// buffers, the row records and a ring of two levels' cell entries.
+// buffers, the row records and a ring of two levels' cell entries (every
+// cp.async16 destination on a 16-byte boundary).
 struct LatSmem {
     size_t pc, ph0, ph1, row, ring, total;
     __host__ __device__ LatSmem(int n_slots, int n_foot, int W, int max_cell_n)
@@ -108,7 +110,7 @@ __device__ bool lat_decode(const LatArgs &a, unsigned t, int epoch, LatRegion *o
     return true;
 }
 
-// Thread 0: bounded wait until every predecessor of r has reported done
+// Control thread: bounded wait until every predecessor of r has reported done
 // (acquire).  False (and the error word set) when a wait gave up or another
 // CTA failed.
 __device__ bool lat_wait(const LatArgs &a, const LatRegion &r)
@@ -133,29 +135,16 @@ __device__ bool lat_wait(const LatArgs &a, const LatRegion &r)
     return true;
 }
 
-// Site index of the cell in slot sl of row `row`: centre + slot + row offset
-// for a region clear of the grid's seam, one wrap per axis otherwise.
-struct SiteMap {
-    int n0, n1, n2;
-    int c0, c1, c2;
-    long long gc;  // site index of the centre
-    bool nowrap;
-    __device__ __forceinline__ long long wrapped(int sl, uint32_t xy, int R) const
-    {
-        int x = c0 + sl - lat_row_base(xy), y = c1 + (int)((xy >> 16) & 31u) - R, z = c2 + (int)((xy >> 21) & 31u) - R;
-        x += x < 0 ? n0 : 0;
-        x -= x >= n0 ? n0 : 0;
-        y += y < 0 ? n1 : 0;
-        y -= y >= n1 ? n1 : 0;
-        z += z < 0 ? n2 : 0;
-        z -= z >= n2 ? n2 : 0;
-        return (long long)x + (long long)n0 * ((long long)y + (long long)n1 * z);
-    }
-    __device__ __forceinline__ long long site(int sl, int row, const LatRow *s_row, const uint32_t *g_xy, int R) const
-    {
-        return nowrap ? gc + (sl + s_row[row].goff) : wrapped(sl, __ldg(g_xy + row), R);
-    }
-};
+// Site index of the cell of entry e in a row with wrapped index yz = y + n1 z:
+// x = (centre x - 2s) + the entry's x field, wrapped once (branch-free;
+// regions are narrower than the grid, so one wrap suffices).
+__device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, int cx, int n0)
+{
+    int x = cx + lat_rx2s(e);
+    x += x < 0 ? n0 : 0;
+    x -= x >= n0 ? n0 : 0;
+    return (unsigned long long)yz * (unsigned)n0 + (unsigned)x;
+}
 
 template <int NW>
 __device__ __forceinline__ void load_imports(uint32_t (&v)[kLatUI], const uint32_t *__restrict__ tab, int off, int n)
@@ -170,18 +159,19 @@ __device__ __forceinline__ void load_imports(uint32_t (&v)[kLatUI], const uint32
 // cp.async of the values in entries v (imports of one level: phi of one
 // level into the phi buffer at byte address phb, and (pi, c) of full imports).
 template <int NW>
-__device__ __forceinline__ void issue_imports(const uint32_t (&v)[kLatUI], int n, const SiteMap &sm,
-                                              const LatRow *s_row, const uint32_t *s_xy, int R, char *pcb, char *phb,
-                                              const float2 *gphi, const float4 *gpc)
+__device__ __forceinline__ void issue_imports(const uint32_t (&v)[kLatUI], int n, int cx, int n0,
+                                              const LatRow *s_row, char *pcb, char *phb, const float2 *gphi,
+                                              const float4 *gpc)
 {
 #pragma unroll
     for (int u = 0; u < kLatUI; ++u) {
         if ((int)threadIdx.x + u * NW < n) {
             const uint32_t e = v[u];
             const int sl = lat_slot(e), row = lat_row(e);
-            const long long g = sm.site(sl, row, s_row, s_xy, R);
+            const LatRow rr = s_row[row];
+            const unsigned long long g = lat_site(e, rr.yz, cx, n0);
             cp_async8(phb + (sl << 3), gphi + g);
-            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + s_row[row].dpc, gpc + g);
+            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
         }
     }
 }
@@ -215,7 +205,7 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
     char *s_ph0 = reinterpret_cast<char *>(smem + L.ph0);
     char *s_ph1 = reinterpret_cast<char *>(smem + L.ph1);
     LatRow *s_row = reinterpret_cast<LatRow *>(smem + L.row);
-    const uint32_t *__restrict__ s_xy = a.row_xy;  // global (read through L1): wrapped sites and per-region offsets
+    const uint32_t *__restrict__ g_xy = a.row_xy;  // row coordinates, for the per-region row indices
     uint32_t *s_ring = reinterpret_cast<uint32_t *>(smem + L.ring);
     const uint32_t *__restrict__ g_cell = a.cell;
     const uint32_t *__restrict__ g_imp = a.imp;
@@ -233,16 +223,19 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
         r.dy = (lat_dym(nb) * 8 & 0xffff) | (lat_dyp(nb) * 8) << 16;
         r.dz = (lat_dzm(nb) * 8 & 0xffff) | (lat_dzp(nb) * 8) << 16;
         r.dpc = a.row_pc[i] * 16;
-        r.goff = 0;
+        r.yz = 0;
         s_row[i] = r;
     }
-    // thread 0's control state: the next ticket, and early (relaxed) reads of
-    // the flags of the region that ticket names
+    // The control thread is the last one: cells are dealt out from thread 0,
+    // so it has the least evolution work at every level.  Its state: the next
+    // ticket, and early (relaxed) reads of the flags of the region that
+    // ticket names.
+    const int ctl = NW - 1;
     unsigned next = 0;
     int epoch = 0;
     int fv[4] = {0, 0, 0, 0};
     bool early = false;
-    if (tid == 0) {
+    if (tid == ctl) {
         epoch = *(volatile int *)&a.ctl->epoch;
         s_stop = 0;
         const unsigned t = atomicAdd(&a.ctl->head, 1u);
@@ -255,30 +248,29 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
     while (!s_stop) {
         const LatRegion r = s_reg;
         const LatSimDev &sdr = a.sims[r.sim];
-        SiteMap sm;
-        sm.n0 = sdr.n[0], sm.n1 = sdr.n[1], sm.n2 = sdr.n[2];
-        sm.c0 = r.c[0], sm.c1 = r.c[1], sm.c2 = r.c[2];
-        sm.gc = (long long)sm.c0 + (long long)sm.n0 * ((long long)sm.c1 + (long long)sm.n1 * sm.c2);
-        // the fast path needs the region clear of the seam and the row offsets
-        // within 32 bits
-        sm.nowrap = sm.c0 >= R && sm.c0 + R < sm.n0 && sm.c1 >= R && sm.c1 + R < sm.n1 && sm.c2 >= R &&
-                    sm.c2 + R < sm.n2 && (long long)sm.n0 * sm.n1 * (R + 1) < (1ll << 30);
-        // the rows' site offsets for this region's grid
-        if (sm.nowrap)
+        const int n0 = sdr.n[0], cx = r.c[0] - R;
+        // the rows' wrapped y + n1 z for this region
+        {
+            const int n1 = sdr.n[1], n2 = sdr.n[2];
             for (int i = tid; i < WW; i += NW) {
-                const uint32_t xy = __ldg(s_xy + i);
-                s_row[i].goff = sm.n0 * ((int)((xy >> 16) & 31u) - R + sm.n1 * ((int)((xy >> 21) & 31u) - R)) -
-                                lat_row_base(xy);
+                const uint32_t xy = __ldg(g_xy + i);
+                int y = r.c[1] + (int)((xy >> 16) & 31u) - R, z = r.c[2] + (int)((xy >> 21) & 31u) - R;
+                y += y < 0 ? n1 : 0;
+                y -= y >= n1 ? n1 : 0;
+                z += z < 0 ? n2 : 0;
+                z -= z >= n2 ? n2 : 0;
+                s_row[i].yz = (unsigned)y + (unsigned)n1 * (unsigned)z;
             }
+        }
         const PhysConst q = sdr.q;
         const LevelCoef *__restrict__ coef = sdr.coef;
         float2 *const g_even = sdr.phi0;
         float2 *const g_odd = sdr.phi1;
         float4 *const gpc = sdr.pc;
         unsigned long long t_start = 0;
-        if (tid == 0 && a.trace) t_start = globaltimer_ns();
+        if (tid == ctl && a.trace) t_start = globaltimer_ns();
         const int par0 = r.tau_b & 1;  // level k of the region is global parity par0 ^ (k & 1)
-        __syncthreads();  // row offsets written
+        __syncthreads();  // row indices written
 
         // a region cut by the call's first level: its own cells of level k_lo - 1, whole
         if (r.k_lo > 0) {
@@ -289,9 +281,10 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
             for (int i = tid; i < n; i += NW) {
                 const uint32_t e = __ldg(g_cell + off + i);
                 const int sl = lat_slot(e), row = lat_row(e);
-                const long long g = sm.site(sl, row, s_row, s_xy, R);
+                const LatRow rr = s_row[row];
+                const unsigned long long g = lat_site(e, rr.yz, cx, n0);
                 cp_async8(phb + (sl << 3), gp + g);
-                cp_async16(s_pcb + (sl << 4) + s_row[row].dpc, gpc + g);
+                cp_async16(s_pcb + (sl << 4) + rr.dpc, gpc + g);
             }
         }
         copy_entries<NW>(s_ring + (r.k_lo & 1) * max_cell_n, g_cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
@@ -299,7 +292,7 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
         load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo], s_imp_n[r.k_lo]);
         {
             const int kb = r.k_lo - 1;
-            issue_imports<NW>(imp, s_imp_n[r.k_lo], sm, s_row, s_xy, R, s_pcb, (kb & 1) ? s_ph1 : s_ph0,
+            issue_imports<NW>(imp, s_imp_n[r.k_lo], cx, n0, s_row, s_pcb, (kb & 1) ? s_ph1 : s_ph0,
                               (par0 ^ (kb & 1)) ? g_odd : g_even, gpc);
         }
         if (r.k_lo < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo + 1], s_imp_n[r.k_lo + 1]);
@@ -315,14 +308,14 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
             if (k < r.k_hi) {
                 // imports of level k + 1 (values of level k, into buffer k & 1), the
                 // cell entries of level k + 1, then the import entries of level k + 2
-                issue_imports<NW>(imp, s_imp_n[k + 1], sm, s_row, s_xy, R, s_pcb, wr, (par0 ^ odd) ? g_odd : g_even,
+                issue_imports<NW>(imp, s_imp_n[k + 1], cx, n0, s_row, s_pcb, wr, (par0 ^ odd) ? g_odd : g_even,
                                   gpc);
                 copy_entries<NW>(s_ring + ((k + 1) & 1) * max_cell_n, g_cell, s_cell_off[k + 1], s_cell_n[k + 1]);
                 cp_async_commit();
                 if (k + 1 < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[k + 2], s_imp_n[k + 2]);
                 co_next = coef[r.tau_b + k];
             }
-            if (tid == 0 && k == r.k_lo) {
+            if (tid == ctl && k == r.k_lo) {
                 // every thread has copied the descriptor: decode the next
                 // region into it and read its predecessors' flags early
                 early = lat_decode(a, next, epoch, &s_reg);
@@ -352,7 +345,7 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
                 const float4 pcv = make_float4(pi.x, pi.y, cc.x, cc.y);
                 *reinterpret_cast<float4 *>(s_pcb + pcoff) = pcv;
                 if (e & (exp_phi | exp_pc)) {
-                    const long long g = sm.nowrap ? sm.gc + (sl + rr.goff) : sm.wrapped(sl, __ldg(s_xy + row), R);
+                    const unsigned long long g = lat_site(e, rr.yz, cx, n0);
                     if (e & exp_phi) gout[g] = out;
                     if (e & exp_pc) gpc[g] = pcv;
                 }
@@ -361,7 +354,7 @@ __global__ void __launch_bounds__(NW, (NW <= 64 ? 8 : NW <= 128 ? kLatMinBlocks 
             __syncthreads();
             co = co_next;
         }
-        if (tid == 0) {
+        if (tid == ctl) {
             if (a.trace) {
                 a.trace[2 * r.id] = t_start;
                 a.trace[2 * r.id + 1] = globaltimer_ns();
