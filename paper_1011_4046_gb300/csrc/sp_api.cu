@@ -1164,10 +1164,14 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         const sp::LatticeTables &t = it->second.host;
         GroupCfg c;
         c.B = 4 * it->first;
-        // default: the fewest workers (at least 128) whose registers hold a level's entries
+        // default (measured): 128 workers up to s = 3, 192 at s = 4, then the
+        // fewest of 256 and 512 whose registers hold a level's import entries
         c.threads = threads;
-        for (int nt : {128, 256, 512})
-            if (!c.threads && sp::lattice_threads_fit(nt, t.max_imp_n)) c.threads = nt;
+        const int s_lat = it->first;
+        for (int nt : {128, 192, 256, 512}) {
+            const bool pref = nt == 128 ? s_lat <= 3 : nt == 192 ? s_lat == 4 : true;
+            if (!c.threads && pref && sp::lattice_threads_fit(nt, t.max_imp_n)) c.threads = nt;
+        }
         c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot, t.rb_side, t.max_cell_n);
         if (c.smem > 227 * 1024 || !sp::lattice_threads_fit(c.threads, t.max_imp_n)) return SP_EINVAL;
         e = sp::lattice_occupancy(c.threads, c.smem, &c.ctas_per_sm);
@@ -1326,7 +1330,7 @@ int autotune_lattice(sp_grid *g, int base_B, int block_shape, std::vector<int> *
     }
     if (sizes.empty()) return SP_EINVAL;
     const std::vector<int> shapes =
-        block_shape == SP_AUTOTUNE ? std::vector<int>{64, 128, 256, 512} : std::vector<int>{block_shape};
+        block_shape == SP_AUTOTUNE ? std::vector<int>{64, 128, 192, 256, 512} : std::vector<int>{block_shape};
     constexpr int kTrialSteps = 32;
     double best = 0.0;
     bool have = false;

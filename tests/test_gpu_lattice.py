@@ -78,9 +78,9 @@ def test_lattice_bit_exact_vs_monolithic(B, n, calls, nu):
     assert_bit_equal(reg, run(p, st, calls, mono=True)[0])
 
 
-@pytest.mark.parametrize("B,threads", [(16, 256), (16, 512), (8, 64), (12, 64)])
+@pytest.mark.parametrize("B,threads", [(16, 128), (16, 256), (16, 512), (8, 64), (12, 64), (20, 192)])
 def test_lattice_worker_counts(B, threads):
-    n, steps = (48, 48, 48), 24
+    n, steps = ((48, 48, 48) if 48 % B == 0 else (40, 60, 40)), 24
     p = params_for(n, 2.0, steps)
     st = inputs.initial_state(n, 5, "phase")
     reg, info = run(p, st, [steps], base_B=B, threads=threads)
