@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <map>
 #include <set>
+#include <tuple>
+#include <utility>
 
 namespace sp {
 
@@ -297,8 +299,9 @@ std::string build_lattice_tables(int s, LatticeTables *t)
             }
         }
         std::vector<std::pair<int, uint32_t>> list;  // ascending slots
-        for (const R3 &r : full) list.push_back({slot.at(r), entry_of(r) | kLatImpFull});
-        for (const R3 &r : phi) list.push_back({slot.at(r), entry_of(r)});
+        const uint32_t buf = ((k - 1) & 1) ? kLatImpBuf : 0u;
+        for (const R3 &r : full) list.push_back({slot.at(r), entry_of(r) | kLatImpFull | buf});
+        for (const R3 &r : phi) list.push_back({slot.at(r), entry_of(r) | buf});
         std::sort(list.begin(), list.end());
         for (const auto &e : list) t->imp.push_back(e.second);
         t->imp_n[k] = (int32_t)list.size();
@@ -308,6 +311,19 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         t->imports_phi += (int64_t)phi.size();
     }
     t->imp_off[K] = (int32_t)t->imp.size();
+    {
+        // every import in one list: by buffer, then offset (z, y, x)
+        std::vector<std::pair<std::tuple<int, int, int, int>, std::pair<uint32_t, uint32_t>>> all;
+        for (int k = 0; k < K; ++k)
+            for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i) {
+                const uint32_t e = t->imp[i];
+                int rx, ry, rz;
+                t->offset_of(lat_slot(e), lat_row(e), &rx, &ry, &rz);
+                all.push_back({{(e & kLatImpBuf) ? 1 : 0, rz, ry, rx}, {e, (uint32_t)k}});
+            }
+        std::sort(all.begin(), all.end());
+        for (const auto &x : all) t->imp_all.push_back(x.second.first), t->imp_all.push_back(x.second.second);
+    }
     t->bytes_read = 24 * t->imports_full + 8 * t->imports_phi;
     t->bytes_written = 8 * t->exports_phi + 16 * t->exports_pc;
 
@@ -372,6 +388,32 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         }
     }
 
+    // check 1b: each (slot, phi buffer) is imported at most once, and no cell
+    // computation writes it, or reads it, at a level before the import's (so
+    // a region may load all its imports at its start)
+    {
+        std::map<std::pair<int, int>, int> imp_level;
+        for (int k = 0; k < K; ++k)
+            for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i) {
+                const auto key = std::make_pair(lat_slot(t->imp[i]), (k - 1) & 1);
+                if (imp_level.count(key)) return fail("a slot of a phi buffer imported twice (level %d)", k);
+                if (((t->imp[i] & kLatImpBuf) != 0) != (((k - 1) & 1) != 0)) return fail("import buffer bit wrong");
+                imp_level[key] = k;
+            }
+        for (int k = 0; k < K; ++k)
+            for (int i = t->cell_off[k]; i < t->cell_off[k] + t->cell_n[k]; ++i) {
+                R3 r;
+                int nb[7], pc;
+                decode(t->cell[i], &r, nb, &pc);
+                auto w = imp_level.find(std::make_pair(nb[0], k & 1));
+                if (w != imp_level.end() && w->second > k) return fail("level %d writes a slot imported later", k);
+                for (int d = 0; d < 7; ++d) {
+                    auto q = imp_level.find(std::make_pair(nb[d], (k - 1) & 1));
+                    if (q != imp_level.end() && q->second > k) return fail("level %d reads a slot imported later", k);
+                }
+            }
+        if (t->imp_all.size() != 2 * (size_t)(t->imports_full + t->imports_phi)) return fail("import list incomplete");
+    }
     // check 2: every import is exported by the region computing it.  Place
     // the region at the origin (centre 0, bottom vertex at t = 0); the value
     // imported before level k is at (k - 1, r).

@@ -85,9 +85,18 @@ constexpr int kLatMaxS = 6;  // slot indices are 13 bits, coordinates 5 bits per
 //   table read beyond the row's).  Each level's list is ordered so
 //   that every 16 consecutive entries have distinct slot residues mod 16,
 //   the first and last 8 of them distinct residues mod 8.
-// Import entry (32 bits): slot | row << 13 | full << 23 | (x offset + 2s) << 25.  A full import
-// loads phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k;
-// otherwise only phi(k-1) of a neighbour outside the region.
+// Import entry (32 bits): slot | row << 13 | full << 23 | ((k - 1) & 1) << 24 |
+// (x offset + 2s) << 25, for an import before level k.  A full import loads
+// phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k; otherwise
+// only phi(k-1) of a neighbour outside the region.
+// Every value a region imports is final when the region starts (its producers
+// are its ancestors, which are done) and stays in place until the region is
+// done (whoever overwrites it depends on the region), and a region imports each
+// (slot, phi buffer) at most once and touches that slot of that buffer only
+// from the import's level on (the builder checks both), so a region may load
+// all its imports at its start: imp_all holds them in one list, sorted by
+// buffer and by offset from the centre (z, y, x: ascending addresses), each
+// with its level, which regions cut by a call's first or last level filter.
 // Every level's lists start on a 16-byte boundary (padded with zero entries
 // to a multiple of four).
 constexpr uint32_t kLatSlotMask = 0x1fffu;
@@ -96,6 +105,7 @@ constexpr uint32_t kLatRowMask = 0x3ffu;
 constexpr uint32_t kLatExpPhi = 1u << 23;
 constexpr uint32_t kLatExpPc = 1u << 24;
 constexpr uint32_t kLatImpFull = 1u << 23;
+constexpr uint32_t kLatImpBuf = 1u << 24;  // the phi buffer ((k - 1) & 1) of the value
 constexpr int kLatRxShift = 25;
 constexpr uint32_t kLatRxMask = 0x1fu;  // 4s <= 24
 
@@ -121,6 +131,7 @@ struct LatticeTables {
     std::vector<int32_t> cell_off, cell_n;  // K + 1 offsets (multiples of 4), K counts
     std::vector<uint32_t> imp;      // before level k: imp[imp_off[k] .. imp_off[k] + imp_n[k]), padded
     std::vector<int32_t> imp_off, imp_n;
+    std::vector<uint32_t> imp_all;  // pairs (entry, level k) of every import, address order
     int max_cell_n = 0, max_imp_n = 0;  // padded to multiples of 4
     // one whole region: site-updates, bytes read and written (this design)
     int64_t updates = 0, bytes_read = 0, bytes_written = 0;

@@ -55,7 +55,7 @@ struct TablesOnDevice {
 struct LatOnDevice {
     sp::LatticeTables host;
     uint32_t *d_cell = nullptr;
-    uint32_t *d_imp = nullptr;
+    uint32_t *d_imp_all = nullptr;  // imp_all: pairs (entry, level)
     uint64_t *d_nb = nullptr;
     int32_t *d_pcoff = nullptr;
     uint32_t *d_xy = nullptr;
@@ -630,7 +630,7 @@ void free_plan(sp_grid *g)
     g->mbox.clear();
     for (auto &kv : g->lat) {
         cudaFree(kv.second.d_cell);
-        cudaFree(kv.second.d_imp);
+        cudaFree(kv.second.d_imp_all);
         cudaFree(kv.second.d_nb);
         cudaFree(kv.second.d_pcoff);
         cudaFree(kv.second.d_xy);
@@ -964,7 +964,8 @@ int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
         a.per_layer_all = (unsigned)per_layer_all;
         a.total = (unsigned)(per_layer_all * Lcount);
         a.cell = ld.d_cell;
-        a.imp = ld.d_imp;
+        a.imp_all = reinterpret_cast<const uint2 *>(ld.d_imp_all);
+        a.n_imp_all = (int)(t.imp_all.size() / 2);
         a.row_nb = ld.d_nb;
         a.row_pc = ld.d_pcoff;
         a.row_xy = ld.d_xy;
@@ -974,11 +975,7 @@ int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
         a.fault_drop = g->fault_drop;
         for (int k = 0; k <= t.K; ++k) {
             a.cell_off[k] = t.cell_off[k];
-            a.imp_off[k] = t.imp_off[k];
-            if (k < t.K) {
-                a.cell_n[k] = t.cell_n[k];
-                a.imp_n[k] = t.imp_n[k];
-            }
+            if (k < t.K) a.cell_n[k] = t.cell_n[k];
         }
         sim_off.push_back(first);
         launches.push_back(l);
@@ -1140,14 +1137,14 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         if (!sp::build_lattice_tables(s, &ld.host).empty()) return SP_EINVAL;
         const sp::LatticeTables &t = ld.host;
         e = cudaMalloc((void **)&ld.d_cell, t.cell.size() * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp, std::max<size_t>(t.imp.size(), 4) * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp_all, std::max<size_t>(t.imp_all.size(), 4) * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_nb, t.row_nb.size() * sizeof(uint64_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_xy, t.row_xy.size() * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_pcoff, t.row_pc.size() * sizeof(int32_t));
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !t.imp.empty())
-            e = cudaMemcpy(ld.d_imp, t.imp.data(), t.imp.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !t.imp_all.empty())
+            e = cudaMemcpy(ld.d_imp_all, t.imp_all.data(), t.imp_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_nb, t.row_nb.data(), t.row_nb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -1164,16 +1161,12 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         const sp::LatticeTables &t = it->second.host;
         GroupCfg c;
         c.B = 4 * it->first;
-        // default (measured): 128 workers up to s = 3, 192 at s = 4, then the
-        // fewest of 256 and 512 whose registers hold a level's import entries
-        c.threads = threads;
+        // default (measured): 128 workers up to s = 3, 192 at s = 4, 256 at
+        // s = 5, 512 at s = 6
         const int s_lat = it->first;
-        for (int nt : {128, 192, 256, 512}) {
-            const bool pref = nt == 128 ? s_lat <= 3 : nt == 192 ? s_lat == 4 : true;
-            if (!c.threads && pref && sp::lattice_threads_fit(nt, t.max_imp_n)) c.threads = nt;
-        }
+        c.threads = threads ? threads : s_lat <= 3 ? 128 : s_lat == 4 ? 192 : s_lat == 5 ? 256 : 512;
         c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot, t.rb_side, t.max_cell_n);
-        if (c.smem > 227 * 1024 || !sp::lattice_threads_fit(c.threads, t.max_imp_n)) return SP_EINVAL;
+        if (c.smem > 227 * 1024) return SP_EINVAL;
         e = sp::lattice_occupancy(c.threads, c.smem, &c.ctas_per_sm);
         if (e != cudaSuccess || c.ctas_per_sm < 1) return SP_EINVAL;
         c.grid = c.ctas_per_sm * g->sm_count;

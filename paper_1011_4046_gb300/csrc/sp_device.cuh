@@ -184,17 +184,17 @@ struct LatArgs {
     long long fault_drop;            // region id (as in the trace) that never reports done (-1: none)
     unsigned per_layer_all, total;
     const uint32_t *cell;            // cell entries (lattice.h), all levels (16-byte aligned per level)
-    const uint32_t *imp;             // import entries, all levels
+    const uint2 *imp_all;            // (entry, level) of every import of a region, address order
     const uint64_t *row_nb;          // (4s + 1)^2 row records: neighbour steps
     const int32_t *row_pc;           // (4s + 1)^2 row records: (pi, c) index - slot
     const uint32_t *row_xy;          // (4s + 1)^2 row records: slot base, (y, z) offsets
-    int max_cell_n, pad1;            // longest level's cell list (padded)
+    int max_cell_n, n_imp_all;       // longest level's cell list (padded); imports of a region
     int *flags;
     Ctl *ctl;
     unsigned long long *trace;       // optional (start, end) globaltimer per region: simulation by
                                      // simulation, layer by layer (trace_base + layer * per_layer + idx)
-    int cell_off[4 * 6 + 1], imp_off[4 * 6 + 1];  // per level (entries)
-    int cell_n[4 * 6], imp_n[4 * 6];
+    int cell_off[4 * 6 + 1];  // per level (entries)
+    int cell_n[4 * 6];
 };
 
 struct RegionArgs {

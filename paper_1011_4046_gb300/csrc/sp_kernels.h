@@ -38,7 +38,6 @@ namespace sp {
 // error word, layer epoch) and the launch.
 size_t lattice_smem_bytes(int n_slots, int n_foot, int rb_side, int max_cell_n);
 bool lattice_valid_threads(int threads);
-bool lattice_threads_fit(int threads, int max_imports);
 cudaError_t lattice_occupancy(int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_lattice_reset(Ctl *ctl, int layers, cudaStream_t st);
 cudaError_t launch_lattice(const LatArgs &a, int threads, size_t smem, int grid, cudaStream_t st);

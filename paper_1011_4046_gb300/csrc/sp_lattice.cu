@@ -7,17 +7,17 @@
 // 1225 phi slots in two parity buffers and 847 (pi, c) slots, 33 KB), so
 // several regions run on one SM, one per CTA.  A region
 //   1. waits until its four predecessors (layer L - 1) have reported done,
-//   2. copies in the values it does not compute (cp.async, one level ahead of
-//      the evolution: phi of the halo and the whole state of cells entering
-//      the region), straight from the state arrays,
+//   2. copies in the values it does not compute (cp.async: phi of the halo
+//      and the whole state of cells entering the region), straight from the
+//      state arrays, all at its start and in address order (every one is
+//      final by then and stays in place until the region is done; lattice.h),
 //   3. evolves level by level in shared memory (the site update of
 //      sp_update.h), writing every value another region needs (a per-cell
 //      flag of the tables) straight into the state arrays,
 //   4. reports done with a release store of its layer number.
-// The per-level lists (cell and import entries, lattice.h) are the same for
+// The per-level cell lists and the import list (lattice.h) are the same for
 // every region: a level's cell entries are copied into shared memory a level
-// ahead (cp.async), each thread's import entries are held in registers a
-// level ahead, so no table read waits on memory.  A cell's neighbours, its
+// ahead (cp.async), so no table read waits on memory.  A cell's neighbours, its
 // (pi, c) slot and its site index follow from its slot and one 16-byte
 // per-row record in shared memory (byte offsets; the row's wrapped (y, z)
 // index is refilled for each region), and the site's x follows from the x
@@ -40,9 +40,6 @@
 namespace sp {
 
 namespace {
-
-// Import entries per thread and level held in registers (loaded a level ahead).
-constexpr int kLatUI = 4;
 
 // Per-row record in shared memory (16 bytes): byte offsets, from a cell's phi
 // slot, of its y - 1 / y + 1 neighbours (dy: low / high 16 bits, signed) and
@@ -146,33 +143,24 @@ __device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, 
     return (unsigned long long)yz * (unsigned)n0 + (unsigned)x;
 }
 
+// cp.async of every import of levels k_lo..k_hi of a region (the list of all
+// its imports, in address order): phi of one level into its buffer, and the
+// (pi, c) of full imports.  imp_all entries: (entry, import level).
 template <int NW>
-__device__ __forceinline__ void load_imports(uint32_t (&v)[kLatUI], const uint32_t *__restrict__ tab, int off, int n)
+__device__ __forceinline__ void issue_all_imports(const uint2 *__restrict__ imp_all, int n, int k_lo, int k_hi,
+                                                  int cx, int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
+                                                  const float2 *g0, const float2 *g1, const float4 *gpc)
 {
-#pragma unroll
-    for (int u = 0; u < kLatUI; ++u) {
-        const int i = (int)threadIdx.x + u * NW;
-        v[u] = i < n ? __ldg(tab + off + i) : 0u;
-    }
-}
-
-// cp.async of the values in entries v (imports of one level: phi of one
-// level into the phi buffer at byte address phb, and (pi, c) of full imports).
-template <int NW>
-__device__ __forceinline__ void issue_imports(const uint32_t (&v)[kLatUI], int n, int cx, int n0,
-                                              const LatRow *s_row, char *pcb, char *phb, const float2 *gphi,
-                                              const float4 *gpc)
-{
-#pragma unroll
-    for (int u = 0; u < kLatUI; ++u) {
-        if ((int)threadIdx.x + u * NW < n) {
-            const uint32_t e = v[u];
-            const int sl = lat_slot(e), row = lat_row(e);
-            const LatRow rr = s_row[row];
-            const unsigned long long g = lat_site(e, rr.yz, cx, n0);
-            cp_async8(phb + (sl << 3), gphi + g);
-            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
-        }
+    for (int i = (int)threadIdx.x; i < n; i += NW) {
+        const uint2 ie = __ldg(imp_all + i);
+        if ((int)ie.y < k_lo || (int)ie.y > k_hi) continue;
+        const uint32_t e = ie.x;
+        const int sl = lat_slot(e), row = lat_row(e);
+        const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
+        const LatRow rr = s_row[row];
+        const unsigned long long g = lat_site(e, rr.yz, cx, n0);
+        cp_async8((b ? ph1 : ph0) + (sl << 3), (b ? g1 : g0) + g);
+        if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
     }
 }
 
@@ -187,14 +175,14 @@ __device__ __forceinline__ void copy_entries(uint32_t *ring, const uint32_t *__r
 __device__ __forceinline__ float2 ld_f2(const char *base, int off) { return *reinterpret_cast<const float2 *>(base + off); }
 
 // CTAs per SM the register budget is set for (shared memory allows 5 regions
-// of edge 16 per SM; measured at 240^3: 192 workers at 4 per SM, 70
-// registers, 1.017e11 site-updates/s; 128 at 5 per SM 9.42e10; 192 at 5 per
-// SM, 56 registers, 9.10e10; 224 at 4 per SM 1.017e11; 256 at 4 per SM
-// 9.59e10).
+// of edge 16 per SM; measured at 240^3 with all imports at the region's
+// start: 192 workers at 5 per SM, 56 registers, 1.108e11 site-updates/s;
+// at 4 per SM, 72 registers, 1.020e11; 128 at 5 per SM 1.024e11; 256 at 3
+// per SM 9.32e10).
 template <int NW>
 constexpr int lat_min_blocks()
 {
-    return NW <= 64 ? 8 : NW <= 128 ? 6 : NW <= 192 ? 4 : NW <= 256 ? 3 : 1;
+    return NW <= 64 ? 8 : NW <= 128 ? 6 : NW <= 192 ? 5 : NW <= 256 ? 3 : 1;
 }
 
 template <int NW>
@@ -202,8 +190,7 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
     lattice_kernel(const LatArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_cell_off[4 * kLatMaxS + 1], s_cell_n[4 * kLatMaxS], s_imp_off[4 * kLatMaxS + 1],
-        s_imp_n[4 * kLatMaxS];
+    __shared__ int s_cell_off[4 * kLatMaxS + 1], s_cell_n[4 * kLatMaxS];
     __shared__ LatRegion s_reg;
     __shared__ int s_stop;
     const int tid = threadIdx.x;
@@ -217,14 +204,9 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
     const uint32_t *__restrict__ g_xy = a.row_xy;  // row coordinates, for the per-region row indices
     uint32_t *s_ring = reinterpret_cast<uint32_t *>(smem + L.ring);
     const uint32_t *__restrict__ g_cell = a.cell;
-    const uint32_t *__restrict__ g_imp = a.imp;
     if (tid <= a.K) {
         s_cell_off[tid] = a.cell_off[tid];
-        s_imp_off[tid] = a.imp_off[tid];
-        if (tid < a.K) {
-            s_cell_n[tid] = a.cell_n[tid];
-            s_imp_n[tid] = a.imp_n[tid];
-        }
+        if (tid < a.K) s_cell_n[tid] = a.cell_n[tid];
     }
     for (int i = tid; i < WW; i += NW) {
         const uint64_t nb = a.row_nb[i];
@@ -297,14 +279,10 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
             }
         }
         copy_entries<NW>(s_ring + (r.k_lo & 1) * max_cell_n, g_cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
-        uint32_t imp[kLatUI];
-        load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo], s_imp_n[r.k_lo]);
-        {
-            const int kb = r.k_lo - 1;
-            issue_imports<NW>(imp, s_imp_n[r.k_lo], cx, n0, s_row, s_pcb, (kb & 1) ? s_ph1 : s_ph0,
-                              (par0 ^ (kb & 1)) ? g_odd : g_even, gpc);
-        }
-        if (r.k_lo < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[r.k_lo + 1], s_imp_n[r.k_lo + 1]);
+        // every import of the region's levels; buffer b holds values of local
+        // levels of parity b, global parity par0 ^ b
+        issue_all_imports<NW>(a.imp_all, a.n_imp_all, r.k_lo, r.k_hi, cx, n0, s_row, s_pcb, s_ph0, s_ph1,
+                              par0 ? g_odd : g_even, par0 ? g_even : g_odd, gpc);
         LevelCoef co = coef[r.tau_b + r.k_lo - 1];
         cp_async_commit();
         cp_async_wait_all();
@@ -315,13 +293,9 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
             char *wr = odd ? s_ph1 : s_ph0;
             LevelCoef co_next = co;
             if (k < r.k_hi) {
-                // imports of level k + 1 (values of level k, into buffer k & 1), the
-                // cell entries of level k + 1, then the import entries of level k + 2
-                issue_imports<NW>(imp, s_imp_n[k + 1], cx, n0, s_row, s_pcb, wr, (par0 ^ odd) ? g_odd : g_even,
-                                  gpc);
+                // the cell entries of level k + 1
                 copy_entries<NW>(s_ring + ((k + 1) & 1) * max_cell_n, g_cell, s_cell_off[k + 1], s_cell_n[k + 1]);
                 cp_async_commit();
-                if (k + 1 < r.k_hi) load_imports<NW>(imp, g_imp, s_imp_off[k + 2], s_imp_n[k + 2]);
                 co_next = coef[r.tau_b + k];
             }
             if (tid == ctl && k == r.k_lo) {
@@ -432,10 +406,6 @@ size_t lattice_smem_bytes(int n_slots, int n_foot, int rb_side, int max_cell_n)
 }
 
 bool lattice_valid_threads(int threads) { return lattice_fn(threads) != nullptr; }
-
-// A worker count fits a lattice size when every level's imports fit the
-// entries each thread holds in registers.
-bool lattice_threads_fit(int threads, int max_imports) { return max_imports <= kLatUI * threads; }
 
 cudaError_t lattice_occupancy(int threads, size_t smem, int *blocks_per_sm)
 {

@@ -188,7 +188,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
     std::vector<int> tps[2];
     std::vector<float> pcs;
     std::vector<int> tpc;
-    std::vector<char> inflight_phi, inflight_pc;
     auto slot_of = [&](uint32_t e) { return sp::lat_slot(e); };
     auto pc_of = [&](uint32_t e) { return sp::lat_slot(e) + t.row_pc[sp::lat_row(e)]; };
 
@@ -201,7 +200,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         if (k_lo > k_hi) return err("empty region in the call"), finish(-1);
         for (int p = 0; p < 2; ++p) ps[p].assign(t.n_slots, {0, 0}), tps[p].assign(t.n_slots, -999);
         pcs.assign(4 * (size_t)t.n_foot, 0.0f), tpc.assign(t.n_foot, -999);
-        inflight_phi.assign(t.n_slots, 0), inflight_pc.assign(t.n_foot, 0);
         auto load = [&](uint32_t en, bool full, int k) {  // value of local level k (global tau_b + k)
             const int sl = slot_of(en);
             if (sl < 0 || sl >= t.n_slots) return err("slot out of range");
@@ -228,17 +226,16 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         if (k_lo > 0)
             for (int i = t.cell_off[k_lo - 1]; i < t.cell_off[k_lo - 1] + t.cell_n[k_lo - 1]; ++i)
                 if (!load(t.cell[i], true, k_lo - 1)) return finish(-1);
-        for (int i = t.imp_off[k_lo]; i < t.imp_off[k_lo] + t.imp_n[k_lo]; ++i)
-            if (!load(t.imp[i], (t.imp[i] & sp::kLatImpFull) != 0, k_lo - 1)) return finish(-1);
+        // every import of the region's levels, at its start, in the kernel's
+        // order (the one list of all imports, filtered by level)
+        for (size_t i = 0; i + 1 < t.imp_all.size(); i += 2) {
+            const uint32_t en = t.imp_all[i];
+            const int kk = (int)t.imp_all[i + 1];
+            if (kk < k_lo || kk > k_hi) continue;
+            if (((en & sp::kLatImpBuf) != 0) != (((kk - 1) & 1) != 0)) return err("import buffer bit"), finish(-1);
+            if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1)) return finish(-1);
+        }
         for (int k = k_lo; k <= k_hi; ++k) {
-            // next level's imports are in flight during this level
-            std::vector<int> fl_phi, fl_pc;
-            if (k < k_hi)
-                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 1] + t.imp_n[k + 1]; ++i) {
-                    const int sl = slot_of(t.imp[i]);
-                    inflight_phi[sl] = 1, fl_phi.push_back(sl);
-                    if (t.imp[i] & sp::kLatImpFull) inflight_pc[pc_of(t.imp[i])] = 1, fl_pc.push_back(pc_of(t.imp[i]));
-                }
             const int tau = tau_b + k;
             const float *cf = coef4 + 4 * (tau - 1);
             const sp::LevelCoef co = {cf[0], cf[1], cf[2], 0.0f};
@@ -258,7 +255,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                                                             std::to_string(tps[rp][nb[j]])), finish(-1);
                 }
                 if (tpc[pi] != k - 1) return err("level reads a (pi, c) slot of a wrong level"), finish(-1);
-                if (inflight_phi[sl] || inflight_pc[pi]) return err("a cell writes a slot with a copy in flight"), finish(-1);
                 f2 p = {pcs[4 * pi], pcs[4 * pi + 1]}, cc = {pcs[4 * pi + 2], pcs[4 * pi + 3]};
                 const f2 out = sp::site_update(ps[rp][nb[0]], ps[rp][nb[1]], ps[rp][nb[2]], ps[rp][nb[3]], ps[rp][nb[4]],
                                                ps[rp][nb[5]], ps[rp][nb[6]], p, cc, co, q);
@@ -279,12 +275,6 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
                     log.push_back({2 * sites + g, (int32_t)id, tau, true, k + 1});
                 }
             }
-            // the copies land: the next level's imports
-            for (int sl : fl_phi) inflight_phi[sl] = 0;
-            for (int pi : fl_pc) inflight_pc[pi] = 0;
-            if (k < k_hi)
-                for (int i = t.imp_off[k + 1]; i < t.imp_off[k + 1] + t.imp_n[k + 1]; ++i)
-                    if (!load(t.imp[i], (t.imp[i] & sp::kLatImpFull) != 0, k)) return finish(-1);
         }
     }
     for (size_t i = 0; i < computed.size(); ++i)

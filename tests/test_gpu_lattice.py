@@ -78,7 +78,7 @@ def test_lattice_bit_exact_vs_monolithic(B, n, calls, nu):
     assert_bit_equal(reg, run(p, st, calls, mono=True)[0])
 
 
-@pytest.mark.parametrize("B,threads", [(16, 128), (16, 256), (16, 512), (8, 64), (12, 64), (20, 192)])
+@pytest.mark.parametrize("B,threads", [(16, 64), (16, 128), (16, 256), (16, 512), (8, 64), (12, 64), (20, 192)])
 def test_lattice_worker_counts(B, threads):
     n, steps = ((48, 48, 48) if 48 % B == 0 else (40, 60, 40)), 24
     p = params_for(n, 2.0, steps)
@@ -88,15 +88,14 @@ def test_lattice_worker_counts(B, threads):
     assert_bit_equal(reg, run(p, st, [steps], mono=True)[0])
 
 
-def test_lattice_worker_count_too_small_is_refused():
-    """Each worker holds at most six cells and four imports of a level in
-    registers: at s = 4 (660 cells in the widest level) 64 workers cannot,
-    and the plan says so instead of running."""
+def test_lattice_worker_count_not_offered_is_refused():
+    """Worker counts without a kernel instance (here 96) are refused by the
+    plan instead of running."""
     p = params_for((32, 32, 32), 0.0, 8)
     g = sp.Grid([p])
     try:
         g.set_option(sp.SP_OPT_REGION_SHAPE, sp.SP_SHAPE_LATTICE)
-        assert sp.sp_region_plan(g.h, 16, 64, sp.SP_ORDER_STATIC, None) == sp.SP_EINVAL
+        assert sp.sp_region_plan(g.h, 16, 96, sp.SP_ORDER_STATIC, None) == sp.SP_EINVAL
     finally:
         g.close()
 
