@@ -206,8 +206,8 @@ int sp_grid_create(const sp_params *p, int32_t n_sims, void *const *state_dev, v
  *                4; SP_AUTOTUNE times the sizes that divide every side.
  *   block_shape: worker threads per CTA (64, 128, 256, 320, 384, 480, 512 or 768;
  *                lattice plans: 64, 128, 192, 256 or 512, one region per CTA
- *                and no manager warp (default: 128 up to s = 3, 192 at
- *                s = 4, 256 at s = 5, 512 at s = 6);
+ *                and no manager warp (default: 128 up to s = 4, 256 at
+ *                s = 5, 512 at s = 6);
  *                every worker taking every step of a region); one manager
  *                warp is added.  0 for the default of each base (64 for
  *                bases 4 and 8, 384 for 16); SP_AUTOTUNE to time the

@@ -151,16 +151,27 @@ __device__ __forceinline__ void issue_all_imports(const uint2 *__restrict__ imp_
                                                   int cx, int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
                                                   const float2 *g0, const float2 *g1, const float4 *gpc)
 {
-    for (int i = (int)threadIdx.x; i < n; i += NW) {
-        const uint2 ie = __ldg(imp_all + i);
-        if ((int)ie.y < k_lo || (int)ie.y > k_hi) continue;
-        const uint32_t e = ie.x;
-        const int sl = lat_slot(e), row = lat_row(e);
-        const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
-        const LatRow rr = s_row[row];
-        const unsigned long long g = lat_site(e, rr.yz, cx, n0);
-        cp_async8((b ? ph1 : ph0) + (sl << 3), (b ? g1 : g0) + g);
-        if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
+    // U entries loaded before any is used, so the entry reads overlap: with
+    // 128 workers 20 cover a whole region of edge 16 (2437 imports) in one
+    // round (measured at 240^3, 128 workers: 8, 16, 20, 24 entries 1.194e11,
+    // 1.220e11, 1.226e11, 1.221e11); 160 and 192 workers keep 8 (their
+    // register budget at 5 CTAs per SM, 56 registers, spills with more)
+    constexpr int U = (NW == 160 || NW == 192) ? 8 : 20;
+    for (int i0 = (int)threadIdx.x; i0 < n; i0 += U * NW) {
+        uint2 ie[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) ie[u] = i0 + u * NW < n ? __ldg(imp_all + i0 + u * NW) : make_uint2(0u, ~0u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if ((int)ie[u].y < k_lo || (int)ie[u].y > k_hi) continue;  // (also the padding, level ~0u)
+            const uint32_t e = ie[u].x;
+            const int sl = lat_slot(e), row = lat_row(e);
+            const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
+            const LatRow rr = s_row[row];
+            const unsigned long long g = lat_site(e, rr.yz, cx, n0);
+            cp_async8((b ? ph1 : ph0) + (sl << 3), (b ? g1 : g0) + g);
+            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
+        }
     }
 }
 
@@ -175,14 +186,14 @@ __device__ __forceinline__ void copy_entries(uint32_t *ring, const uint32_t *__r
 __device__ __forceinline__ float2 ld_f2(const char *base, int off) { return *reinterpret_cast<const float2 *>(base + off); }
 
 // CTAs per SM the register budget is set for (shared memory allows 5 regions
-// of edge 16 per SM; measured at 240^3 with all imports at the region's
-// start: 192 workers at 5 per SM, 56 registers, 1.108e11 site-updates/s;
-// at 4 per SM, 72 registers, 1.020e11; 128 at 5 per SM 1.024e11; 256 at 3
-// per SM 9.32e10).
+// of edge 16 per SM, 2 of edge 20; measured at 240^3 with all imports at the
+// region's start: 128 workers at 5 per SM 1.226e11 site-updates/s, 160 at 5
+// per SM 1.204e11, 192 at 5 per SM (56 registers) 1.182e11, at 4 per SM
+// (72 registers) 1.020e11).
 template <int NW>
 constexpr int lat_min_blocks()
 {
-    return NW <= 64 ? 8 : NW <= 128 ? 6 : NW <= 192 ? 5 : NW <= 256 ? 3 : 1;
+    return NW <= 64 ? 8 : NW <= 192 ? 5 : NW <= 256 ? 2 : 1;
 }
 
 template <int NW>
