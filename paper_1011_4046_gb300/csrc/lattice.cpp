@@ -312,6 +312,25 @@ std::string build_lattice_tables(int s, LatticeTables *t)
     }
     t->imp_off[K] = (int32_t)t->imp.size();
     {
+        // the pair bit: slot ^ 1 is x +- 1 of the same row, or never imported
+        // into the same buffer
+        std::map<int, R3> cell_of;
+        for (const auto &kv : slot) cell_of[kv.second] = kv.first;
+        std::set<std::pair<int, int>> imported;
+        for (int k = 0; k < K; ++k)
+            for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i)
+                imported.insert({lat_slot(t->imp[i]), (k - 1) & 1});
+        for (int k = 0; k < K; ++k)
+            for (int i = t->imp_off[k]; i < t->imp_off[k] + t->imp_n[k]; ++i) {
+                const int sl = lat_slot(t->imp[i]), p = sl ^ 1;
+                const R3 &c = cell_of.at(sl);
+                auto q = cell_of.find(p);
+                const bool same_row =
+                    q != cell_of.end() && q->second.y == c.y && q->second.z == c.z && q->second.x - c.x == p - sl;
+                if (same_row || !imported.count({p, (k - 1) & 1})) t->imp[i] |= kLatImpPair;
+            }
+    }
+    {
         // every import in one list: by buffer, then offset (z, y, x)
         std::vector<std::pair<std::tuple<int, int, int, int>, std::pair<uint32_t, uint32_t>>> all;
         for (int k = 0; k < K; ++k)

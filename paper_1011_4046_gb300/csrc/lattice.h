@@ -86,7 +86,7 @@ constexpr int kLatMaxS = 6;  // slot indices are 13 bits, coordinates 5 bits per
 //   that every 16 consecutive entries have distinct slot residues mod 16,
 //   the first and last 8 of them distinct residues mod 8.
 // Import entry (32 bits): slot | row << 13 | full << 23 | ((k - 1) & 1) << 24 |
-// (x offset + 2s) << 25, for an import before level k.  A full import loads
+// (x offset + 2s) << 25 | pair << 30, for an import before level k.  A full import loads
 // phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k; otherwise
 // only phi(k-1) of a neighbour outside the region.
 // Every value a region imports is final when the region starts (its producers
@@ -106,6 +106,12 @@ constexpr uint32_t kLatExpPhi = 1u << 23;
 constexpr uint32_t kLatExpPc = 1u << 24;
 constexpr uint32_t kLatImpFull = 1u << 23;
 constexpr uint32_t kLatImpBuf = 1u << 24;  // the phi buffer ((k - 1) & 1) of the value
+// Bit 30 of an import entry: the slot's pair partner (slot ^ 1) holds the
+// neighbour in x of the same row, or is never imported into this buffer, so a
+// region that loads nothing else into its phi buffers at its start may copy
+// the aligned 16-byte site pair into the aligned slot pair when slot and
+// site have the same parity.
+constexpr uint32_t kLatImpPair = 1u << 30;
 constexpr int kLatRxShift = 25;
 constexpr uint32_t kLatRxMask = 0x1fu;  // 4s <= 24
 

@@ -52,16 +52,18 @@ struct alignas(16) LatRow {
 };
 
 // Shared-memory layout of one region (bytes): (pi, c) slots, the two phi
-// buffers, the row records and a ring of two levels' cell entries (every
-// cp.async16 destination on a 16-byte boundary).
+// buffers (an even number of slots each, so that every even slot starts a
+// 16-byte pair), the row records and a ring of two levels' cell entries
+// (every cp.async16 destination on a 16-byte boundary).
 struct LatSmem {
     size_t pc, ph0, ph1, row, ring, total;
     __host__ __device__ LatSmem(int n_slots, int n_foot, int W, int max_cell_n)
     {
+        const size_t nb = 8 * (((size_t)n_slots + 1) & ~(size_t)1);
         pc = 0;
         ph0 = 16 * (size_t)n_foot;
-        ph1 = ph0 + 8 * (size_t)n_slots;
-        row = (ph1 + 8 * (size_t)n_slots + 15) & ~(size_t)15;
+        ph1 = ph0 + nb;
+        row = ph1 + nb;
         ring = row + 16 * (size_t)W * W;
         total = ring + 2 * 4 * (size_t)max_cell_n;
     }
@@ -146,10 +148,16 @@ __device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, 
 // cp.async of every import of levels k_lo..k_hi of a region (the list of all
 // its imports, in address order): phi of one level into its buffer, and the
 // (pi, c) of full imports.  imp_all entries: (entry, import level).
+// pairs: the region loads nothing else into its phi buffers at its start
+// (no cut at the call's first level), so a phi import whose slot and site
+// have the same parity copies the aligned 16-byte site pair into the aligned
+// slot pair (L2 only): the other slot of the pair is then either imported too
+// (the same value, both copies write it) or written by the region only at a
+// later level, and an 8-byte copy would have to allocate in L1.
 template <int NW>
 __device__ __forceinline__ void issue_all_imports(const uint2 *__restrict__ imp_all, int n, int k_lo, int k_hi,
                                                   int cx, int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
-                                                  const float2 *g0, const float2 *g1, const float4 *gpc)
+                                                  const float2 *g0, const float2 *g1, const float4 *gpc, bool pairs)
 {
     // U entries loaded before any is used, so the entry reads overlap: with
     // 128 workers 20 cover a whole region of edge 16 (2437 imports) in one
@@ -169,7 +177,12 @@ __device__ __forceinline__ void issue_all_imports(const uint2 *__restrict__ imp_
             const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
             const LatRow rr = s_row[row];
             const unsigned long long g = lat_site(e, rr.yz, cx, n0);
-            cp_async8((b ? ph1 : ph0) + (sl << 3), (b ? g1 : g0) + g);
+            char *dst = (b ? ph1 : ph0) + (sl << 3);
+            const float2 *src = (b ? g1 : g0) + g;
+            if (pairs && (e & kLatImpPair) && ((sl ^ (int)g) & 1) == 0)
+                cp_async16(dst - ((sl & 1) << 3), src - (g & 1));
+            else
+                cp_async8(dst, src);
             if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
         }
     }
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
         // every import of the region's levels; buffer b holds values of local
         // levels of parity b, global parity par0 ^ b
         issue_all_imports<NW>(a.imp_all, a.n_imp_all, r.k_lo, r.k_hi, cx, n0, s_row, s_pcb, s_ph0, s_ph1,
-                              par0 ? g_odd : g_even, par0 ? g_even : g_odd, gpc);
+                              par0 ? g_odd : g_even, par0 ? g_even : g_odd, gpc, r.k_lo == 0);
         LevelCoef co = coef[r.tau_b + r.k_lo - 1];
         cp_async_commit();
         cp_async_wait_all();

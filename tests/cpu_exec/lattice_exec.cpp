@@ -198,9 +198,12 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         const int tau_b = 1 + s * L;
         const int k_lo = std::max(0, 1 - tau_b), k_hi = std::min(c.K - 1, nsteps - tau_b);
         if (k_lo > k_hi) return err("empty region in the call"), finish(-1);
-        for (int p = 0; p < 2; ++p) ps[p].assign(t.n_slots, {0, 0}), tps[p].assign(t.n_slots, -999);
+        for (int p = 0; p < 2; ++p) ps[p].assign((t.n_slots + 1) & ~1, {0, 0}), tps[p].assign((t.n_slots + 1) & ~1, -999);
         pcs.assign(4 * (size_t)t.n_foot, 0.0f), tpc.assign(t.n_foot, -999);
-        auto load = [&](uint32_t en, bool full, int k) {  // value of local level k (global tau_b + k)
+        // value of local level k (global tau_b + k); pair: as the kernel does for a
+        // region not cut by the call's first level, also copy the site pair's
+        // other value into the slot pair's other slot (what the array holds now)
+        auto load = [&](uint32_t en, bool full, int k, bool pair = false) {
             const int sl = slot_of(en);
             if (sl < 0 || sl >= t.n_slots) return err("slot out of range");
             int rx, ry, rz;
@@ -212,6 +215,16 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             log.push_back({par * sites + g, (int32_t)id, tau, false, k + 1});
             ps[k & 1][sl] = P[par][g];
             tps[k & 1][sl] = k;
+            if (pair && (en & sp::kLatImpPair) && ((sl ^ (int)(g & 1)) & 1) == 0) {
+                const int ps2 = sl ^ 1;
+                const int64_t g2 = g ^ 1;  // the row's other site of the aligned pair (sides are even)
+                if (ps2 >= (int)ps[k & 1].size()) return err("pair slot out of range");
+                if (tps[k & 1][ps2] != -999 && !(tps[k & 1][ps2] == tagP[par][g2] - tau_b && ps[k & 1][ps2].x == P[par][g2].x &&
+                                                  ps[k & 1][ps2].y == P[par][g2].y))
+                    return err("pair copy overwrites a loaded slot with another value");
+                ps[k & 1][ps2] = P[par][g2];
+                tps[k & 1][ps2] = tagP[par][g2] - tau_b;
+            }
             if (full) {
                 const int pi = pc_of(en);
                 if (pi < 0 || pi >= t.n_foot) return err("(pi, c) index out of range");
@@ -233,7 +246,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             const int kk = (int)t.imp_all[i + 1];
             if (kk < k_lo || kk > k_hi) continue;
             if (((en & sp::kLatImpBuf) != 0) != (((kk - 1) & 1) != 0)) return err("import buffer bit"), finish(-1);
-            if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1)) return finish(-1);
+            if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1, k_lo == 0)) return finish(-1);
         }
         for (int k = k_lo; k <= k_hi; ++k) {
             const int tau = tau_b + k;
