@@ -356,7 +356,14 @@ std::string build_lattice_tables(int s, LatticeTables *t)
         *pc = sl + t->row_pc[row];
     };
 
-    // check 0: every entry's x field is its cell's x offset (plus 2s)
+    // check 0: the row index divides by 4s + 1 as the kernel divides it, and
+    // every entry's x field is its cell's x offset (plus 2s)
+    for (int row = 0; row < W * W; ++row) {
+        const uint32_t xy = t->row_xy[row];
+        const int y2s = lat_row_y2s(row, lat_row_div(s));
+        if (y2s != (int)((xy >> 16) & 31u) || row - y2s * W != (int)((xy >> 21) & 31u))
+            return fail("row %d does not divide into its y and z", row);
+    }
     for (int k = 0; k < K; ++k) {
         auto x_ok = [&](uint32_t e) {
             int rx, ry, rz;

@@ -124,6 +124,11 @@ LAT_HD int lat_dzp(uint64_t nb) { return (int)(int16_t)(uint16_t)((nb >> 48) & 0
 LAT_HD int lat_row_base(uint32_t xy) { return (int)(int16_t)(xy & 0xffffu); }
 // x offset from the region's centre, plus 2s
 LAT_HD int lat_rx2s(uint32_t e) { return (int)((e >> kLatRxShift) & kLatRxMask); }
+// A row index's y offset plus 2s, row / (4s + 1), by one multiply and shift:
+// exact for every row index below (4s + 1)^2 with m = lat_row_div(s) (the
+// table builder checks it); the z offset plus 2s is row - (4s + 1) y.
+LAT_HD unsigned lat_row_div(int s) { return (65536u + 4u * (unsigned)s) / (4u * (unsigned)s + 1u); }
+LAT_HD int lat_row_y2s(int row, unsigned m) { return (int)(((unsigned)row * m) >> 16); }
 
 struct LatticeTables {
     int s = 0, K = 0;             // K = 4s levels per region

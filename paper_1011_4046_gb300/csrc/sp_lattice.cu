@@ -154,37 +154,50 @@ __device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, 
 // slot pair (L2 only): the other slot of the pair is then either imported too
 // (the same value, both copies write it) or written by the region only at a
 // later level, and an 8-byte copy would have to allocate in L1.
+// Import entries a thread loads before using any, so the entry reads
+// overlap: with 128 workers 20 cover a whole region of edge 16 (2437
+// imports) in one round (measured at 240^3, 128 workers: 8, 16, 20, 24
+// entries 1.194e11, 1.220e11, 1.226e11, 1.221e11 site-updates/s); 160 and
+// 192 workers keep 8 (their register budget at 5 CTAs per SM, 56 registers,
+// spills with more).
 template <int NW>
-__device__ __forceinline__ void issue_all_imports(const uint2 *__restrict__ imp_all, int n, int k_lo, int k_hi,
-                                                  int cx, int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
-                                                  const float2 *g0, const float2 *g1, const float4 *gpc, bool pairs)
+__host__ __device__ constexpr int lat_imp_batch()
 {
-    // U entries loaded before any is used, so the entry reads overlap: with
-    // 128 workers 20 cover a whole region of edge 16 (2437 imports) in one
-    // round (measured at 240^3, 128 workers: 8, 16, 20, 24 entries 1.194e11,
-    // 1.220e11, 1.226e11, 1.221e11); 160 and 192 workers keep 8 (their
-    // register budget at 5 CTAs per SM, 56 registers, spills with more)
-    constexpr int U = (NW == 160 || NW == 192) ? 8 : 20;
-    for (int i0 = (int)threadIdx.x; i0 < n; i0 += U * NW) {
-        uint2 ie[U];
+    return (NW == 160 || NW == 192) ? 8 : 20;
+}
+
+// One batch of import entries, i0 + u NW (padding: level ~0u).
+template <int NW>
+__device__ __forceinline__ void load_import_batch(uint2 (&ie)[lat_imp_batch<NW>()], const uint2 *__restrict__ imp_all,
+                                                  int n, int i0)
+{
 #pragma unroll
-        for (int u = 0; u < U; ++u) ie[u] = i0 + u * NW < n ? __ldg(imp_all + i0 + u * NW) : make_uint2(0u, ~0u);
+    for (int u = 0; u < lat_imp_batch<NW>(); ++u)
+        ie[u] = i0 + u * NW < n ? __ldg(imp_all + i0 + u * NW) : make_uint2(0u, ~0u);
+}
+
+// cp.async of one batch of imports of levels k_lo..k_hi: phi of one level
+// into its buffer, and the (pi, c) of full imports.
+template <int NW>
+__device__ __forceinline__ void issue_import_batch(const uint2 (&ie)[lat_imp_batch<NW>()], int k_lo, int k_hi, int cx,
+                                                   int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
+                                                   const float2 *g0, const float2 *g1, const float4 *gpc, bool pairs)
+{
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if ((int)ie[u].y < k_lo || (int)ie[u].y > k_hi) continue;  // (also the padding, level ~0u)
-            const uint32_t e = ie[u].x;
-            const int sl = lat_slot(e), row = lat_row(e);
-            const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
-            const LatRow rr = s_row[row];
-            const unsigned long long g = lat_site(e, rr.yz, cx, n0);
-            char *dst = (b ? ph1 : ph0) + (sl << 3);
-            const float2 *src = (b ? g1 : g0) + g;
-            if (pairs && (e & kLatImpPair) && ((sl ^ (int)g) & 1) == 0)
-                cp_async16(dst - ((sl & 1) << 3), src - (g & 1));
-            else
-                cp_async8(dst, src);
-            if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
-        }
+    for (int u = 0; u < lat_imp_batch<NW>(); ++u) {
+        if ((int)ie[u].y < k_lo || (int)ie[u].y > k_hi) continue;  // (also the padding, level ~0u)
+        const uint32_t e = ie[u].x;
+        const int sl = lat_slot(e), row = lat_row(e);
+        const bool b = (e & kLatImpBuf) != 0;  // phi buffer (k - 1) & 1; g0 / g1 are its arrays
+        const LatRow rr = s_row[row];
+        const unsigned long long g = lat_site(e, rr.yz, cx, n0);
+        char *dst = (b ? ph1 : ph0) + (sl << 3);
+        const float2 *src = (b ? g1 : g0) + g;
+        if (pairs && (e & kLatImpPair) && ((sl ^ (int)g) & 1) == 0)
+            cp_async16(dst - ((sl & 1) << 3), src - (g & 1));
+        else
+            cp_async8(dst, src);
+        if (e & kLatImpFull) cp_async16(pcb + (sl << 4) + rr.dpc, gpc + g);
     }
 }
 
@@ -225,7 +238,6 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
     char *s_ph0 = reinterpret_cast<char *>(smem + L.ph0);
     char *s_ph1 = reinterpret_cast<char *>(smem + L.ph1);
     LatRow *s_row = reinterpret_cast<LatRow *>(smem + L.row);
-    const uint32_t *__restrict__ g_xy = a.row_xy;  // row coordinates, for the per-region row indices
     uint32_t *s_ring = reinterpret_cast<uint32_t *>(smem + L.ring);
     const uint32_t *__restrict__ g_cell = a.cell;
     if (tid <= a.K) {
@@ -264,12 +276,16 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
         const LatRegion r = s_reg;
         const LatSimDev &sdr = a.sims[r.sim];
         const int n0 = sdr.n[0], cx = r.c[0] - R;
-        // the rows' wrapped y + n1 z for this region
+        // the first batch of import entries (their loads overlap the row set-up)
+        uint2 ie[lat_imp_batch<NW>()];
+        load_import_batch<NW>(ie, a.imp_all, a.n_imp_all, tid);
+        // the rows' wrapped y + n1 z for this region (row = (y + 2s) W + z + 2s)
         {
             const int n1 = sdr.n[1], n2 = sdr.n[2];
+            const unsigned wdiv = lat_row_div(a.s);
             for (int i = tid; i < WW; i += NW) {
-                const uint32_t xy = __ldg(g_xy + i);
-                int y = r.c[1] + (int)((xy >> 16) & 31u) - R, z = r.c[2] + (int)((xy >> 21) & 31u) - R;
+                const int y2s = lat_row_y2s(i, wdiv);
+                int y = r.c[1] + y2s - R, z = r.c[2] + (i - y2s * W) - R;
                 y += y < 0 ? n1 : 0;
                 y -= y >= n1 ? n1 : 0;
                 z += z < 0 ? n2 : 0;
@@ -305,8 +321,13 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
         copy_entries<NW>(s_ring + (r.k_lo & 1) * max_cell_n, g_cell, s_cell_off[r.k_lo], s_cell_n[r.k_lo]);
         // every import of the region's levels; buffer b holds values of local
         // levels of parity b, global parity par0 ^ b
-        issue_all_imports<NW>(a.imp_all, a.n_imp_all, r.k_lo, r.k_hi, cx, n0, s_row, s_pcb, s_ph0, s_ph1,
-                              par0 ? g_odd : g_even, par0 ? g_even : g_odd, gpc, r.k_lo == 0);
+        for (int i0 = tid;;) {
+            issue_import_batch<NW>(ie, r.k_lo, r.k_hi, cx, n0, s_row, s_pcb, s_ph0, s_ph1, par0 ? g_odd : g_even,
+                                   par0 ? g_even : g_odd, gpc, r.k_lo == 0);
+            i0 += lat_imp_batch<NW>() * NW;
+            if (i0 >= a.n_imp_all) break;
+            load_import_batch<NW>(ie, a.imp_all, a.n_imp_all, i0);
+        }
         LevelCoef co = coef[r.tau_b + r.k_lo - 1];
         cp_async_commit();
         cp_async_wait_all();
