@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
                 *reinterpret_cast<float4 *>(s_pcb + pcoff) = pcv;
                 if (e & (exp_phi | exp_pc)) {
                     const unsigned long long g = lat_site(e, rr.yz, cx, n0);
-                    if (e & exp_phi) gout[g] = out;
-                    if (e & exp_pc) gpc[g] = pcv;
+                    if (e & exp_phi) __stcg(gout + g, out);  // L2 only: read by other SMs
+                    if (e & exp_pc) __stcg(gpc + g, pcv);
                 }
             }
             cp_async_wait_all();

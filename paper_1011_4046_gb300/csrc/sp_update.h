@@ -17,6 +17,11 @@
 // The Kahan carry c holds the negated low-order part lost when dt*pi' was
 // added to phi; keeping it per site (8 extra bytes) makes the FP32 position
 // sum as accurate as an FP64 one over the run.
+//
+// On the GPU the real and imaginary parts go through the packed FP32 pipe
+// (one f32x2 add, multiply or fused multiply-add for both lanes wherever they
+// follow the same formula); each lane rounds as the scalar operation does,
+// so the results are those of the scalar form, bit for bit.
 #pragma once
 
 #if defined(__CUDACC__)
@@ -76,5 +81,24 @@ SP_HD V2 site_update(V2 phi, V2 xm, V2 xp, V2 ym, V2 yp, V2 zm, V2 zp, V2 &pi, V
     out.y = ti;
     return out;
 }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+// The packed form of the update above, for float2 on the device.
+__device__ __forceinline__ float2 site_update(float2 phi, float2 xm, float2 xp, float2 ym, float2 yp, float2 zm,
+                                              float2 zp, float2 &pi, float2 &c, const LevelCoef &k,
+                                              const PhysConst &q)
+{
+    const float2 s = __fadd2_rn(__fadd2_rn(__fadd2_rn(xm, xp), __fadd2_rn(ym, yp)), __fadd2_rn(zm, zp));
+    const float2 l = __fmul2_rn(__ffma2_rn(make_float2(-6.0f, -6.0f), phi, s), make_float2(q.inv_dx2, q.inv_dx2));
+    const float s2 = fma_rn(phi.x, phi.x, fma_rn(phi.y, phi.y, -q.eta2));
+    const float ms = k.m * s2;
+    const float2 f = __ffma2_rn(make_float2(-ms, -ms), phi, l);
+    pi = __ffma2_rn(make_float2(k.c1, k.c1), pi, __fmul2_rn(make_float2(k.c2, k.c2), f));
+    const float2 y = __ffma2_rn(make_float2(q.dt, q.dt), pi, make_float2(-c.x, -c.y));
+    const float2 t = __fadd2_rn(phi, y);
+    c = __fadd2_rn(__fadd2_rn(t, make_float2(-phi.x, -phi.y)), make_float2(-y.x, -y.y));
+    return t;
+}
+#endif
 
 }  // namespace sp
