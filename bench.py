@@ -595,9 +595,11 @@ def run_small(args):
 
 def run_batched(args):
     """The batched workload: 64 simulations, N drawn from the multiples of 8 in
-    [48, 160], nu in {0, 1, 2} (seeds 0-63), 192 steps each, in one autotuned
-    persistent launch replayed from a CUDA graph; the monolithic sweep of the
-    same batch beside it.  One JSON line (1 GPU)."""
+    [48, 160], nu in {0, 1, 2} (seeds 0-63), 192 steps each, in one persistent
+    launch per region size replayed from a CUDA graph (lattice regions: edge 16
+    where it divides a simulation's sides, else 8; split tiling: the autotuned
+    base and block shape); the monolithic sweep of the same batch beside it.
+    One JSON line (1 GPU)."""
     import torch
 
     from paper_1011_4046_gb300 import inputs, sp
@@ -617,7 +619,10 @@ def run_batched(args):
     updates = sum(p.n[0] * p.n[1] * p.n[2] for p in params) * steps
     g = sp.Grid(params, stream=stream)
     t0 = time.perf_counter()
-    g.plan(base_B=sp.SP_AUTOTUNE, threads=sp.SP_AUTOTUNE)
+    if args.shape == "lattice":
+        g.plan(base_B=0, threads=0, shape=sp.SP_SHAPE_LATTICE)
+    else:
+        g.plan(base_B=sp.SP_AUTOTUNE, threads=sp.SP_AUTOTUNE)
     tune_s = time.perf_counter() - t0
     infos = [g.plan_info(i) for i in range(len(params))]
     l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -650,8 +655,9 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded random-phase / Gaussian fields)",
             "config": {"workload": "batched: 64 simulations, N uniform over multiples of 8 in [48,160], "
-                                   "nu in {0,1,2}, seeds 0-63, 192 steps each, one autotuned persistent launch "
-                                   "per region base, replayed from a CUDA graph",
+                                   "nu in {0,1,2}, seeds 0-63, 192 steps each, one persistent launch per "
+                                   "region base, replayed from a CUDA graph",
+                       "region_shape": args.shape,
                        "site_updates": updates, "region_bases": bases,
                        "threads_per_cta": {str(b): next(i["threads"] for i in infos if i["base_B"] == b)
                                            for b in bases},
@@ -748,9 +754,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-levels", type=int, default=4, help="leapfrog steps per reference-arm step")
     ap.add_argument("--base", type=int, default=0, help="region base (0: the workload's)")
-    ap.add_argument("--shape", default="lattice", choices=["split", "lattice"],
-                    help="region geometry: the paper's 4-cube lattice (default) or the split tiling "
-                         "(pyramids and wedges)")
+    ap.add_argument("--shape", default=None, choices=["split", "lattice"],
+                    help="region geometry: the paper's 4-cube lattice or the split tiling (pyramids and "
+                         "wedges); default: the lattice for the grid workloads, the split tiling for the "
+                         "batch (each measured the faster there)")
     ap.add_argument("--threads", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--grid", type=int, default=0, help="grid side (profiling of smaller cases only)")
     ap.add_argument("--per-step", type=int, default=0, help="leapfrog steps per bench step (profiling only)")
@@ -762,6 +769,8 @@ def main():
     ap.add_argument("--small-steps", type=int, default=5)
     ap.add_argument("--small-warmup", type=int, default=3)
     args = ap.parse_args()
+    if args.shape is None:
+        args.shape = "split" if args.workload == "batched" else "lattice"
     if args.impl == "reference":
         out = run_reference(args)
     elif args.workload == "batched":

@@ -1161,9 +1161,10 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         const sp::LatticeTables &t = it->second.host;
         GroupCfg c;
         c.B = 4 * it->first;
-        // default (measured): 128 workers up to s = 4, 256 at s = 5, 512 at s = 6
+        // default (measured): 64 workers up to s = 2 (at most 76 cells a
+        // level), 128 at s = 3 and 4, 256 at s = 5, 512 at s = 6
         const int s_lat = it->first;
-        c.threads = threads ? threads : s_lat <= 4 ? 128 : s_lat == 5 ? 256 : 512;
+        c.threads = threads ? threads : s_lat <= 2 ? 64 : s_lat <= 4 ? 128 : s_lat == 5 ? 256 : 512;
         c.smem = sp::lattice_smem_bytes(t.n_slots, t.n_foot, t.rb_side, t.max_cell_n);
         if (c.smem > 227 * 1024) return SP_EINVAL;
         e = sp::lattice_occupancy(c.threads, c.smem, &c.ctas_per_sm);
