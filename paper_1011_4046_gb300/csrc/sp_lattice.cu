@@ -4,13 +4,16 @@
 //
 // Every region is a translate of one 4-cube of 16 s^4 site-updates over 4s
 // levels, whose cells and halo fit a few tens of KB of shared memory (s = 4:
-// 1225 phi slots in two parity buffers and 847 (pi, c) slots, 33 KB), so
-// several regions run on one SM, one per CTA.  A region
+// 1278 phi slots in each of two parity buffers and 878 (pi, c) slots, 34.5
+// KB; 44.4 KB with the row records and the entry ring), so several regions
+// run on one SM, one per CTA (five at s = 4).  A region
 //   1. waits until its four predecessors (layer L - 1) have reported done,
 //   2. copies in the values it does not compute (cp.async: phi of the halo
 //      and the whole state of cells entering the region), straight from the
 //      state arrays, all at its start and in address order (every one is
 //      final by then and stays in place until the region is done; lattice.h),
+//      a phi value as the 16-byte pair of sites around it where the pair's
+//      other slot may take it,
 //   3. evolves level by level in shared memory (the site update of
 //      sp_update.h), writing every value another region needs (a per-cell
 //      flag of the tables) straight into the state arrays,
