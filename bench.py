@@ -363,10 +363,18 @@ def run_grid(args, w, extra=None):
     # legs: allocated just before the leg, late in a long run, its copies
     # measured about half as fast (0.40 / 0.78 s against 0.26 / 0.39 s for
     # the 50 GB in / out at 1280^3)
+    # (every rank of the node holds one: pinned only with room for all of them
+    # and two more, and no e2e leg without room for them all)
     e2e_host = None
-    if not args.no_e2e:
-        e2e_nbytes = 24 * sites
-        e2e_pinned = host_available_bytes() > 3 * e2e_nbytes
+    e2e_nbytes = 24 * sites
+    local_ranks = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    e2e_room = host_available_bytes()
+    e2e_skip = None
+    if not args.no_e2e and e2e_room < (local_ranks + 1) * e2e_nbytes:
+        e2e_skip = (f"host memory: {e2e_room / 1e9:.0f} GB available for {local_ranks} rank(s) of "
+                    f"{e2e_nbytes / 1e9:.0f} GB state each")
+    if not args.no_e2e and e2e_skip is None:
+        e2e_pinned = e2e_room > (local_ranks + 2) * e2e_nbytes
         e2e_host = torch.empty(e2e_nbytes // 4, dtype=torch.float32, pin_memory=e2e_pinned)
     g = sp.Grid([p], states=[(phi, pic)], stream=stream)
     g.plan(base_B=B if args.base == 0 else args.base, threads=args.threads, shape=shape_const(shape))
@@ -423,8 +431,8 @@ def run_grid(args, w, extra=None):
         utilisation = trace_utilisation(g.trace(0, regions_per_call), info["grid"])
 
     # ---- e2e through the C ABI: state in host memory, copied in and out every step ----
-    e2e = None
-    if not args.no_e2e:
+    e2e = None if e2e_skip is None else {"unavailable": e2e_skip}
+    if e2e_host is not None:
         nbytes = e2e_nbytes
         if g.level(0) + PER * (args.e2e_steps + 1) > STEPS:
             restore(g)
