@@ -56,7 +56,8 @@ int64_t site_of(const Call &c, const int a[3], int rx, int ry, int rz)
 
 std::string g_err;
 // Planted mistakes (tests of the checks themselves): 1 = one phi buffer for
-// both parities; 2 = the DAG without the edge n - e_1 -> n.
+// both parities; 2 = the DAG without the edge n - e_1 -> n; 3 = pair imports
+// (16-byte site pairs into slot pairs) whatever the pair bit says.
 int g_plant = 0;
 bool err(const std::string &m)
 {
@@ -215,7 +216,8 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             log.push_back({par * sites + g, (int32_t)id, tau, false, k + 1});
             ps[k & 1][sl] = P[par][g];
             tps[k & 1][sl] = k;
-            if (pair && (en & sp::kLatImpPair) && ((sl ^ (int)(g & 1)) & 1) == 0) {
+            // (planted mistake 3: the pair bit ignored)
+            if (pair && ((en & sp::kLatImpPair) || g_plant == 3) && ((sl ^ (int)(g & 1)) & 1) == 0) {
                 const int ps2 = sl ^ 1;
                 const int64_t g2 = g ^ 1;  // the row's other site of the aligned pair (sides are even)
                 if (ps2 >= (int)ps[k & 1].size()) return err("pair slot out of range");

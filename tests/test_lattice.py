@@ -208,6 +208,31 @@ def test_race_check_catches_planted_mistakes(lx, plant, expect):
         lx.lx_plant(0)
 
 
+@pytest.mark.parametrize("s,n,steps", [(2, (16, 16, 16), 12), (4, (16, 16, 16), 12)])
+def test_pair_imports_need_the_pair_bit(lx, s, n, steps):
+    """A phi import may copy its aligned 16-byte site pair into the aligned
+    slot pair only where the table builder set the pair bit (the pair's other
+    slot holds the row's neighbour, or nothing imported into that buffer):
+    copying the pair for every import puts another site's value into a slot
+    another import fills, and the executor reports it."""
+    phi0, pc0 = _state(n, 6)
+    coef = _coef_table(steps, 0.0, 0.25, 2.0, 1.0, 1.0)
+    fp = ctypes.POINTER(ctypes.c_float)
+    f, p = phi0.copy(), pc0.copy()
+    msg = ctypes.create_string_buffer(256)
+    assert lx.lx_run(s, *n, steps, 0, 0, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0, f.view(np.float32).ctypes.data_as(fp),
+                     p.ctypes.data_as(fp), msg, 256, None) == 0, msg.value.decode()
+    lx.lx_plant(3)
+    try:
+        f, p = phi0.copy(), pc0.copy()
+        rc = lx.lx_run(s, *n, steps, 0, 0, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
+                       f.view(np.float32).ctypes.data_as(fp), p.ctypes.data_as(fp), msg, 256, None)
+    finally:
+        lx.lx_plant(0)
+    assert rc == -1
+    assert any(e in msg.value.decode() for e in ("pair copy overwrites", "reads a phi slot")), msg.value.decode()
+
+
 def test_layer_numbers_of_successive_calls_never_reuse_flag_values(lx):
     """Done flags are never cleared: a call waits for 'flag >= its layer
     number - 1'.  For any sequence of calls (long ones followed by short
