@@ -57,7 +57,9 @@ int64_t site_of(const Call &c, const int a[3], int rx, int ry, int rz)
 std::string g_err;
 // Planted mistakes (tests of the checks themselves): 1 = one phi buffer for
 // both parities; 2 = the DAG without the edge n - e_1 -> n; 3 = pair imports
-// (16-byte site pairs into slot pairs) whatever the pair bit says.
+// (16-byte site pairs into slot pairs) whatever the pair bit says; 4 = a
+// region cut by the call's first or last level loading every import of the
+// whole region (no level filter).
 int g_plant = 0;
 bool err(const std::string &m)
 {
@@ -246,7 +248,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
         for (size_t i = 0; i + 1 < t.imp_all.size(); i += 2) {
             const uint32_t en = t.imp_all[i];
             const int kk = (int)t.imp_all[i + 1];
-            if (kk < k_lo || kk > k_hi) continue;
+            if ((kk < k_lo || kk > k_hi) && g_plant != 4) continue;
             if (((en & sp::kLatImpBuf) != 0) != (((kk - 1) & 1) != 0)) return err("import buffer bit"), finish(-1);
             if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1, k_lo == 0)) return finish(-1);
         }

@@ -233,6 +233,26 @@ def test_pair_imports_need_the_pair_bit(lx, s, n, steps):
     assert any(e in msg.value.decode() for e in ("pair copy overwrites", "reads a phi slot")), msg.value.decode()
 
 
+def test_cut_regions_load_only_their_levels_imports(lx):
+    """All of a region's imports are final at its start only for the levels
+    it computes: a region cut by the call's first or last level that loaded
+    the imports of its other levels would read values of levels not yet (or
+    no longer) in the state arrays, and the executor reports it."""
+    s, n, steps = 2, (8, 8, 16), 12
+    phi0, pc0 = _state(n, 8)
+    coef = _coef_table(steps, 0.0, 0.25, 2.0, 1.0, 1.0)
+    fp = ctypes.POINTER(ctypes.c_float)
+    msg = ctypes.create_string_buffer(256)
+    lx.lx_plant(4)
+    try:
+        f, p = phi0.copy(), pc0.copy()
+        rc = lx.lx_run(s, *n, steps, 0, 0, coef.ctypes.data_as(fp), 0.25, 1.0, 1.0,
+                       f.view(np.float32).ctypes.data_as(fp), p.ctypes.data_as(fp), msg, 256, None)
+    finally:
+        lx.lx_plant(0)
+    assert rc == -1 and "sees" in msg.value.decode(), msg.value.decode()
+
+
 def test_layer_numbers_of_successive_calls_never_reuse_flag_values(lx):
     """Done flags are never cleared: a call waits for 'flag >= its layer
     number - 1'.  For any sequence of calls (long ones followed by short
