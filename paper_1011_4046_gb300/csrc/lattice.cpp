@@ -328,6 +328,7 @@ std::string build_lattice_tables(int s, LatticeTables *t)
                 const bool same_row =
                     q != cell_of.end() && q->second.y == c.y && q->second.z == c.z && q->second.x - c.x == p - sl;
                 if (same_row || !imported.count({p, (k - 1) & 1})) t->imp[i] |= kLatImpPair;
+                if (same_row) t->imp[i] |= kLatImpPairRow;
             }
     }
     {

@@ -86,7 +86,8 @@ constexpr int kLatMaxS = 6;  // slot indices are 13 bits, coordinates 5 bits per
 //   that every 16 consecutive entries have distinct slot residues mod 16,
 //   the first and last 8 of them distinct residues mod 8.
 // Import entry (32 bits): slot | row << 13 | full << 23 | ((k - 1) & 1) << 24 |
-// (x offset + 2s) << 25 | pair << 30, for an import before level k.  A full import loads
+// (x offset + 2s) << 25 | pair << 30 | pair-row << 31, for an import before
+// level k.  A full import loads
 // phi(k-1) and (pi, c)(k-1) of a cell entering the region at level k; otherwise
 // only phi(k-1) of a neighbour outside the region.
 // Every value a region imports is final when the region starts (its producers
@@ -112,6 +113,12 @@ constexpr uint32_t kLatImpBuf = 1u << 24;  // the phi buffer ((k - 1) & 1) of th
 // the aligned 16-byte site pair into the aligned slot pair when slot and
 // site have the same parity.
 constexpr uint32_t kLatImpPair = 1u << 30;
+// Bit 31: the pair partner is the row's neighbour in x.  A region cut by the
+// call's first level also loads its own cells of the level before its first
+// from the state at its start; a pair copy whose partner is the row's
+// neighbour writes the partner slot the same bytes any other load of it
+// does, so such a region may copy the pairs with this bit.
+constexpr uint32_t kLatImpPairRow = 1u << 31;
 constexpr int kLatRxShift = 25;
 constexpr uint32_t kLatRxMask = 0x1fu;  // 4s <= 24
 

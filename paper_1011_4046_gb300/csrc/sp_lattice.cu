@@ -151,11 +151,12 @@ __device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, 
 // cp.async of every import of levels k_lo..k_hi of a region (the list of all
 // its imports, in address order): phi of one level into its buffer, and the
 // (pi, c) of full imports.  imp_all entries: (entry, import level).
-// pairs: the region loads nothing else into its phi buffers at its start
-// (no cut at the call's first level), so a phi import whose slot and site
+// pair_bit: a phi import whose entry has this bit (kLatImpPair for a region
+// that loads nothing else into its phi buffers at its start, kLatImpPairRow
+// for one cut by the call's first level, lattice.h) and whose slot and site
 // have the same parity copies the aligned 16-byte site pair into the aligned
-// slot pair (L2 only): the other slot of the pair is then either imported too
-// (the same value, both copies write it) or written by the region only at a
+// slot pair (L2 only): the other slot of the pair then receives the same
+// bytes any other load of it does, or is written by the region only at a
 // later level, and an 8-byte copy would have to allocate in L1.
 // Import entries a thread loads before using any, so the entry reads
 // overlap: with 128 workers 20 cover a whole region of edge 16 (2437
@@ -184,7 +185,7 @@ __device__ __forceinline__ void load_import_batch(uint2 (&ie)[lat_imp_batch<NW>(
 template <int NW>
 __device__ __forceinline__ void issue_import_batch(const uint2 (&ie)[lat_imp_batch<NW>()], int k_lo, int k_hi, int cx,
                                                    int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
-                                                   const float2 *g0, const float2 *g1, const float4 *gpc, bool pairs)
+                                                   const float2 *g0, const float2 *g1, const float4 *gpc, uint32_t pair_bit)
 {
 #pragma unroll
     for (int u = 0; u < lat_imp_batch<NW>(); ++u) {
@@ -196,7 +197,7 @@ __device__ __forceinline__ void issue_import_batch(const uint2 (&ie)[lat_imp_bat
         const unsigned long long g = lat_site(e, rr.yz, cx, n0);
         char *dst = (b ? ph1 : ph0) + (sl << 3);
         const float2 *src = (b ? g1 : g0) + g;
-        if (pairs && (e & kLatImpPair) && ((sl ^ (int)g) & 1) == 0)
+        if ((e & pair_bit) && ((sl ^ (int)g) & 1) == 0)
             cp_async16(dst - ((sl & 1) << 3), src - (g & 1));
         else
             cp_async8(dst, src);
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(NW, lat_min_blocks<NW>())
         // levels of parity b, global parity par0 ^ b
         for (int i0 = tid;;) {
             issue_import_batch<NW>(ie, r.k_lo, r.k_hi, cx, n0, s_row, s_pcb, s_ph0, s_ph1, par0 ? g_odd : g_even,
-                                   par0 ? g_even : g_odd, gpc, r.k_lo == 0);
+                                   par0 ? g_even : g_odd, gpc, r.k_lo == 0 ? kLatImpPair : kLatImpPairRow);
             i0 += lat_imp_batch<NW>() * NW;
             if (i0 >= a.n_imp_all) break;
             load_import_batch<NW>(ie, a.imp_all, a.n_imp_all, i0);

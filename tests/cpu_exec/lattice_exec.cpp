@@ -219,7 +219,8 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             ps[k & 1][sl] = P[par][g];
             tps[k & 1][sl] = k;
             // (planted mistake 3: the pair bit ignored)
-            if (pair && ((en & sp::kLatImpPair) || g_plant == 3) && ((sl ^ (int)(g & 1)) & 1) == 0) {
+            if (pair && ((en & (k_lo == 0 ? sp::kLatImpPair : sp::kLatImpPairRow)) || g_plant == 3) &&
+                ((sl ^ (int)(g & 1)) & 1) == 0) {
                 const int ps2 = sl ^ 1;
                 const int64_t g2 = g ^ 1;  // the row's other site of the aligned pair (sides are even)
                 if (ps2 >= (int)ps[k & 1].size()) return err("pair slot out of range");
@@ -250,7 +251,7 @@ int lx_run(int s, int nx, int ny, int nz, int nsteps, int mode, uint64_t order_s
             const int kk = (int)t.imp_all[i + 1];
             if ((kk < k_lo || kk > k_hi) && g_plant != 4) continue;
             if (((en & sp::kLatImpBuf) != 0) != (((kk - 1) & 1) != 0)) return err("import buffer bit"), finish(-1);
-            if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1, k_lo == 0)) return finish(-1);
+            if (!load(en, (en & sp::kLatImpFull) != 0, kk - 1, true)) return finish(-1);
         }
         for (int k = k_lo; k <= k_hi; ++k) {
             const int tau = tau_b + k;
