@@ -58,7 +58,6 @@ struct LatOnDevice {
     uint32_t *d_imp_all = nullptr;  // imp_all: pairs (entry, level)
     uint64_t *d_nb = nullptr;
     int32_t *d_pcoff = nullptr;
-    uint32_t *d_xy = nullptr;
 };
 
 // One persistent launch per region base: simulations of the same base share a
@@ -633,7 +632,6 @@ void free_plan(sp_grid *g)
         cudaFree(kv.second.d_imp_all);
         cudaFree(kv.second.d_nb);
         cudaFree(kv.second.d_pcoff);
-        cudaFree(kv.second.d_xy);
     }
     g->lat.clear();
     for (float2 *f : g->phi_odd) cudaFree(f);
@@ -968,7 +966,6 @@ int evolve_lattice(sp_grid *g, int64_t n_steps, bool trace, bool timing)
         a.n_imp_all = (int)(t.imp_all.size() / 2);
         a.row_nb = ld.d_nb;
         a.row_pc = ld.d_pcoff;
-        a.row_xy = ld.d_xy;
         a.max_cell_n = t.max_cell_n;
         a.flags = g->d_lat_flags + g->lat_flag_off[gi];
         a.ctl = g->d_ctl + gi;
@@ -1139,7 +1136,6 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
         e = cudaMalloc((void **)&ld.d_cell, t.cell.size() * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_imp_all, std::max<size_t>(t.imp_all.size(), 4) * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_nb, t.row_nb.size() * sizeof(uint64_t));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_xy, t.row_xy.size() * sizeof(uint32_t));
         if (e == cudaSuccess) e = cudaMalloc((void **)&ld.d_pcoff, t.row_pc.size() * sizeof(int32_t));
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_cell, t.cell.data(), t.cell.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -1147,8 +1143,6 @@ int plan_lattice(sp_grid *g, const std::vector<int> &Bs, int threads)
             e = cudaMemcpy(ld.d_imp_all, t.imp_all.data(), t.imp_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_nb, t.row_nb.data(), t.row_nb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(ld.d_xy, t.row_xy.data(), t.row_xy.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(ld.d_pcoff, t.row_pc.data(), t.row_pc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {

@@ -187,7 +187,6 @@ struct LatArgs {
     const uint2 *imp_all;            // (entry, level) of every import of a region, address order
     const uint64_t *row_nb;          // (4s + 1)^2 row records: neighbour steps
     const int32_t *row_pc;           // (4s + 1)^2 row records: (pi, c) index - slot
-    const uint32_t *row_xy;          // (4s + 1)^2 row records: slot base, (y, z) offsets
     int max_cell_n, n_imp_all;       // longest level's cell list (padded); imports of a region
     int *flags;
     Ctl *ctl;
