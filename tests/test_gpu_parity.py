@@ -64,13 +64,13 @@ def assert_bit_equal(x, y):
 
 
 # ------------------------------------------------------------ vs the oracle
-def gpu_checkpoints(params, state, steps, every=32, base_B=0, threads=0):
+def gpu_checkpoints(params, state, steps, every=32, base_B=0, threads=0, shape=None):
     """Region-path run in calls of ``every`` steps; the state after each."""
     g = sp.Grid([params])
     out = {}
     try:
         g.write_state(0, *state)
-        g.plan(base_B=base_B, threads=threads)
+        g.plan(base_B=base_B, threads=threads, shape=shape)
         for lvl in range(every, steps + 1, every):
             g.evolve(every)
             out[lvl] = g.read_state(0)
@@ -84,14 +84,16 @@ def oracle_params(oracle_mod, p):
                                   tau_ref=p.tau_ref, damp_steps=p.damp_steps)
 
 
-def test_gpu_matches_fp64_oracle_plain_method(oracle_mod):
+@pytest.mark.parametrize("shape", [None, sp.SP_SHAPE_LATTICE])
+def test_gpu_matches_fp64_oracle_plain_method(oracle_mod, shape):
     """The plain-method workload: 32^3, nu = 0, Gaussian sigma = 0.5 (seed 0),
-    64 steps, regions of base 8: max |phi_gpu - phi_oracle| <= 1e-5 eta after
-    the run, and on both 32-step segments."""
+    64 steps, regions of base 8 (split tiling, and 4-cube lattice regions of
+    edge 8): max |phi_gpu - phi_oracle| <= 1e-5 eta after the run, and on
+    both 32-step segments."""
     n, steps = 32, 64
     p = params_for(n, 0.0, steps)
     st = inputs.initial_state((n, n, n), 0, "gaussian")
-    cps = gpu_checkpoints(p, st, steps, base_B=8)
+    cps = gpu_checkpoints(p, st, steps, base_B=8, shape=shape)
     reg = cps[steps]
     mono = run_gpu(p, st, steps, flags=sp.SP_MONOLITHIC)
     assert_bit_equal(reg, mono)
