@@ -148,22 +148,13 @@ __device__ __forceinline__ unsigned long long lat_site(uint32_t e, unsigned yz, 
     return (unsigned long long)yz * (unsigned)n0 + (unsigned)x;
 }
 
-// cp.async of every import of levels k_lo..k_hi of a region (the list of all
-// its imports, in address order): phi of one level into its buffer, and the
-// (pi, c) of full imports.  imp_all entries: (entry, import level).
-// pair_bit: a phi import whose entry has this bit (kLatImpPair for a region
-// that loads nothing else into its phi buffers at its start, kLatImpPairRow
-// for one cut by the call's first level, lattice.h) and whose slot and site
-// have the same parity copies the aligned 16-byte site pair into the aligned
-// slot pair (L2 only): the other slot of the pair then receives the same
-// bytes any other load of it does, or is written by the region only at a
-// later level, and an 8-byte copy would have to allocate in L1.
-// Import entries a thread loads before using any, so the entry reads
-// overlap: with 128 workers 20 cover a whole region of edge 16 (2437
-// imports) in one round (measured at 240^3, 128 workers: 8, 16, 20, 24
-// entries 1.194e11, 1.220e11, 1.226e11, 1.221e11 site-updates/s); 160 and
-// 192 workers keep 8 (their register budget at 5 CTAs per SM, 56 registers,
-// spills with more).
+// A region's imports: the list of all of them (imp_all, in address order;
+// entries (entry, import level)), loaded in batches, of which a thread loads
+// lat_imp_batch entries before using any, so the entry reads overlap: with
+// 128 workers 20 cover a whole region of edge 16 (2437 imports) in one round
+// (measured at 240^3, 128 workers: 8, 16, 20, 24 entries 1.194e11,
+// 1.220e11, 1.226e11, 1.221e11 site-updates/s); 160 and 192 workers keep 8
+// (their register budget at 5 CTAs per SM, 56 registers, spills with more).
 template <int NW>
 __host__ __device__ constexpr int lat_imp_batch()
 {
@@ -181,7 +172,14 @@ __device__ __forceinline__ void load_import_batch(uint2 (&ie)[lat_imp_batch<NW>(
 }
 
 // cp.async of one batch of imports of levels k_lo..k_hi: phi of one level
-// into its buffer, and the (pi, c) of full imports.
+// into its buffer, and the (pi, c) of full imports.  pair_bit: a phi import
+// whose entry has this bit (kLatImpPair for a region that loads nothing else
+// into its phi buffers at its start, kLatImpPairRow for one cut by the call's
+// first level, lattice.h) and whose slot and site have the same parity copies
+// the aligned 16-byte site pair into the aligned slot pair (L2 only): the
+// other slot of the pair then receives the same bytes any other load of it
+// does, or is written by the region only at a later level, and an 8-byte copy
+// would have to allocate in L1.
 template <int NW>
 __device__ __forceinline__ void issue_import_batch(const uint2 (&ie)[lat_imp_batch<NW>()], int k_lo, int k_hi, int cx,
                                                    int n0, const LatRow *s_row, char *pcb, char *ph0, char *ph1,
